@@ -1,0 +1,614 @@
+// CPU ORACLE -- test infrastructure only.
+//
+// A plain, slow, FP64 statement of what the solve path computes: CSR SpMV,
+// the l1-Jacobi diagonal, compatible-weighted-matching edge weights, greedy
+// (descending-key) maximum-weight matching, aggregate numbering, the Galerkin
+// triple product, dense Cholesky, the V(1,1) cycle of Eq. (amg) and PCG.
+// Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+// load this library; the GPU library never links or calls it, and this file
+// shares no code with it.
+//
+// Build: g++ -O2 -std=c++17 -ffp-contract=off -fPIC -shared (see build.py).
+// -ffp-contract=off keeps every a*b+c as two roundings, so the setup values
+// (weights, Galerkin sums, l1 diagonal) are reproducible bit for bit.
+//
+// Readings of the paper used here (each also listed in the design notes):
+//  * Matching weight (Sec. 2.3, "Coupled Aggregation Based on Compatible
+//    Weighted Matching"; the paper names the edge weight matrix C without
+//    defining it).  From the compatible-weighted-matching method it cites:
+//      c_ij = 1 - 2 a_ij w_i w_j / (a_ii w_i^2 + a_jj w_j^2),
+//    evaluated as num = ((2*a_ij)*w_i)*w_j, den = (a_ii*w_i)*w_i +
+//    (a_jj*w_j)*w_j, c = 1 - num/den, using the entry stored in row
+//    min(i, j).  Only edges with c > 0 may be matched.
+//  * Approximate maximum-weight matching: edges ordered by the strict key
+//    (c, h(min,max), -min, -max), larger first, with h the splitmix64
+//    finaliser of (uint64)min * n + max; matched greedily in descending key
+//    order, which is the unique result of locally-dominant matching under a
+//    strict total order.
+//  * k matching sweeps give aggregates of at most 2^k rows (Sec. 2.3); sweep
+//    s+1 matches the Galerkin matrix of the composite map after sweep s.
+//    Aggregates are numbered in the order of their smallest member.
+//  * P is piecewise constant with 0/1 entries (the paper's columns are
+//    normalised; a diagonal rescaling of P leaves the V-cycle unchanged).
+//  * Galerkin sum (A_c)_IJ = sum of a_ij over agg(i)=I, agg(j)=J taken in
+//    ascending (min(i,j), max(i,j), [i>j]) order, which makes A_c bitwise
+//    symmetric whenever A is.
+//  * l1 diagonal (Sec. 2.3, l1-Jacobi): d_i = sum_j |a_ij| in ascending
+//    column order (a_ii > 0); the smoother scale is s_i = w_i * (1.0 / d_i)
+//    with w_i the damping weight (1 for plain l1-Jacobi).
+//  * Coarsening stops when n_l <= max_coarse, when n_{l+1} > 0.9 n_l, or at
+//    max_levels levels; the coarsest level is solved by dense Cholesky.
+//  * Dot products: partial sums over fixed blocks of 4096 entries, then the
+//    partials in order.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+namespace {
+
+struct Csr {
+  int64_t n = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  int64_t nnz() const { return (int64_t)col.size(); }
+};
+
+struct Level {
+  Csr A;
+  std::vector<double> dinv;      // smoother scale s_i
+  std::vector<int32_t> agg;      // row -> aggregate on the next level
+  std::vector<int32_t> members;  // stride (1 << sweeps), ascending, -1 padded
+  int64_t nc = 0;
+};
+
+struct Hierarchy {
+  int sweeps = 2;
+  std::vector<Level> lev;
+  std::vector<double> chol;  // dense lower factor of the coarsest matrix, row-major
+  int64_t nco = 0;
+};
+
+// ---------------------------------------------------------------- basics
+
+double dot_blocked(int64_t n, const double* x, const double* y) {
+  const int64_t B = 4096;
+  double total = 0.0;
+  for (int64_t b0 = 0; b0 < n; b0 += B) {
+    int64_t b1 = std::min(n, b0 + B);
+    double part = 0.0;
+    for (int64_t i = b0; i < b1; ++i) part += x[i] * y[i];
+    total += part;
+  }
+  return total;
+}
+
+void spmv(const Csr& A, const double* x, double* y) {
+  for (int64_t i = 0; i < A.n; ++i) {
+    double s = 0.0;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) s += A.val[e] * x[A.col[e]];
+    y[i] = s;
+  }
+}
+
+double diag_of(const Csr& A, int64_t i) {
+  for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e)
+    if (A.col[e] == i) return A.val[e];
+  return 0.0;
+}
+
+uint64_t mix64(uint64_t z) {  // splitmix64 finaliser (Steele, Lea, Flood 2014)
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double match_weight(double aij, double aii, double ajj, double wi, double wj) {
+  double num = ((2.0 * aij) * wi) * wj;
+  double den = (aii * wi) * wi + (ajj * wj) * wj;
+  return 1.0 - num / den;
+}
+
+// ---------------------------------------------------------------- matching
+
+struct Edge {
+  double c;
+  uint64_t h;
+  int32_t lo, hi;
+};
+
+bool heavier(const Edge& a, const Edge& b) {
+  if (a.c != b.c) return a.c > b.c;
+  if (a.h != b.h) return a.h > b.h;
+  if (a.lo != b.lo) return a.lo < b.lo;
+  return a.hi < b.hi;
+}
+
+// Greedy matching in descending key order; mate[i] = partner or -1.
+void match_greedy(const Csr& A, const double* w, std::vector<int32_t>& mate) {
+  const int64_t n = A.n;
+  std::vector<double> d(n);
+  for (int64_t i = 0; i < n; ++i) d[i] = diag_of(A, i);
+  std::vector<Edge> edges;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      int64_t j = A.col[e];
+      if (j <= i) continue;  // the edge is read from row min(i, j)
+      double wi = w ? w[i] : 1.0, wj = w ? w[j] : 1.0;
+      double c = match_weight(A.val[e], d[i], d[j], wi, wj);
+      if (!(c > 0.0)) continue;
+      Edge ed;
+      ed.c = c;
+      ed.h = mix64((uint64_t)i * (uint64_t)n + (uint64_t)j);
+      ed.lo = (int32_t)i;
+      ed.hi = (int32_t)j;
+      edges.push_back(ed);
+    }
+  }
+  std::sort(edges.begin(), edges.end(), heavier);
+  mate.assign(n, -1);
+  for (const Edge& ed : edges) {
+    if (mate[ed.lo] < 0 && mate[ed.hi] < 0) {
+      mate[ed.lo] = ed.hi;
+      mate[ed.hi] = ed.lo;
+    }
+  }
+}
+
+// Aggregates numbered in the order of their smallest member.
+int64_t number_pairs(const std::vector<int32_t>& mate, std::vector<int32_t>& agg) {
+  const int64_t n = (int64_t)mate.size();
+  agg.assign(n, -1);
+  int64_t nc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int32_t m = mate[i];
+    if (m < 0 || m > i) {
+      agg[i] = (int32_t)nc;
+      if (m >= 0) agg[m] = (int32_t)nc;
+      ++nc;
+    }
+  }
+  return nc;
+}
+
+// ---------------------------------------------------------------- Galerkin
+
+struct Contrib {
+  int32_t J;
+  int64_t lo, hi;
+  int flip;  // 1 when the fine entry is (hi, lo)
+  double v;
+};
+
+bool contrib_less(const Contrib& a, const Contrib& b) {
+  if (a.J != b.J) return a.J < b.J;
+  if (a.lo != b.lo) return a.lo < b.lo;
+  if (a.hi != b.hi) return a.hi < b.hi;
+  return a.flip < b.flip;
+}
+
+void members_of(const std::vector<int32_t>& agg, int64_t nc, int stride,
+                std::vector<int32_t>& mem) {
+  mem.assign(nc * stride, -1);
+  std::vector<int> cnt(nc, 0);
+  for (int64_t i = 0; i < (int64_t)agg.size(); ++i) {
+    int32_t I = agg[i];
+    mem[(int64_t)I * stride + cnt[I]++] = (int32_t)i;
+  }
+}
+
+// (A_c)_IJ = sum_{agg(i)=I, agg(j)=J} a_ij in canonical order.
+void galerkin(const Csr& A, const std::vector<int32_t>& agg, int64_t nc,
+              const std::vector<int32_t>& mem, int stride, Csr& Ac) {
+  Ac.n = nc;
+  Ac.rowptr.assign(nc + 1, 0);
+  Ac.col.clear();
+  Ac.val.clear();
+  std::vector<Contrib> buf;
+  for (int64_t I = 0; I < nc; ++I) {
+    buf.clear();
+    for (int s = 0; s < stride; ++s) {
+      int32_t i = mem[I * stride + s];
+      if (i < 0) break;
+      for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+        int64_t j = A.col[e];
+        Contrib c;
+        c.J = agg[j];
+        c.lo = std::min<int64_t>(i, j);
+        c.hi = std::max<int64_t>(i, j);
+        c.flip = i > j ? 1 : 0;
+        c.v = A.val[e];
+        buf.push_back(c);
+      }
+    }
+    std::sort(buf.begin(), buf.end(), contrib_less);
+    size_t k = 0;
+    while (k < buf.size()) {
+      int32_t J = buf[k].J;
+      double s = buf[k].v;
+      ++k;
+      while (k < buf.size() && buf[k].J == J) {
+        s = s + buf[k].v;
+        ++k;
+      }
+      Ac.col.push_back(J);
+      Ac.val.push_back(s);
+    }
+    Ac.rowptr[I + 1] = (int64_t)Ac.col.size();
+  }
+}
+
+void l1_scale(const Csr& A, const double* omega, std::vector<double>& dinv) {
+  dinv.resize(A.n);
+  for (int64_t i = 0; i < A.n; ++i) {
+    double d = 0.0;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) d += std::fabs(A.val[e]);
+    double w = omega ? omega[i] : 1.0;
+    dinv[i] = w * (1.0 / d);
+  }
+}
+
+// ---------------------------------------------------------------- Cholesky
+
+// Right-looking Cholesky of a dense SPD n x n matrix (row-major, full).
+// Returns 0, or -(k+1) when the k-th pivot is not positive.
+int cholesky(int64_t n, std::vector<double> a, std::vector<double>& L) {
+  L.assign(n * n, 0.0);
+  for (int64_t k = 0; k < n; ++k) {
+    double piv = a[k * n + k];
+    if (!(piv > 0.0)) return -(int)(k + 1);
+    double lkk = std::sqrt(piv);
+    L[k * n + k] = lkk;
+    for (int64_t i = k + 1; i < n; ++i) L[i * n + k] = a[i * n + k] / lkk;
+    for (int64_t j = k + 1; j < n; ++j)
+      for (int64_t i = j; i < n; ++i) a[i * n + j] -= L[i * n + k] * L[j * n + k];
+  }
+  return 0;
+}
+
+void chol_solve(int64_t n, const std::vector<double>& L, const double* b, double* x) {
+  std::vector<double> y(n);
+  for (int64_t i = 0; i < n; ++i) {
+    double s = b[i];
+    for (int64_t k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int64_t k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+}
+
+std::vector<double> dense_of(const Csr& A) {
+  std::vector<double> a(A.n * A.n, 0.0);
+  for (int64_t i = 0; i < A.n; ++i)
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) a[i * A.n + A.col[e]] += A.val[e];
+  return a;
+}
+
+// ---------------------------------------------------------------- hierarchy
+
+Csr csr_copy(int64_t n, const int64_t* rp, const int32_t* ci, const double* v) {
+  Csr A;
+  A.n = n;
+  A.rowptr.assign(rp, rp + n + 1);
+  int64_t nnz = rp[n] - rp[0];
+  A.col.assign(ci + rp[0], ci + rp[0] + nnz);
+  A.val.assign(v + rp[0], v + rp[0] + nnz);
+  if (rp[0] != 0)
+    for (auto& p : A.rowptr) p -= rp[0];
+  return A;
+}
+
+// Returns 0 or a negative status (-4 not SPD coarse matrix, -1 arguments).
+int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
+          double stall, int64_t max_dense, const double* omega) {
+  H.sweeps = sweeps;
+  H.lev.clear();
+  const int stride = 1 << sweeps;
+  H.lev.emplace_back();
+  H.lev[0].A = std::move(A0);
+  for (int l = 0;; ++l) {
+    Level& L = H.lev[l];
+    l1_scale(L.A, l == 0 ? omega : nullptr, L.dinv);
+    const int64_t n = L.A.n;
+    if (n <= max_coarse || l + 1 >= max_levels) break;
+    std::vector<int32_t> comp(n);
+    for (int64_t i = 0; i < n; ++i) comp[i] = (int32_t)i;
+    int64_t nc = n;
+    Csr Acur = L.A;  // sweep 1 matches A_l itself
+    for (int s = 0; s < sweeps; ++s) {
+      std::vector<int32_t> mate, ags;
+      match_greedy(Acur, nullptr, mate);
+      nc = number_pairs(mate, ags);
+      for (int64_t i = 0; i < n; ++i) comp[i] = ags[comp[i]];
+      if (s + 1 < sweeps) {
+        std::vector<int32_t> mem;
+        int st = 1 << (s + 1);
+        members_of(comp, nc, st, mem);
+        galerkin(L.A, comp, nc, mem, st, Acur);
+      }
+    }
+    if ((double)nc > stall * (double)n) break;
+    L.agg = comp;
+    L.nc = nc;
+    members_of(comp, nc, stride, L.members);
+    Level next;
+    galerkin(L.A, L.agg, nc, L.members, stride, next.A);
+    H.lev.push_back(std::move(next));
+  }
+  const Csr& C = H.lev.back().A;
+  if (C.n > max_dense) return -1;
+  H.nco = C.n;
+  return cholesky(C.n, dense_of(C), H.chol) == 0 ? 0 : -4;
+}
+
+// V(1,1) with zero initial guess at every level (Eq. amg).
+void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
+  const Level& L = H.lev[l];
+  const int64_t n = L.A.n;
+  if (l + 1 == (int)H.lev.size()) {
+    chol_solve(n, H.chol, b, x);
+    return;
+  }
+  std::vector<double> r(n), bc(L.nc), xc(L.nc);
+  for (int64_t i = 0; i < n; ++i) x[i] = L.dinv[i] * b[i];  // pre-smooth
+  spmv(L.A, x, r.data());
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];  // residual
+  const int stride = 1 << H.sweeps;
+  for (int64_t I = 0; I < L.nc; ++I) {  // restriction b_c = P^T r
+    double s = 0.0;
+    for (int k = 0; k < stride; ++k) {
+      int32_t i = L.members[I * stride + k];
+      if (i < 0) break;
+      s = (k == 0) ? r[i] : s + r[i];
+    }
+    bc[I] = s;
+  }
+  vcycle(H, l + 1, bc.data(), xc.data());
+  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + xc[L.agg[i]];  // prolongation
+  spmv(L.A, x, r.data());
+  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + L.dinv[i] * (b[i] - r[i]);  // post-smooth
+}
+
+// ---------------------------------------------------------------- PCG
+
+struct PcgOut {
+  int iters = 0;
+  int status = 0;  // 0 converged, 1 maxit, -2 breakdown, -3 nan
+  double relres = 0, true_relres = 0;
+};
+
+PcgOut pcg(const Csr& A, const std::function<void(const double*, double*)>& prec,
+           const double* b, double* x, double tol, int maxit, int beta_form,
+           double* res_hist, double* x_hist) {
+  const int64_t n = A.n;
+  PcgOut o;
+  std::vector<double> r(n), z(n), p(n), q(n), rold;
+  spmv(A, x, q.data());
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+  double bnorm = std::sqrt(dot_blocked(n, b, b));
+  if (bnorm == 0.0) bnorm = 1.0;
+  double rr = dot_blocked(n, r.data(), r.data());
+  o.relres = std::sqrt(rr) / bnorm;
+  if (res_hist) res_hist[0] = o.relres;
+  if (x_hist) std::memcpy(x_hist, x, sizeof(double) * n);
+  if (o.relres <= tol) return o;
+  prec(r.data(), z.data());
+  p = z;
+  double rz = dot_blocked(n, r.data(), z.data());
+  int k = 0;
+  o.status = 1;
+  for (; k < maxit; ++k) {
+    spmv(A, p.data(), q.data());
+    double pq = dot_blocked(n, p.data(), q.data());
+    if (!(pq > 0.0)) {
+      o.status = std::isnan(pq) ? -3 : -2;
+      break;
+    }
+    double alpha = rz / pq;
+    if (beta_form == 1) rold = r;
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] = x[i] + alpha * p[i];
+      r[i] = r[i] - alpha * q[i];
+    }
+    rr = dot_blocked(n, r.data(), r.data());
+    o.relres = std::sqrt(rr) / bnorm;
+    if (res_hist) res_hist[k + 1] = o.relres;
+    if (x_hist) std::memcpy(x_hist + (int64_t)(k + 1) * n, x, sizeof(double) * n);
+    if (std::isnan(rr)) {
+      o.status = -3;
+      ++k;
+      break;
+    }
+    if (o.relres <= tol) {
+      o.status = 0;
+      ++k;
+      break;
+    }
+    prec(r.data(), z.data());
+    double rz_new = dot_blocked(n, r.data(), z.data());
+    double beta;
+    if (beta_form == 1) {
+      double zro = dot_blocked(n, z.data(), rold.data());
+      beta = (rz_new - zro) / rz;
+    } else {
+      beta = rz_new / rz;
+    }
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    rz = rz_new;
+  }
+  o.iters = k;
+  spmv(A, x, q.data());
+  for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
+  o.true_relres = std::sqrt(dot_blocked(n, q.data(), q.data())) / bnorm;
+  return o;
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+extern "C" {
+
+double orc_dot(int64_t n, const double* x, const double* y) { return dot_blocked(n, x, y); }
+
+void orc_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x,
+              double* y) {
+  Csr A = csr_copy(n, rp, ci, v);
+  spmv(A, x, y);
+}
+
+void orc_l1_scale(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                  const double* omega, double* dinv) {
+  Csr A = csr_copy(n, rp, ci, v);
+  std::vector<double> d;
+  l1_scale(A, omega, d);
+  std::memcpy(dinv, d.data(), sizeof(double) * n);
+}
+
+// Weight of every stored entry (0 on the diagonal), aligned with val.
+void orc_match_weights(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                       const double* w, double* c) {
+  Csr A = csr_copy(n, rp, ci, v);
+  for (int64_t i = 0; i < n; ++i) {
+    double aii = diag_of(A, i);
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      int64_t j = A.col[e];
+      if (j == i) {
+        c[e] = 0.0;
+        continue;
+      }
+      int64_t e2 = (j < i) ? -1 : e;  // weight read from row min(i, j)
+      double aij = A.val[e];
+      if (e2 < 0)
+        for (int64_t f = A.rowptr[j]; f < A.rowptr[j + 1]; ++f)
+          if (A.col[f] == i) aij = A.val[f];
+      c[e] = match_weight(aij, (j < i) ? diag_of(A, j) : aii, (j < i) ? aii : diag_of(A, j),
+                          w ? w[std::min(i, j)] : 1.0, w ? w[std::max(i, j)] : 1.0);
+    }
+  }
+}
+
+uint64_t orc_mix64(uint64_t z) { return mix64(z); }
+
+void orc_match(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* w,
+               int32_t* mate) {
+  Csr A = csr_copy(n, rp, ci, v);
+  std::vector<int32_t> m;
+  match_greedy(A, w, m);
+  std::memcpy(mate, m.data(), sizeof(int32_t) * n);
+}
+
+int64_t orc_number_pairs(int64_t n, const int32_t* mate, int32_t* agg) {
+  std::vector<int32_t> m(mate, mate + n), a;
+  int64_t nc = number_pairs(m, a);
+  std::memcpy(agg, a.data(), sizeof(int32_t) * n);
+  return nc;
+}
+
+// Galerkin product into caller buffers.  Call with rp_c only to size it
+// (col_c == nullptr), then again with col_c/val_c of rp_c[nc] entries.
+void orc_galerkin(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                  const int32_t* agg, int64_t nc, int64_t* rp_c, int32_t* col_c, double* val_c) {
+  Csr A = csr_copy(n, rp, ci, v);
+  std::vector<int32_t> ag(agg, agg + n), mem;
+  std::vector<int> cnt(nc, 0);
+  int stride = 1;
+  for (int64_t i = 0; i < n; ++i) stride = std::max(stride, ++cnt[ag[i]]);
+  members_of(ag, nc, stride, mem);
+  Csr Ac;
+  galerkin(A, ag, nc, mem, stride, Ac);
+  std::memcpy(rp_c, Ac.rowptr.data(), sizeof(int64_t) * (nc + 1));
+  if (col_c) std::memcpy(col_c, Ac.col.data(), sizeof(int32_t) * Ac.col.size());
+  if (val_c) std::memcpy(val_c, Ac.val.data(), sizeof(double) * Ac.val.size());
+}
+
+int orc_cholesky(int64_t n, const double* a, double* L) {
+  std::vector<double> A(a, a + n * n), Lv;
+  int st = cholesky(n, A, Lv);
+  std::memcpy(L, Lv.data(), sizeof(double) * n * n);
+  return st;
+}
+
+void orc_chol_solve(int64_t n, const double* L, const double* b, double* x) {
+  std::vector<double> Lv(L, L + n * n);
+  chol_solve(n, Lv, b, x);
+}
+
+// ---- hierarchy handle
+void* orc_setup(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, int sweeps,
+                int64_t max_coarse, int max_levels, double stall, int64_t max_dense,
+                const double* omega, int* status) {
+  Hierarchy* H = new Hierarchy();
+  *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
+                  omega);
+  return H;
+}
+
+void orc_free(void* h) { delete (Hierarchy*)h; }
+
+int orc_levels(void* h) { return (int)((Hierarchy*)h)->lev.size(); }
+
+int64_t orc_level_n(void* h, int l) { return ((Hierarchy*)h)->lev[l].A.n; }
+
+int64_t orc_level_nnz(void* h, int l) { return ((Hierarchy*)h)->lev[l].A.nnz(); }
+
+void orc_level_csr(void* h, int l, int64_t* rp, int32_t* ci, double* v) {
+  const Csr& A = ((Hierarchy*)h)->lev[l].A;
+  std::memcpy(rp, A.rowptr.data(), sizeof(int64_t) * (A.n + 1));
+  std::memcpy(ci, A.col.data(), sizeof(int32_t) * A.nnz());
+  std::memcpy(v, A.val.data(), sizeof(double) * A.nnz());
+}
+
+void orc_level_agg(void* h, int l, int32_t* agg) {
+  const Level& L = ((Hierarchy*)h)->lev[l];
+  std::memcpy(agg, L.agg.data(), sizeof(int32_t) * L.agg.size());
+}
+
+void orc_level_dinv(void* h, int l, double* d) {
+  const Level& L = ((Hierarchy*)h)->lev[l];
+  std::memcpy(d, L.dinv.data(), sizeof(double) * L.dinv.size());
+}
+
+void orc_coarse_factor(void* h, double* L) {
+  const Hierarchy* H = (Hierarchy*)h;
+  std::memcpy(L, H->chol.data(), sizeof(double) * H->chol.size());
+}
+
+void orc_vcycle(void* h, const double* r, double* z) { vcycle(*(Hierarchy*)h, 0, r, z); }
+
+// PCG preconditioned by the V-cycle (h != nullptr), by a dense matrix
+// (binv != nullptr, row-major n x n), or unpreconditioned (both null).
+// out = {iterations, status, relres, true_relres}.
+void orc_pcg(void* h, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+             const double* binv, const double* b, double* x, double tol, int maxit,
+             int beta_form, double* res_hist, double* x_hist, double* out) {
+  Csr A = csr_copy(n, rp, ci, v);
+  std::function<void(const double*, double*)> prec;
+  if (h) {
+    Hierarchy* H = (Hierarchy*)h;
+    prec = [H](const double* r, double* z) { vcycle(*H, 0, r, z); };
+  } else if (binv) {
+    prec = [n, binv](const double* r, double* z) {
+      for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t k = 0; k < n; ++k) s += binv[i * n + k] * r[k];
+        z[i] = s;
+      }
+    };
+  } else {
+    prec = [n](const double* r, double* z) { std::memcpy(z, r, sizeof(double) * n); };
+  }
+  PcgOut o = pcg(A, prec, b, x, tol, maxit, beta_form, res_hist, x_hist);
+  out[0] = o.iters;
+  out[1] = o.status;
+  out[2] = o.relres;
+  out[3] = o.true_relres;
+}
+
+}  // extern "C"
