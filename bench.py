@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark: seconds for PCG-AMG to reach relative residual 1e-8 on the
+256^3 7-point Poisson problem (16.8M rows, 117M nonzeros, FP64 sliced-ELL,
+V(1,1) l1-Jacobi, aggregates <= 4, dense Cholesky below 200 rows) on one
+GB300, plus the V-cycle's HBM bandwidth.
+
+One step = one pcg_solve from x0 = 0 with the hierarchy resident (the solve
+phase the paper times); the hierarchy setup is timed separately (setup_s).
+The matrix (1.4 GB) and vectors (134 MB each) exceed the 126 MB L2, so no L2
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--side 256] [--precision f64|f32]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+With N > 1 (torchrun) every rank solves its own replica of the problem: the
+path has no exchange step on one node, so there is no collective in it.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("PCG-AMG seconds to 1e-8 rel. residual (256³ Poisson, 1 GB300); "
+          "V-cycle HBM GB/s")
+SAMPLE_SIDE = 64     # CPU-oracle sample grid
+RHS_SEED = 2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--side", type=int, default=256)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax = max(smax, float(p[1]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def _oracle_iterations(side):
+    path = os.path.join(ROOT, "tests", "golden", "oracle_poisson%d.json" % side)
+    try:
+        with open(path) as f:
+            return json.load(f)["iterations"]
+    except Exception:
+        return None
+
+
+def oracle_sample(min_seconds=10.0, repeats=None, tol=1e-8):
+    """Times the CPU oracle's PCG-AMG solve on the SAMPLE_SIDE^3 problem."""
+    import oracle
+    from synthetic import poisson3d, uniform01
+
+    A = poisson3d(SAMPLE_SIDE)
+    b = uniform01(RHS_SEED, SAMPLE_SIDE ** 3)
+    H = oracle.Hierarchy(A)
+    times, its = [], None
+    t_all = time.perf_counter()
+    k = 0
+    while True:
+        t0 = time.perf_counter()
+        _, info = oracle.pcg(A, b, tol=tol, hier=H)
+        times.append(time.perf_counter() - t0)
+        its = info["iterations"]
+        k += 1
+        if repeats is not None and k >= repeats:
+            break
+        if repeats is None and time.perf_counter() - t_all >= min_seconds:
+            break
+    return times, its
+
+
+def scale_to_full(t_sample, it_sample, side):
+    """Per unknown-iteration scaling of a sample solve time to side^3."""
+    it_full = _oracle_iterations(side)
+    factor = (side / SAMPLE_SIDE) ** 3 * ((it_full / it_sample) if it_full else 1.0)
+    return t_sample * factor, it_full
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    W, K = a.warmup, a.steps
+    times, its = oracle_sample(repeats=W + K, tol=a.tol)
+    timed = times[W:]
+    per = sum(timed) / len(timed)
+    val, it_full = scale_to_full(per, its, a.side)
+    sample = ("oracle FP64 PCG-AMG solve of %d^3 Poisson (same generator, RHS seed %d) to %g: "
+              "%.3f s, %d iterations; scaled by unknowns x iterations to %d^3 (%s iterations, "
+              "the oracle's own count)" % (SAMPLE_SIDE, RHS_SEED, a.tol, per, its, a.side,
+                                           it_full))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "s",
+            "n_gpus": a.gpus, "steps": K, "warmup": W, "ms_per_step": per * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "poisson3d_%d^3_pcg_amg_v11_tol%g" % (a.side, a.tol),
+                       "sample_side": SAMPLE_SIDE},
+            "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def _traffic_from_profiles(kernel_key, workload):
+    """traffic_bytes_per_launch recorded from an ncu capture of this kernel."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, fn)) as f:
+            for ln in f:
+                p = ln.split()
+                if len(p) == 4 and p[0] == "traffic_bytes_per_launch" and p[1] == kernel_key \
+                        and p[2] == workload:
+                    return float(p[3])
+    return None
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_2406_19754_gb300 as amg
+    from synthetic import poisson3d, uniform01
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    side = a.side
+    n = side ** 3
+    A = poisson3d(side)
+    nnz = int(A[0][-1])
+    b_host = uniform01(RHS_SEED, n)
+    Ad = amg.csr_to_device(A, dev)
+    del A
+    b = torch.as_tensor(b_host, device=dev)
+    x = torch.zeros_like(b)
+
+    # warm the module on a small problem, then time the setup of the real one
+    amg.Hierarchy(*amg.csr_to_device(poisson3d(16), dev), precision=a.precision).close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = amg.Hierarchy(*Ad, precision=a.precision)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    nl = H.levels
+    levels = [H.level_info(l) for l in range(nl)]
+    oc = H.operator_complexity()
+
+    for _ in range(a.warmup):
+        x.zero_()
+        _, info = H.pcg(b, x, tol=a.tol)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    iters = []
+    for _ in range(a.steps):
+        x.zero_()
+        _, info = H.pcg(b, x, tol=a.tol)
+        iters.append(info["iterations"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if ws > 1:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    per_solve = elapsed / a.steps
+    it = iters[-1]
+    assert info["status"] == 0, info
+
+    # our kernel launches per solve (see pcg.cu / vcycle.cu)
+    V = 2 if nl == 1 else 3 * (nl - 1) + 1
+    launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1) * a.steps
+
+    # per-kernel V-cycle timing (CUDA events on the launching stream)
+    agg = {}
+    for _ in range(3):
+        H.vcycle_profile(b)
+    reps = 5
+    for _ in range(reps):
+        _, recs = H.vcycle_profile(b)
+        for r_ in recs:
+            key = (r_["level"], r_["kind"])
+            e = agg.setdefault(key, [0.0, r_["bytes"]])
+            e[0] += r_["ms"] / reps
+    vc_ms = sum(v[0] for v in agg.values())
+    vc_bytes = sum(v[1] for v in agg.values())
+    vcycle_gbs = vc_bytes / (vc_ms * 1e-3) / 1e9
+    (dl, dk), (dms, dbytes) = max(agg.items(), key=lambda kv: kv[1][0])
+    peak, peak_src = _peaks()
+    dom_name = "vcycle_%s_level%d" % (dk, dl)
+    workload = "poisson%d_%s" % (side, a.precision)
+    roof = {"bound": "hbm", "kernel": dom_name, "achieved": dbytes / (dms * 1e-3) / 1e9,
+            "peak": peak, "unit": "GB/s", "frac": dbytes / (dms * 1e-3) / 1e9 / peak,
+            "peak_source": peak_src,
+            "traffic": _traffic_from_profiles(dom_name, workload),
+            "bytes_per_launch": dbytes, "ms_per_launch": dms}
+
+    # SpMV (PCG operator) timed alone
+    y = torch.empty_like(b)
+    for _ in range(3):
+        H.spmv(b, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        H.spmv(b, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = e0.elapsed_time(e1) / 10
+    spmv_gbs = (12.0 * nnz + 16.0 * n) / (spmv_ms * 1e-3) / 1e9
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not a.no_e2e:
+        bh = torch.from_numpy(b_host).pin_memory()
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+        bd = torch.empty_like(b)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(a.steps):
+            bd.copy_(bh, non_blocking=True)
+            x.zero_()
+            H.pcg(bd, x, tol=a.tol)
+            xh.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_s = e0.elapsed_time(e1) / 1e3 / a.steps
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 8 * n}
+        assert np.allclose(xh[:8].numpy(), x[:8].cpu().numpy())
+
+    cpu = None
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        times, its_s = oracle_sample(min_seconds=10.0, tol=a.tol)
+        per = sum(times) / len(times)
+        val, it_full = scale_to_full(per, its_s, side)
+        cpu = {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": ("oracle FP64 PCG-AMG solve of %d^3 Poisson (same generator, RHS seed "
+                          "%d) to %g, %d runs of %.3f s, %d iterations; scaled by unknowns x "
+                          "iterations to %d^3 (%s iterations, the oracle's own count)"
+                          % (SAMPLE_SIDE, RHS_SEED, a.tol, len(times), per, its_s, side,
+                             it_full))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "f64"
+            else "f64 outer / f32 V-cycle", "data": "synthetic",
+            "config": {"workload": "poisson3d_%d^3_pcg_amg_v11_tol%g" % (side, a.tol),
+                       "n": n, "nnz": nnz, "levels": nl,
+                       "level_rows": [lv[0] for lv in levels],
+                       "operator_complexity": round(oc, 4), "iterations": it,
+                       "precision": a.precision, "rhs": "uniform[0,1) seed %d" % RHS_SEED,
+                       "l2": "inputs larger than L2 (matrix %.2f GB)" % (12.0 * nnz / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "setup_s": setup_s, "iterations": it, "vcycle_gbs": vcycle_gbs,
+            "vcycle_ms": vc_ms, "spmv_gbs": spmv_gbs, "spmv_ms": spmv_ms,
+            "ms_per_iteration": per_solve * 1e3 / max(it, 1),
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+            "vcycle_kernels": [{"level": k[0], "kind": k[1], "ms": round(v[0], 5),
+                                "gbs": round(v[1] / (v[0] * 1e-3) / 1e9, 1)}
+                               for k, v in sorted(agg.items())],
+        }
+        if ws > 1:
+            line["solves_per_s"] = ws * a.steps / elapsed
+        print(json.dumps(line), flush=True)
+    H.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,225 @@
+/*
+ * amg.h -- C ABI of the GB300 (sm_103a) PCG + aggregation-AMG solver.
+ *
+ * The library solves A x = b (Eq. linearsystem, Sec. 2.1) for a sparse
+ * symmetric positive-definite A by the conjugate gradient method (Sec. 3,
+ * flexible CG) preconditioned by one V(1,1) cycle of aggregation-based
+ * algebraic multigrid (Eq. amg, Sec. 2.3).  The hierarchy is built on the GPU:
+ * pairwise aggregation by weighted matching (Sec. 2.3, "Coupled Aggregation
+ * Based on Compatible Weighted Matching"), the Galerkin product
+ * A_{l+1} = P_l^T A_l P_l (Sec. 2.3) and the l1-Jacobi smoother (Sec. 2.3,
+ * "GPU enabled smoothers"); the coarsest level is solved by dense Cholesky.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers documented "device" point to GPU global memory of the current
+ *    device; "host" pointers to CPU memory.  The caller owns every buffer it
+ *    passes; the library never frees or retains caller buffers after a call
+ *    returns (amg_setup copies the matrix).
+ *  - A handle owns all internal device memory (hierarchy, work vectors,
+ *    captured CUDA graphs) until amg_destroy.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls documented "synchronous" wait for it.
+ *  - Every function returns an int status: 0 success, >0 a soft condition
+ *    (AMG_NOT_CONVERGED), <0 an error (the AMG_ERR_* codes below), mirroring
+ *    the `info` argument of the paper's library calls (Sec. 2.1).  After an
+ *    error the handle stays valid unless the status is AMG_ERR_CUDA.
+ *  - Matrices are CSR with int64 row pointers, int32 column indices sorted
+ *    ascending within each row, float64 values, zero-based.  A must be
+ *    symmetric bit for bit (a_ij == a_ji), have a positive diagonal entry
+ *    stored in every row, and be SPD.
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* amg_stream_t; /* same object as cudaStream_t */
+
+/* ------------------------------------------------------------ status codes */
+#define AMG_OK 0
+#define AMG_NOT_CONVERGED 1      /* PCG hit maxit before reaching tol */
+#define AMG_ERR_ARG (-1)         /* bad size, null pointer or option */
+#define AMG_ERR_NOT_SPD (-2)     /* coarse Cholesky pivot <= 0 */
+#define AMG_ERR_BREAKDOWN (-3)   /* PCG: p^T A p <= 0 */
+#define AMG_ERR_NAN (-4)         /* NaN/Inf in a PCG scalar */
+#define AMG_ERR_CUDA (-5)        /* a CUDA runtime call or launch failed */
+#define AMG_ERR_OOM (-6)         /* device allocation failed */
+#define AMG_ERR_DEVICE_CHECK (-7) /* a kernel's own bounds/limit check fired */
+#define AMG_ERR_UNSUPPORTED (-8) /* input outside the implemented limits */
+
+/* Value precision of the stored hierarchy and of the V-cycle arithmetic. */
+#define AMG_PREC_F64 0
+#define AMG_PREC_F32 1
+
+/* Flexible-CG beta choice (Sec. 3; flexible CG with truncation 1). */
+#define PCG_BETA_AUTO (-1)     /* FR for an F64 hierarchy, flexible otherwise */
+#define PCG_BETA_FR 0          /* beta = (r+, z+) / (r, z) */
+#define PCG_BETA_FLEXIBLE 1    /* beta = -(z+, q) / (p, q), q = A p */
+
+typedef struct amg_handle amg_handle;
+
+/* A sparse matrix in CSR (device pointers, see conventions above). */
+typedef struct amg_csr {
+  int64_t n;              /* rows = columns */
+  int64_t nnz;            /* stored entries, == rowptr[n] - rowptr[0] */
+  const int64_t* rowptr;  /* device, n + 1 */
+  const int32_t* col;     /* device, nnz */
+  const double* val;      /* device, nnz */
+} amg_csr;
+
+/* Hierarchy options (Sec. 2.3 prec%set keys in brackets). */
+typedef struct amg_options {
+  int sweeps;            /* matching sweeps per level; aggregates <= 2^sweeps
+                            [aggr_size]; 1..3, default 2 */
+  int max_levels;        /* level cap, default 30 */
+  int64_t max_coarse;    /* stop once a level has <= max_coarse rows, default 200 */
+  double stall_ratio;    /* stop when n_{l+1} > stall_ratio * n_l, default 0.9 */
+  int64_t max_dense;     /* largest coarsest level factored densely, default 4096 */
+  int precision;         /* AMG_PREC_F64 (default) or AMG_PREC_F32 */
+  int bf16_from_level;   /* with F32: levels >= this keep BF16 values; 0 = off */
+  int slice_height;      /* sliced-ELL slice height 8/16/32/64; 0 = default 32 */
+  int threads_per_row;   /* 1/2/4/8 threads per row; 0 = default */
+  int autotune;          /* 1: choose slice height / threads per row per level by
+                            timing the kernels at setup */
+} amg_options;
+
+/* PCG controls (Sec. 3, psb_krylov arguments). */
+typedef struct pcg_options {
+  double tol;            /* stop when ||r_k||_2 / ||b||_2 <= tol (recursive r) */
+  int maxit;             /* iteration cap */
+  int beta_form;         /* PCG_BETA_* */
+  double* res_history;   /* host, maxit + 1 entries or NULL: relative residuals */
+  double* x_history;     /* device, (maxit + 1) * n entries or NULL: iterates */
+  int use_graph;         /* 1 (default via pcg_default_options): replay each
+                            iteration as one captured CUDA graph */
+} pcg_options;
+
+/* Result of a solve. */
+typedef struct pcg_stats {
+  int iterations;        /* SpMV + update steps taken */
+  int status;            /* same as the return value */
+  double rel_residual;   /* recursive ||r|| / ||b|| at exit */
+  double true_rel_residual; /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+  double solve_ms;       /* device time of the solve (CUDA events) */
+} pcg_stats;
+
+/* Fills `opt` with the defaults documented above. Never fails. */
+int amg_default_options(amg_options* opt);
+int pcg_default_options(pcg_options* opt);
+
+/* Text for a status code (static storage). */
+const char* amg_status_string(int status);
+
+/*
+ * Builds the AMG hierarchy of A on the GPU (Sec. 2.3 hierarchy build and
+ * smoother build).  A: device CSR (see conventions).  opt: host, may be NULL
+ * for defaults.  On success *H receives a new handle.  Synchronous.
+ * Errors: AMG_ERR_ARG (n <= 0, nnz mismatch, bad option), AMG_ERR_NOT_SPD
+ * (coarsest matrix not SPD), AMG_ERR_UNSUPPORTED (coarsening stalled above
+ * max_dense rows, or a Galerkin row above the kernel's staging limit),
+ * AMG_ERR_OOM, AMG_ERR_CUDA.  *H is NULL on error.
+ */
+int amg_setup(const amg_csr* A, const amg_options* opt, amg_stream_t stream, amg_handle** H);
+
+/* Releases everything the handle owns. NULL is accepted. */
+int amg_destroy(amg_handle* H);
+
+/*
+ * Replaces the level-0 smoother damping weights: s_i = omega_i * (1 / d_i)
+ * with d_i the l1 row sum (Sec. 2.3, l1-Jacobi).  omega: device float32[n0],
+ * each in (0, 1], or NULL to restore omega == 1.  Levels >= 1 keep plain
+ * l1-Jacobi.  Asynchronous.
+ */
+int amg_set_smoother_weights(amg_handle* H, const float* omega, amg_stream_t stream);
+
+/*
+ * z = B r: one V(1,1) cycle with zero initial guess (Eq. amg).  r, z: device
+ * float64[n0], distinct.  Asynchronous.
+ */
+int amg_vcycle_apply(const amg_handle* H, const double* r, double* z, amg_stream_t stream);
+
+/*
+ * y = alpha * A_l x + beta * y with the level-l matrix in FP64 (level 0 = the
+ * input A).  x, y: device float64[n_l], distinct.  beta == 0 ignores y's
+ * contents.  Asynchronous.
+ */
+int amg_spmv(const amg_handle* H, int level, double alpha, const double* x, double beta,
+             double* y, amg_stream_t stream);
+
+/*
+ * Preconditioned CG for A x = b (Sec. 3; psb_krylov('FCG', ...)).
+ * b: device float64[n0]; x: device float64[n0], initial guess in, solution
+ * out.  o: host, NULL for defaults; st: host, may be NULL.  Synchronous.
+ * Returns AMG_OK, AMG_NOT_CONVERGED, AMG_ERR_BREAKDOWN, AMG_ERR_NAN or an
+ * error code.
+ */
+int pcg_solve(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
+              amg_stream_t stream);
+
+/* ----------------------------------------------------------- inspection */
+
+/* One V-cycle kernel launch timed by amg_vcycle_profile. */
+typedef struct amg_kernel_time {
+  int level;     /* hierarchy level */
+  int kind;      /* 0 pre-smooth+residual, 1 restriction, 2 prolongation+post-smooth,
+                    3 coarsest-level Cholesky solve */
+  double bytes;  /* algorithmic bytes: each matrix entry (value + int32 column) and
+                    each vector entry read or written once */
+  double ms;     /* device time between CUDA events around the launch */
+} amg_kernel_time;
+
+/*
+ * z = B r like amg_vcycle_apply, with a CUDA event pair around every kernel
+ * (the paper reports time per iteration; this splits it per kernel).
+ * out: host array of max_out records; *count receives the number of kernels
+ * launched (records beyond max_out are dropped).  Synchronous.
+ */
+int amg_vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_time* out,
+                       int max_out, int* count, amg_stream_t stream);
+
+/* Number of levels (>= 1). */
+int amg_num_levels(const amg_handle* H, int* levels);
+
+/* Rows and stored entries of level l. */
+int amg_level_info(const amg_handle* H, int level, int64_t* n, int64_t* nnz);
+
+/*
+ * Copies level-l data into caller device buffers (each may be NULL):
+ * rowptr int64[n+1], col int32[nnz], val float64[nnz] (levels >= 1 only;
+ * level 0 is the caller's own matrix), agg int32[n] (row -> aggregate on
+ * level l+1; not for the coarsest level), sscale float64[n] (smoother
+ * scale s_i = omega_i / d_i).  Asynchronous.
+ */
+int amg_level_export(const amg_handle* H, int level, int64_t* rowptr, int32_t* col,
+                     double* val, int32_t* agg, double* sscale, amg_stream_t stream);
+
+/*
+ * Pairwise locally-dominant weighted matching of the graph of A (Sec. 2.3;
+ * the first sweep of one coarsening step), as a standalone call.  A: device
+ * CSR.  mate: device int32[n], receives the partner of each row or -1.
+ * rounds: host, may be NULL, receives the number of pointer rounds.
+ * Synchronous.
+ */
+int amg_pairwise_match(const amg_csr* A, int32_t* mate, int* rounds, amg_stream_t stream);
+
+/* ----------------------------------------------------------- test hooks */
+
+/*
+ * Host-side fault injection: the `count`-th device allocation made by the
+ * library from now on (0 = the next one) fails with AMG_ERR_OOM before any
+ * GPU memory is touched; -1 disarms.  No counterpart in the paper (its
+ * routines report failures through `info`, Sec. 2.1); used to test error
+ * paths without faulting a GPU.
+ */
+int amg_debug_fail_alloc_after(long count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_GB300_H */

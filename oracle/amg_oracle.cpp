@@ -21,10 +21,10 @@
 //    (a_jj*w_j)*w_j, c = 1 - num/den, using the entry stored in row
 //    min(i, j).  Only edges with c > 0 may be matched.
 //  * Approximate maximum-weight matching: edges ordered by the strict key
-//    (c, h(min,max), -min, -max), larger first, with h the splitmix64
-//    finaliser of (uint64)min * n + max; matched greedily in descending key
-//    order, which is the unique result of locally-dominant matching under a
-//    strict total order.
+//    (c, -min, -max), larger first (equal weights go to the edge with the
+//    smaller endpoints, the order a sequential greedy pass over the rows
+//    takes); matched greedily in descending key order, which is the unique
+//    result of locally-dominant matching under a strict total order.
 //  * k matching sweeps give aggregates of at most 2^k rows (Sec. 2.3); sweep
 //    s+1 matches the Galerkin matrix of the composite map after sweep s.
 //    Aggregates are numbered in the order of their smallest member.
@@ -101,7 +101,9 @@ double diag_of(const Csr& A, int64_t i) {
   return 0.0;
 }
 
-uint64_t mix64(uint64_t z) {  // splitmix64 finaliser (Steele, Lea, Flood 2014)
+// splitmix64 finaliser (Steele, Lea, Flood 2014); exported only so the tests
+// can pin the input generator's random stream against the published values.
+uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
@@ -117,13 +119,11 @@ double match_weight(double aij, double aii, double ajj, double wi, double wj) {
 
 struct Edge {
   double c;
-  uint64_t h;
   int32_t lo, hi;
 };
 
 bool heavier(const Edge& a, const Edge& b) {
   if (a.c != b.c) return a.c > b.c;
-  if (a.h != b.h) return a.h > b.h;
   if (a.lo != b.lo) return a.lo < b.lo;
   return a.hi < b.hi;
 }
@@ -143,7 +143,6 @@ void match_greedy(const Csr& A, const double* w, std::vector<int32_t>& mate) {
       if (!(c > 0.0)) continue;
       Edge ed;
       ed.c = c;
-      ed.h = mix64((uint64_t)i * (uint64_t)n + (uint64_t)j);
       ed.lo = (int32_t)i;
       ed.hi = (int32_t)j;
       edges.push_back(ed);

@@ -1,0 +1,218 @@
+// C-ABI entry points declared in include/amg.h: argument checks, handle
+// lifecycle, and dispatch into the setup, V-cycle and PCG drivers.
+#include <string.h>
+
+#include "common.cuh"
+
+using namespace amg;
+
+extern "C" {
+
+int amg_default_options(amg_options* o) {
+  if (!o) return AMG_ERR_ARG;
+  memset(o, 0, sizeof(*o));
+  o->sweeps = 2;
+  o->max_levels = 30;
+  o->max_coarse = 200;
+  o->stall_ratio = 0.9;
+  o->max_dense = 2048;
+  o->precision = AMG_PREC_F64;
+  o->bf16_from_level = 0;
+  o->slice_height = 0;
+  o->threads_per_row = 0;
+  o->autotune = 0;
+  return AMG_OK;
+}
+
+int pcg_default_options(pcg_options* o) {
+  if (!o) return AMG_ERR_ARG;
+  memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->maxit = 500;
+  o->beta_form = PCG_BETA_AUTO;
+  o->use_graph = 1;
+  return AMG_OK;
+}
+
+const char* amg_status_string(int s) {
+  switch (s) {
+    case AMG_OK: return "ok";
+    case AMG_NOT_CONVERGED: return "not converged (maxit reached)";
+    case AMG_ERR_ARG: return "invalid argument";
+    case AMG_ERR_NOT_SPD: return "matrix not symmetric positive definite (coarse Cholesky)";
+    case AMG_ERR_BREAKDOWN: return "PCG breakdown: p^T A p <= 0";
+    case AMG_ERR_NAN: return "NaN or Inf in a PCG scalar";
+    case AMG_ERR_CUDA: return "CUDA error";
+    case AMG_ERR_OOM: return "device allocation failed";
+    case AMG_ERR_DEVICE_CHECK: return "device-side check failed";
+    case AMG_ERR_UNSUPPORTED: return "input outside implemented limits";
+    default: return "unknown status";
+  }
+}
+
+static int check_options(const amg_options& o) {
+  if (o.sweeps < 1 || o.sweeps > 3) return AMG_ERR_ARG;
+  if (o.max_levels < 1 || o.max_coarse < 1 || o.max_dense < 1 || o.max_dense > 3072)
+    return AMG_ERR_ARG;
+  if (!(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0)) return AMG_ERR_ARG;
+  if (o.precision != AMG_PREC_F64 && o.precision != AMG_PREC_F32) return AMG_ERR_ARG;
+  if (o.bf16_from_level < 0) return AMG_ERR_ARG;
+  const int C = o.slice_height, t = o.threads_per_row;
+  if (C != 0 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
+  if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8) return AMG_ERR_ARG;
+  if (C && t && C * t != 32) return AMG_ERR_ARG;
+  return AMG_OK;
+}
+
+static int check_csr(const amg_csr* A) {
+  if (!A || A->n <= 0 || A->nnz < A->n || !A->rowptr || !A->col || !A->val) return AMG_ERR_ARG;
+  if (A->n > (int64_t)0x7fffffff) return AMG_ERR_UNSUPPORTED;
+  return AMG_OK;
+}
+
+static void destroy(amg_handle* H) {
+  if (!H) return;
+  if (H->graph) cudaGraphExecDestroy(H->graph);
+  if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+  if (H->ev0) cudaEventDestroy(H->ev0);
+  if (H->ev1) cudaEventDestroy(H->ev1);
+  if (H->sc_host) cudaFreeHost(H->sc_host);
+  H->arena.release_all();
+  delete H;
+}
+
+static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_handle** out) {
+  amg_handle* H = new amg_handle();
+  *out = H;
+  if (opt)
+    H->opt = *opt;
+  else
+    amg_default_options(&H->opt);
+  AMG_TRY(check_options(H->opt));
+  AMG_CUDA_TRY(cudaGetDevice(&H->device));
+  AMG_CUDA_TRY(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->device));
+  AMG_CUDA_TRY(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
+  AMG_CUDA_TRY(cudaEventCreate(&H->ev0));
+  AMG_CUDA_TRY(cudaEventCreate(&H->ev1));
+  AMG_CUDA_TRY(cudaMallocHost((void**)&H->sc_host, sizeof(PcgScalars)));
+  Arena& ar = H->arena;
+  AMG_TRY(ar.alloc_n(&H->dev_status, 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(H->dev_status, 0, sizeof(int), s));
+  H->red.max_blocks = H->num_sms * 16;
+  AMG_TRY(ar.alloc_n(&H->red.partials, (int64_t)H->red.max_blocks * 4));
+  AMG_TRY(ar.alloc_n(&H->red.ticket, 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(H->red.ticket, 0, sizeof(unsigned), s));
+  AMG_TRY(ar.alloc_n(&H->sc, 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(H->sc, 0, sizeof(PcgScalars), s));
+  AMG_TRY(setup_hierarchy(H, A, s));
+  const int64_t n = A->n;
+  AMG_TRY(ar.alloc_n(&H->r, n));
+  AMG_TRY(ar.alloc_n(&H->z, n));
+  AMG_TRY(ar.alloc_n(&H->p, n));
+  AMG_TRY(ar.alloc_n(&H->q, n));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+int amg_setup(const amg_csr* A, const amg_options* opt, amg_stream_t stream, amg_handle** H) {
+  if (!H) return AMG_ERR_ARG;
+  *H = nullptr;
+  int rc = check_csr(A);
+  if (rc < 0) return rc;
+  amg_handle* h = nullptr;
+  rc = create(A, opt, (cudaStream_t)stream, &h);
+  if (rc < 0) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    destroy(h);
+    return rc;
+  }
+  *H = h;
+  return AMG_OK;
+}
+
+int amg_destroy(amg_handle* H) {
+  destroy(H);
+  return AMG_OK;
+}
+
+int amg_set_smoother_weights(amg_handle* H, const float* omega, amg_stream_t stream) {
+  if (!H) return AMG_ERR_ARG;
+  return set_level0_weights(H, omega, (cudaStream_t)stream);
+}
+
+int amg_vcycle_apply(const amg_handle* H, const double* r, double* z, amg_stream_t stream) {
+  if (!H || !r || !z || (const double*)z == r) return AMG_ERR_ARG;
+  return vcycle_run(H, r, z, 0, nullptr, (cudaStream_t)stream);
+}
+
+int amg_vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_time* out,
+                       int max_out, int* count, amg_stream_t stream) {
+  if (!H || !r || !z || (const double*)z == r || max_out < 0 || (max_out > 0 && !out))
+    return AMG_ERR_ARG;
+  return vcycle_profile(H, r, z, out, max_out, count, (cudaStream_t)stream);
+}
+
+int amg_spmv(const amg_handle* H, int level, double alpha, const double* x, double beta,
+             double* y, amg_stream_t stream) {
+  if (!H || level < 0 || level >= (int)H->L.size() || !x || !y || (const double*)y == x)
+    return AMG_ERR_ARG;
+  return sell_spmv64(H->L[level].A, alpha, x, beta, y, H->num_sms, (cudaStream_t)stream);
+}
+
+int pcg_solve(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
+              amg_stream_t stream) {
+  if (!H || !b || !x) return AMG_ERR_ARG;
+  pcg_options def;
+  pcg_default_options(&def);
+  const pcg_options* op = o ? o : &def;
+  if (op->maxit < 0 || !(op->tol >= 0.0)) return AMG_ERR_ARG;
+  if (op->beta_form < PCG_BETA_AUTO || op->beta_form > PCG_BETA_FLEXIBLE) return AMG_ERR_ARG;
+  return pcg_run(H, b, x, op, st, (cudaStream_t)stream);
+}
+
+int amg_num_levels(const amg_handle* H, int* levels) {
+  if (!H || !levels) return AMG_ERR_ARG;
+  *levels = (int)H->L.size();
+  return AMG_OK;
+}
+
+int amg_level_info(const amg_handle* H, int level, int64_t* n, int64_t* nnz) {
+  if (!H || level < 0 || level >= (int)H->L.size()) return AMG_ERR_ARG;
+  if (n) *n = H->L[level].n;
+  if (nnz) *nnz = H->L[level].nnz;
+  return AMG_OK;
+}
+
+int amg_level_export(const amg_handle* H, int level, int64_t* rowptr, int32_t* col, double* val,
+                     int32_t* agg, double* sscale, amg_stream_t stream) {
+  if (!H || level < 0 || level >= (int)H->L.size()) return AMG_ERR_ARG;
+  const Level& L = H->L[level];
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((rowptr || col || val) && level == 0) return AMG_ERR_ARG;
+  if (agg && !L.agg) return AMG_ERR_ARG;
+  if (rowptr)
+    AMG_CUDA_TRY(cudaMemcpyAsync(rowptr, L.rowptr, sizeof(int64_t) * (L.n + 1),
+                                 cudaMemcpyDeviceToDevice, s));
+  if (col)
+    AMG_CUDA_TRY(cudaMemcpyAsync(col, L.col, sizeof(int32_t) * L.nnz, cudaMemcpyDeviceToDevice, s));
+  if (val)
+    AMG_CUDA_TRY(cudaMemcpyAsync(val, L.val, sizeof(double) * L.nnz, cudaMemcpyDeviceToDevice, s));
+  if (agg)
+    AMG_CUDA_TRY(cudaMemcpyAsync(agg, L.agg, sizeof(int32_t) * L.n, cudaMemcpyDeviceToDevice, s));
+  if (sscale)
+    AMG_CUDA_TRY(cudaMemcpyAsync(sscale, L.s64, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+  return AMG_OK;
+}
+
+int amg_pairwise_match(const amg_csr* A, int32_t* mate, int* rounds, amg_stream_t stream) {
+  int rc = check_csr(A);
+  if (rc < 0) return rc;
+  if (!mate) return AMG_ERR_ARG;
+  Arena ar;
+  rc = match_pairwise(ar, A->n, A->rowptr, A->col, A->val, mate, rounds, (cudaStream_t)stream);
+  cudaStreamSynchronize((cudaStream_t)stream);
+  ar.release_all();
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,264 @@
+// Internal declarations shared by the translation units of the GPU library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "amg.h"
+
+namespace amg {
+
+// ------------------------------------------------------------------ errors
+
+struct Status {
+  int code = AMG_OK;
+};
+
+#define AMG_CUDA_TRY(...)                                    \
+  do {                                                       \
+    cudaError_t _e = (__VA_ARGS__);                          \
+    if (_e != cudaSuccess) {                                 \
+      amg::note_cuda_error(_e, #__VA_ARGS__, __FILE__, __LINE__); \
+      return _e == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA; \
+    }                                                        \
+  } while (0)
+
+#define AMG_TRY(...)         \
+  do {                       \
+    int _s = (__VA_ARGS__);  \
+    if (_s < 0) return _s;   \
+  } while (0)
+
+#define AMG_LAUNCH_CHECK() AMG_CUDA_TRY(cudaGetLastError())
+
+void note_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ------------------------------------------------------------------ memory
+
+// Device allocation used by every internal buffer (a failing allocation
+// turns into AMG_ERR_OOM).  Allocations are tracked by their owner.
+struct Arena {
+  std::vector<void*> blocks;
+  int alloc(void** p, size_t bytes);
+  template <typename T>
+  int alloc_n(T** p, int64_t n) {
+    return alloc((void**)p, sizeof(T) * (size_t)(n > 0 ? n : 1));
+  }
+  void release(void* p);
+  void release_all();
+};
+
+// ------------------------------------------------------------------ SELL
+
+// Sliced ELLPACK (Sec. 2.2, "Hacked ELLPACK"): rows in slices of C rows,
+// each slice an ELLPACK block of width = its longest row, stored column
+// major (entry k of row r of slice s at sliceptr[s] + k * C + r).  Padding
+// entries carry val = 0 and a valid column (the row itself).
+struct Sell {
+  int64_t n = 0, nslices = 0, nnz_pad = 0;
+  int C = 32, tpr = 1;
+  int64_t* sliceptr = nullptr;
+  int32_t* col = nullptr;
+  double* v64 = nullptr;
+  float* v32 = nullptr;
+  __nv_bfloat16* v16 = nullptr;
+};
+
+template <typename V>
+struct SellView {
+  int64_t n, nslices;
+  const int64_t* sliceptr;
+  const int32_t* col;
+  const V* val;
+};
+
+// Value storage of a level in the V-cycle.
+enum { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
+
+struct Level {
+  int64_t n = 0, nnz = 0;
+  // FP64 CSR (levels >= 1; level 0 belongs to the caller)
+  int64_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  Sell A;
+  int vstore = VAL_F64;
+  double* d = nullptr;     // l1 row sums
+  double* s64 = nullptr;   // smoother scale s_i = omega_i * (1 / d_i)
+  float* s32 = nullptr;
+  int32_t* agg = nullptr;      // row -> aggregate on level l+1
+  int32_t* members = nullptr;  // nc x stride, ascending, -1 padded
+  int stride = 0;
+  int64_t nc = 0;
+  // V-cycle work vectors of the V-cycle compute type
+  void* b = nullptr;
+  void* x = nullptr;
+  void* r = nullptr;
+};
+
+// Device-resident PCG scalars.
+struct PcgScalars {
+  double bb, rr, rz, pq, zq, alpha, beta;
+  int status;
+  int beta_form;
+  int pq_fail;
+};
+
+// Deterministic grid reduction scratch: per-block partials + ticket.
+struct Reduce {
+  double* partials = nullptr;  // [max_blocks * 4]
+  unsigned* ticket = nullptr;
+  int max_blocks = 0;
+};
+
+}  // namespace amg
+
+struct amg_handle {
+  amg_options opt;
+  int device = 0;
+  int num_sms = 0;
+  amg::Arena arena;
+  std::vector<amg::Level> L;
+  int64_t nco = 0;
+  double* Linv = nullptr;   // coarsest: L^-1, row-major n x n
+  double* LinvT = nullptr;  // (L^-1)^T, row-major
+  // PCG workspace
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  amg::PcgScalars* sc = nullptr;
+  amg::PcgScalars* sc_host = nullptr;  // pinned
+  amg::Reduce red;
+  int* dev_status = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  const double* graph_b = nullptr;
+  double* graph_x = nullptr;
+  int graph_beta = -2;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace amg {
+
+// ------------------------------------------------------------------ device helpers
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+  // splitmix64 finaliser (Steele, Lea, Flood 2014)
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+  return __ldcs(p);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 ld_stream<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return *p;
+}
+
+__device__ __forceinline__ double to_f(double v, double) { return v; }
+__device__ __forceinline__ float to_f(float v, float) { return v; }
+__device__ __forceinline__ float to_f(double v, float) { return (float)v; }
+__device__ __forceinline__ double to_f(float v, double) { return (double)v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_f(__nv_bfloat16 v, double) {
+  return (double)__bfloat162float(v);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over a block; result valid in thread 0.  Fixed tree => deterministic.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < nw ? sh[k][lane] : 0.0;
+      v[k] = warp_sum(t);
+    }
+  }
+}
+
+// Grid-wide deterministic reduction: each block stores its partial sums; the
+// last block to finish adds all partials in block order (fixed tree) and
+// runs `epi(total)` in thread 0.  Requires gridDim.x <= red.max_blocks.
+template <int NV, typename Epi>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], Reduce red, Epi epi) {
+  __shared__ bool last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red.partials[(size_t)k * red.max_blocks + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(red.ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    acc[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      acc[k] += __ldcg(&red.partials[(size_t)k * red.max_blocks + b]);
+  }
+  block_sum<NV>(acc);
+  if (threadIdx.x == 0) {
+    *red.ticket = 0u;
+    epi(acc);
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+
+int grid_for(int64_t work_items, int threads, int num_sms, int blocks_per_sm);
+
+// Exclusive scans; *total (host) receives the sum when non-null (synchronises).
+int scan_exclusive_i32(Arena& ar, const int32_t* in, int32_t* out, int64_t n, int64_t* total,
+                       cudaStream_t s);
+int scan_exclusive_i64(Arena& ar, const int64_t* in, int64_t* out, int64_t n, int64_t* total,
+                       cudaStream_t s);
+
+// SELL conversion (sell.cu)
+int sell_from_csr(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+                  const double* val, int C, int tpr, Sell& out, cudaStream_t s);
+int sell_make_copies(Arena& ar, Sell& A, int vstore, cudaStream_t s);
+int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, double* y,
+                int num_sms, cudaStream_t s);
+
+// Setup (setup.cu)
+int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s);
+int match_pairwise(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+                   const double* val, int32_t* mate, int* rounds, cudaStream_t s);
+int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s);
+
+// V-cycle (vcycle.cu).  dots: 0 none; 1 (r, z); 2 (r, z) and (z, q).
+int vcycle_run(const amg_handle* H, const double* r, double* z, int dots, const double* q,
+               cudaStream_t s);
+int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_time* out,
+                   int max_out, int* count, cudaStream_t s);
+
+// PCG (pcg.cu)
+int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
+            cudaStream_t s);
+
+}  // namespace amg

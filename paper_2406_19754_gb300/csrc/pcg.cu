@@ -1,0 +1,281 @@
+// Preconditioned conjugate gradient (Sec. 3; flexible CG with truncation 1)
+// on the level-0 sliced-ELL matrix in FP64, preconditioned by the V-cycle.
+//
+//   r = b - A x;  z = B r;  p = z
+//   repeat:  q = A p;  alpha = (r, z) / (p, q);  x += alpha p;  r -= alpha q
+//            stop when ||r|| / ||b|| <= tol
+//            z = B r;  beta = (r+, z+)/(r, z)  or  -(z+, q)/(p, q);  p = z + beta p
+//
+// Every dot product is fused into the kernel that produces its operands and
+// reduced deterministically (per-block partials, summed in block order by the
+// last block, which also computes alpha or beta on the device).  One
+// iteration (V-cycle, p update, SpMV, update) can be replayed as a single
+// captured CUDA graph; the host reads the scalars once per iteration for the
+// convergence test.
+#include <math.h>
+
+#include "sellk.cuh"
+
+namespace amg {
+
+struct InitEpi {
+  PcgScalars* sc;
+  __device__ void operator()(double (&t)[2]) const {
+    sc->rr = t[0];
+    sc->bb = t[1];
+  }
+};
+
+struct TrueResEpi {
+  PcgScalars* sc;
+  __device__ void operator()(double (&t)[1]) const { sc->zq = t[0]; }
+};
+
+// r = b - A x with (r, r) and (b, b); mode 1 writes (r, r) to sc->zq only.
+template <int TPR, int MODE>
+__global__ void __launch_bounds__(SELL_BLOCK)
+    k_residual(SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
+               double* __restrict__ r, Reduce red, PcgScalars* sc) {
+  const Lanes<TPR> ln;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double d[2] = {0.0, 0.0};
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+       sl += nw) {
+    const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(x + j); });
+    const int64_t i = sl * Lanes<TPR>::C + ln.r;
+    if (ln.t == 0 && i < A.n) {
+      const double bi = b[i];
+      const double ri = bi - acc;
+      r[i] = ri;
+      d[0] += ri * ri;
+      d[1] += bi * bi;
+    }
+  }
+  if (MODE == 0) {
+    grid_reduce<2>(d, red, InitEpi{sc});
+  } else {
+    double e[1] = {d[0]};
+    grid_reduce<1>(e, red, TrueResEpi{sc});
+  }
+}
+
+struct PqEpi {
+  PcgScalars* sc;
+  __device__ void operator()(double (&t)[1]) const {
+    const double pq = t[0];
+    sc->pq = pq;
+    if (!(pq > 0.0)) {
+      sc->status = isfinite(pq) ? AMG_ERR_BREAKDOWN : AMG_ERR_NAN;
+      sc->pq_fail = 1;
+    }
+    sc->alpha = sc->rz / pq;
+  }
+};
+
+// q = A p and (p, q); the last block sets alpha = (r, z) / (p, q).
+template <int TPR>
+__global__ void __launch_bounds__(SELL_BLOCK)
+    k_spmv_dot(SellView<double> A, const double* __restrict__ p, double* __restrict__ q,
+               Reduce red, PcgScalars* sc) {
+  const Lanes<TPR> ln;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double d[1] = {0.0};
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+       sl += nw) {
+    const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(p + j); });
+    const int64_t i = sl * Lanes<TPR>::C + ln.r;
+    if (ln.t == 0 && i < A.n) {
+      q[i] = acc;
+      d[0] += p[i] * acc;
+    }
+  }
+  grid_reduce<1>(d, red, PqEpi{sc});
+}
+
+struct RrEpi {
+  PcgScalars* sc;
+  __device__ void operator()(double (&t)[1]) const {
+    sc->rr = t[0];
+    if (!isfinite(t[0]) && sc->status == 0) sc->status = AMG_ERR_NAN;
+  }
+};
+
+// x += alpha p; r -= alpha q; (r, r).  Skipped after a breakdown.
+__global__ void k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                            const double* __restrict__ p, const double* __restrict__ q, Reduce red,
+                            PcgScalars* sc) {
+  if (sc->status < 0) return;  // uniform across the grid: no block reduces
+  const double alpha = sc->alpha;
+  double d[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = x[i] + alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    d[0] += ri * ri;
+  }
+  grid_reduce<1>(d, red, RrEpi{sc});
+}
+
+__global__ void k_p_update(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                           const PcgScalars* sc) {
+  const double beta = sc->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// ------------------------------------------------------------------ driver
+
+static int launch_residual(const amg_handle* H, int mode, const double* b, const double* x,
+                           double* r, cudaStream_t s) {
+  const Level& L = H->L[0];
+  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const SellView<double> v = view<double>(L.A, L.A.v64);
+  if (mode == 0) {
+    AMG_DISPATCH_TPR(L.A.tpr,
+                     (k_residual<TPR, 0><<<grid, SELL_BLOCK, 0, s>>>(v, b, x, r, H->red, H->sc)));
+  } else {
+    AMG_DISPATCH_TPR(L.A.tpr,
+                     (k_residual<TPR, 1><<<grid, SELL_BLOCK, 0, s>>>(v, b, x, r, H->red, H->sc)));
+  }
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+static int launch_spmv_dot(const amg_handle* H, cudaStream_t s) {
+  const Level& L = H->L[0];
+  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const SellView<double> v = view<double>(L.A, L.A.v64);
+  AMG_DISPATCH_TPR(L.A.tpr,
+                   (k_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(v, H->p, H->q, H->red, H->sc)));
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+static int launch_update(const amg_handle* H, double* x, cudaStream_t s) {
+  const int64_t n = H->L[0].n;
+  k_cg_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, x, H->r, H->p, H->q, H->red,
+                                                              H->sc);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+// One iteration after the first: z = B r (+ dots, beta), p = z + beta p,
+// q = A p (+ alpha), x/r update (+ (r, r)).
+static int iteration_body(const amg_handle* H, double* x, int dots, cudaStream_t s) {
+  const int64_t n = H->L[0].n;
+  AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s));
+  k_p_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, H->p, H->z, H->sc);
+  AMG_LAUNCH_CHECK();
+  AMG_TRY(launch_spmv_dot(H, s));
+  AMG_TRY(launch_update(H, x, s));
+  return AMG_OK;
+}
+
+static int ensure_graph(amg_handle* H, double* x, int dots, int beta_form) {
+  if (H->graph && H->graph_x == x && H->graph_beta == beta_form) return AMG_OK;
+  if (H->graph) {
+    cudaGraphExecDestroy(H->graph);
+    H->graph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  AMG_CUDA_TRY(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = iteration_body(H, x, dots, H->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(H->cap_stream, &g);
+  if (rc < 0) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  AMG_CUDA_TRY(e);
+  e = cudaGraphInstantiate(&H->graph, g, 0);
+  cudaGraphDestroy(g);
+  AMG_CUDA_TRY(e);
+  H->graph_x = x;
+  H->graph_beta = beta_form;
+  return AMG_OK;
+}
+
+static int read_scalars(amg_handle* H, cudaStream_t s) {
+  AMG_CUDA_TRY(cudaMemcpyAsync(H->sc_host, H->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
+            cudaStream_t s) {
+  const int64_t n = H->L[0].n;
+  int beta_form = o->beta_form;
+  if (beta_form == PCG_BETA_AUTO)
+    beta_form = H->opt.precision == AMG_PREC_F32 ? PCG_BETA_FLEXIBLE : PCG_BETA_FR;
+  const int dots = beta_form == PCG_BETA_FLEXIBLE ? 2 : 1;
+  if (o->use_graph) AMG_TRY(ensure_graph(H, x, dots, beta_form));
+
+  PcgScalars init = {};
+  init.beta_form = beta_form;
+  *H->sc_host = init;
+  AMG_CUDA_TRY(cudaMemcpyAsync(H->sc, H->sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+  AMG_CUDA_TRY(cudaEventRecord(H->ev0, s));
+  AMG_TRY(launch_residual(H, 0, b, x, H->r, s));
+  AMG_TRY(read_scalars(H, s));
+  double bnorm = sqrt(H->sc_host->bb);
+  if (bnorm == 0.0) bnorm = 1.0;
+  double relres = sqrt(H->sc_host->rr) / bnorm;
+  if (o->res_history) o->res_history[0] = relres;
+  if (o->x_history)
+    AMG_CUDA_TRY(cudaMemcpyAsync(o->x_history, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  int status = AMG_NOT_CONVERGED;
+  int k = 0;
+  if (relres <= o->tol) {
+    status = AMG_OK;
+  } else if (o->maxit > 0) {
+    AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(H->p, H->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    AMG_TRY(launch_spmv_dot(H, s));
+    AMG_TRY(launch_update(H, x, s));
+    for (;;) {
+      AMG_TRY(read_scalars(H, s));
+      const int dstat = H->sc_host->status;
+      if (H->sc_host->pq_fail) {  // x and r were not updated in this step
+        status = dstat;
+        break;
+      }
+      ++k;
+      relres = sqrt(H->sc_host->rr) / bnorm;
+      if (o->res_history) o->res_history[k] = relres;
+      if (o->x_history)
+        AMG_CUDA_TRY(cudaMemcpyAsync(o->x_history + (int64_t)k * n, x, sizeof(double) * n,
+                                     cudaMemcpyDeviceToDevice, s));
+      if (dstat < 0) {
+        status = dstat;
+        break;
+      }
+      if (relres <= o->tol) {
+        status = AMG_OK;
+        break;
+      }
+      if (k >= o->maxit) break;
+      if (o->use_graph) {
+        AMG_CUDA_TRY(cudaGraphLaunch(H->graph, s));
+      } else {
+        AMG_TRY(iteration_body(H, x, dots, s));
+      }
+    }
+  }
+  AMG_CUDA_TRY(cudaEventRecord(H->ev1, s));
+  // true residual ||b - A x|| / ||b|| (outside the timed region)
+  AMG_TRY(launch_residual(H, 1, b, x, H->z, s));
+  AMG_TRY(read_scalars(H, s));
+  float ms = 0.f;
+  AMG_CUDA_TRY(cudaEventElapsedTime(&ms, H->ev0, H->ev1));
+  if (st) {
+    st->iterations = k;
+    st->status = status;
+    st->rel_residual = relres;
+    st->true_rel_residual = sqrt(H->sc_host->zq) / bnorm;
+    st->solve_ms = ms;
+  }
+  return status;
+}
+
+}  // namespace amg

@@ -1,0 +1,88 @@
+// Sliced-ELL row traversal shared by the SpMV, smoother and PCG kernels.
+//
+// Mapping: one warp per slice, C * TPR == 32.  Lane = t * C + r handles row r
+// of the slice and the entries k = t, t + TPR, ... of that row, so every load
+// instruction of a warp touches C * TPR consecutive entries of the
+// column-major slice (fully coalesced).  The TPR partial sums of a row are
+// combined with xor-shuffles (fixed order).  Matrix values and column indices
+// are streamed with evict-first loads; the gathered vectors stay in L2.
+#pragma once
+
+#include "common.cuh"
+
+namespace amg {
+
+constexpr int SELL_BLOCK = 256;  // threads per block (8 slices in flight)
+
+template <int TPR>
+struct Lanes {
+  static constexpr int C = 32 / TPR;
+  int r, t;
+  __device__ __forceinline__ Lanes() {
+    int lane = threadIdx.x & 31;
+    r = lane % C;
+    t = lane / C;
+  }
+};
+
+// sum_k a_{row,k} * g(col_{row,k}) over the row's entries, accumulated in AccT.
+template <int TPR, typename AccT, typename V, typename G>
+__device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const Lanes<TPR>& ln,
+                                         G g) {
+  constexpr int C = Lanes<TPR>::C;
+  const int64_t beg = __ldg(A.sliceptr + s);
+  const int w = (int)((__ldg(A.sliceptr + s + 1) - beg) / C);
+  const int32_t* cp = A.col + beg + ln.r;
+  const V* vp = A.val + beg + ln.r;
+  AccT acc = AccT(0);
+#pragma unroll 4
+  for (int k = ln.t; k < w; k += TPR) {
+    const int j = ld_stream(cp + (int64_t)k * C);
+    const AccT a = to_f(ld_stream(vp + (int64_t)k * C), AccT(0));
+    acc = fma(a, g(j), acc);
+  }
+#pragma unroll
+  for (int o = C; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  return acc;
+}
+
+#define AMG_DISPATCH_TPR(tpr, ...)        \
+  switch (tpr) {                          \
+    case 1: {                             \
+      constexpr int TPR = 1;              \
+      __VA_ARGS__;                        \
+    } break;                              \
+    case 2: {                             \
+      constexpr int TPR = 2;              \
+      __VA_ARGS__;                        \
+    } break;                              \
+    case 4: {                             \
+      constexpr int TPR = 4;              \
+      __VA_ARGS__;                        \
+    } break;                              \
+    case 8: {                             \
+      constexpr int TPR = 8;              \
+      __VA_ARGS__;                        \
+    } break;                              \
+    default:                              \
+      return AMG_ERR_ARG;                 \
+  }
+
+template <typename V>
+inline SellView<V> view(const Sell& A, const V* val) {
+  SellView<V> v;
+  v.n = A.n;
+  v.nslices = A.nslices;
+  v.sliceptr = A.sliceptr;
+  v.col = A.col;
+  v.val = val;
+  return v;
+}
+
+// Grid for one-warp-per-slice kernels: enough blocks to fill the GPU, capped
+// by the slice count (grid-stride loop inside).
+inline int sell_grid(int64_t nslices, int num_sms, int blocks_per_sm = 8) {
+  return grid_for(nslices * 32, SELL_BLOCK, num_sms, blocks_per_sm);
+}
+
+}  // namespace amg

@@ -1,0 +1,796 @@
+// Hierarchy setup on the GPU (Sec. 2.3): l1-Jacobi diagonal, pairwise
+// locally-dominant weighted matching, aggregate numbering, the Galerkin
+// product A_{l+1} = P^T A_l P with a piecewise-constant 0/1 P, and the dense
+// Cholesky factor of the coarsest level.
+//
+// Bit-exactness: every value the setup produces (matching weights, Galerkin
+// sums, l1 row sums, Cholesky factor) is computed with explicitly rounded
+// operations (__dadd_rn, __dmul_rn, ...) in a fixed order, so no FMA
+// contraction can change a bit, and the aggregates and coarse matrices are
+// reproducible run to run and against a sequential FP64 evaluation in the
+// same order.
+#include <algorithm>
+
+#include "common.cuh"
+#include "sellk.cuh"
+
+namespace amg {
+
+// ------------------------------------------------------------------ l1 diagonal
+
+// d_i = sum_j |a_ij| in stored (ascending column) order; diag_i = a_ii.
+__global__ void k_l1_diag(int64_t n, const int64_t* rowptr, const int32_t* col,
+                          const double* val, double* d, double* diag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0, a = 0.0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      double v = val[e];
+      s = __dadd_rn(s, fabs(v));
+      if (col[e] == i) a = v;
+    }
+    if (d) d[i] = s;
+    diag[i] = a;
+  }
+}
+
+// s_i = omega_i * (1 / d_i) (omega == NULL: 1).
+__global__ void k_smoother_scale(int64_t n, const double* d, const float* omega, double* s64,
+                                 float* s32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double inv = __ddiv_rn(1.0, d[i]);
+    double w = omega ? (double)omega[i] : 1.0;
+    double s = __dmul_rn(w, inv);
+    s64[i] = s;
+    if (s32) s32[i] = (float)s;
+  }
+}
+
+// ------------------------------------------------------------------ matching
+// Edge weight (compatible weighted matching, w == 1):
+//   c_ij = 1 - (2 a_ij) / (a_ii + a_jj);  eligible iff c_ij > 0.
+// Strict total order on edges: (c, -lo, -hi), larger wins, i.e. equal weights
+// go to the edge with the smaller endpoints (the order of a sequential greedy
+// pass over the rows).  Locally-dominant rounds: every active vertex points
+// at its heaviest eligible unmatched neighbour; mutual pointers match.  Under
+// a strict total order this reproduces greedy matching in descending key
+// order exactly.
+//
+// Only vertices whose neighbourhood changed need a new pointer, so each round
+// works on a frontier list: the unmatched neighbours of the vertices matched
+// in the previous round.  Total work is O(nnz) however many rounds the
+// dependency chains need (on lexicographically numbered grids the index
+// order makes them a diagonal wavefront of ~2.5 x side rounds).
+
+struct EdgeKey {
+  double c;
+  int32_t lo, hi;
+};
+
+__device__ __forceinline__ bool heavier(const EdgeKey& a, const EdgeKey& b) {
+  if (a.c != b.c) return a.c > b.c;
+  if (a.lo != b.lo) return a.lo < b.lo;
+  return a.hi < b.hi;
+}
+
+// mate[i]: >= 0 matched, -1 active, -2 no eligible partner left (singleton).
+// flag[i]: 1 while i sits on the next frontier list.
+__global__ void k_match_cand(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
+                             const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ diag,
+                             const int32_t* __restrict__ mate, int32_t* __restrict__ cand,
+                             int32_t* __restrict__ flag, int* rounds) {
+  const int nw = *nwl;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && nw > 0) ++*rounds;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += gridDim.x * blockDim.x) {
+    const int32_t i = wl[t];
+    flag[i] = 0;
+    if (mate[i] != -1) continue;
+    const double di = diag[i];
+    EdgeKey best;
+    int32_t bj = -1;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      if (j == i || mate[j] != -1) continue;
+      const double c =
+          __dsub_rn(1.0, __ddiv_rn(__dmul_rn(2.0, val[e]), __dadd_rn(di, diag[j])));
+      if (!(c > 0.0)) continue;
+      EdgeKey k;
+      k.c = c;
+      k.lo = min(j, i);
+      k.hi = max(j, i);
+      if (bj < 0 || heavier(k, best)) {
+        best = k;
+        bj = j;
+      }
+    }
+    cand[i] = bj;
+  }
+}
+
+// Mutual pointers match; a vertex without an eligible neighbour is final.
+__global__ void k_match_commit(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
+                               const int32_t* __restrict__ cand, int32_t* mate) {
+  const int nw = *nwl;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += gridDim.x * blockDim.x) {
+    const int32_t i = wl[t];
+    if (mate[i] != -1) continue;
+    const int32_t j = cand[i];
+    if (j < 0) {
+      mate[i] = -2;
+    } else if (cand[j] == i) {  // both sides may write: same values
+      mate[i] = j;
+      mate[j] = i;
+    }
+  }
+}
+
+// Next frontier: unmatched neighbours of the pairs matched in this round.
+__global__ void k_match_expand(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
+                               const int64_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ mate,
+                               int32_t* __restrict__ flag, int32_t* __restrict__ wl_next,
+                               int* __restrict__ nwl_next) {
+  const int nw = *nwl;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nw; t += gridDim.x * blockDim.x) {
+    const int32_t i = wl[t];
+    const int32_t m = mate[i];
+    if (m < 0) continue;  // frontier vertices were unmatched when the round began
+    for (int side = 0; side < 2; ++side) {
+      const int32_t v = side == 0 ? i : m;
+      for (int64_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+        const int32_t k = col[e];
+        if (k != v && mate[k] == -1 && atomicExch(&flag[k], 1) == 0)
+          wl_next[atomicAdd(nwl_next, 1)] = k;
+      }
+    }
+  }
+}
+
+__global__ void k_match_final(int64_t n, int32_t* mate) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (mate[i] < 0) mate[i] = -1;
+}
+
+__global__ void k_iota(int64_t n, int32_t* a);
+
+static int match_rounds(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+                        const double* val, const double* diag, int32_t* mate, int* rounds_out,
+                        int num_sms, cudaStream_t s) {
+  int32_t *cand = nullptr, *flag = nullptr, *wl = nullptr;
+  int* cnt = nullptr;  // [0], [1]: frontier sizes; [2]: rounds with a non-empty frontier
+  AMG_TRY(ar.alloc_n(&cand, n));
+  AMG_TRY(ar.alloc_n(&flag, n));
+  AMG_TRY(ar.alloc_n(&wl, 2 * n));
+  AMG_TRY(ar.alloc_n(&cnt, 4));
+  AMG_CUDA_TRY(cudaMemsetAsync(mate, 0xFF, sizeof(int32_t) * n, s));
+  AMG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t) * n, s));
+  const int hcnt[4] = {(int)n, 0, 0, 0};
+  AMG_CUDA_TRY(cudaMemcpyAsync(cnt, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, s));
+  const int grid = grid_for(n, 256, num_sms, 8);
+  k_iota<<<grid, 256, 0, s>>>(n, wl);
+  AMG_LAUNCH_CHECK();
+  int cur = 0;
+  int rc = AMG_OK;
+  int64_t launched = 0;
+  for (;;) {
+    // a batch of rounds between host checks; empty rounds exit immediately
+    for (int r = 0; r < 8; ++r) {
+      int32_t* w = wl + (int64_t)cur * n;
+      int32_t* wn = wl + (int64_t)(1 - cur) * n;
+      k_match_cand<<<grid, 256, 0, s>>>(w, cnt + cur, rowptr, col, val, diag, mate, cand, flag,
+                                        cnt + 2);
+      AMG_LAUNCH_CHECK();
+      k_match_commit<<<grid, 256, 0, s>>>(w, cnt + cur, cand, mate);
+      AMG_LAUNCH_CHECK();
+      AMG_CUDA_TRY(cudaMemsetAsync(cnt + 1 - cur, 0, sizeof(int), s));
+      k_match_expand<<<grid, 256, 0, s>>>(w, cnt + cur, rowptr, col, mate, flag, wn,
+                                          cnt + 1 - cur);
+      AMG_LAUNCH_CHECK();
+      cur = 1 - cur;
+    }
+    launched += 8;
+    int h[4];
+    AMG_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h[cur] == 0) {
+      if (rounds_out) *rounds_out = h[2];
+      break;
+    }
+    if (launched > 4 * n + 64) {  // each round matches at least the heaviest edge
+      rc = AMG_ERR_DEVICE_CHECK;
+      break;
+    }
+  }
+  k_match_final<<<grid, 256, 0, s>>>(n, mate);
+  AMG_LAUNCH_CHECK();
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  ar.release(cand);
+  ar.release(flag);
+  ar.release(wl);
+  ar.release(cnt);
+  return rc;
+}
+
+int match_pairwise(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+                   const double* val, int32_t* mate, int* rounds, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  AMG_CUDA_TRY(cudaGetDevice(&dev));
+  AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double* diag = nullptr;
+  AMG_TRY(ar.alloc_n(&diag, n));
+  k_l1_diag<<<grid_for(n, 256, sms, 8), 256, 0, s>>>(n, rowptr, col, val, nullptr, diag);
+  AMG_LAUNCH_CHECK();
+  int rc = match_rounds(ar, n, rowptr, col, val, diag, mate, rounds, sms, s);
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  ar.release(diag);
+  return rc;
+}
+
+// ------------------------------------------------------------------ aggregation
+
+__global__ void k_leader_flags(int64_t n, const int32_t* mate, int32_t* flag) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t m = mate[i];
+    flag[i] = (m < 0 || m > i) ? 1 : 0;
+  }
+}
+
+// agg of a pair is the number of its smaller member; composes comp = agg[comp].
+__global__ void k_assign_compose(int64_t n_fine, int64_t n, const int32_t* mate,
+                                 const int32_t* id, int32_t* comp) {
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n_fine;
+       f += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = comp[f];
+    const int32_t m = mate[i];
+    const int32_t lead = (m < 0 || m > i) ? i : m;
+    comp[f] = id[lead];
+  }
+}
+
+__global__ void k_iota(int64_t n, int32_t* a) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
+}
+
+__global__ void k_member_fill(int64_t n, const int32_t* agg, int stride, int32_t* cnt,
+                              int32_t* members, int* status) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t I = agg[i];
+    const int slot = atomicAdd(&cnt[I], 1);
+    if (slot < stride)
+      members[(int64_t)I * stride + slot] = (int32_t)i;
+    else
+      atomicExch(status, AMG_ERR_DEVICE_CHECK);
+  }
+}
+
+__global__ void k_member_sort(int64_t nc, int stride, const int32_t* cnt, int32_t* members) {
+  for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
+       I += (int64_t)gridDim.x * blockDim.x) {
+    int32_t* m = members + I * stride;
+    const int c = min(cnt[I], stride);
+    for (int a = 1; a < c; ++a) {
+      int32_t v = m[a];
+      int b = a - 1;
+      while (b >= 0 && m[b] > v) {
+        m[b + 1] = m[b];
+        --b;
+      }
+      m[b + 1] = v;
+    }
+    for (int a = c; a < stride; ++a) m[a] = -1;
+  }
+}
+
+static int build_members(Arena& ar, int64_t n, const int32_t* agg, int64_t nc, int stride,
+                         int32_t* members, int* dev_status, int num_sms, cudaStream_t s) {
+  int32_t* cnt = nullptr;
+  AMG_TRY(ar.alloc_n(&cnt, nc));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nc, s));
+  k_member_fill<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(n, agg, stride, cnt, members,
+                                                             dev_status);
+  AMG_LAUNCH_CHECK();
+  k_member_sort<<<grid_for(nc, 256, num_sms, 8), 256, 0, s>>>(nc, stride, cnt, members);
+  AMG_LAUNCH_CHECK();
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  ar.release(cnt);
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------------ Galerkin
+// (A_c)_IJ = sum of a_ij over agg(i) = I, agg(j) = J, added left to right in
+// ascending (min(i,j), max(i,j), [i > j]) order.  For each coarse row a team
+// (one warp, or one block for long rows) stages the contributions of its
+// member rows in shared memory, sorts them by (J, min, max, flip) with a
+// bitonic network and adds each J-run sequentially.
+
+constexpr int GAL_WARP_CAP = 512;   // contributions per warp-staged row
+constexpr int GAL_WARPS = 4;        // warps per block in the warp kernel
+constexpr int GAL_BLOCK_CAP = 8192; // contributions per block-staged row
+constexpr int GAL_BLOCK_THREADS = 512;
+
+__device__ __forceinline__ bool gless(uint64_t a1, uint64_t a2, uint64_t b1, uint64_t b2) {
+  return a1 < b1 || (a1 == b1 && a2 < b2);
+}
+
+template <bool WARP>
+__device__ __forceinline__ void team_sync() {
+  if (WARP)
+    __syncwarp();
+  else
+    __syncthreads();
+}
+
+template <bool WARP>
+__device__ void bitonic_sort(uint64_t* k1, uint64_t* k2, double* v, int P, int tid, int tsz) {
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = tid; t < (P >> 1); t += tsz) {
+        const int i = 2 * stride * (t / stride) + (t % stride);
+        const int j = i + stride;
+        const bool up = (i & size) == 0;
+        const bool sw = up ? gless(k1[j], k2[j], k1[i], k2[i]) : gless(k1[i], k2[i], k1[j], k2[j]);
+        if (sw) {
+          uint64_t a = k1[i], b = k2[i];
+          double c = v[i];
+          k1[i] = k1[j];
+          k2[i] = k2[j];
+          v[i] = v[j];
+          k1[j] = a;
+          k2[j] = b;
+          v[j] = c;
+        }
+      }
+      team_sync<WARP>();
+    }
+  }
+}
+
+struct GalArgs {
+  int64_t nc;
+  int stride;
+  const int32_t* members;
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const int32_t* agg;
+  int64_t* cnt;           // count pass: distinct J per coarse row
+  const int64_t* rowptr_c;  // fill pass
+  int32_t* col_c;
+  double* val_c;
+  int32_t* ovf_list;      // rows staged by the block kernel
+  int* ovf_count;
+  int* status;
+};
+
+__device__ __forceinline__ int64_t gal_total(const GalArgs& g, int64_t I) {
+  int64_t tot = 0;
+  for (int s = 0; s < g.stride; ++s) {
+    const int32_t m = g.members[I * g.stride + s];
+    if (m < 0) break;
+    tot += g.rowptr[m + 1] - g.rowptr[m];
+  }
+  return tot;
+}
+
+template <bool WARP>
+__device__ void gal_stage(const GalArgs& g, int64_t I, uint64_t* k1, uint64_t* k2, double* v,
+                          int total, int P, int tid, int tsz) {
+  int pos = 0;
+  for (int s = 0; s < g.stride; ++s) {
+    const int32_t m = g.members[I * g.stride + s];
+    if (m < 0) break;
+    const int64_t beg = g.rowptr[m], end = g.rowptr[m + 1];
+    for (int64_t e = beg + tid; e < end; e += tsz) {
+      const int32_t j = g.col[e];
+      const uint32_t J = (uint32_t)g.agg[j];
+      const uint32_t lo = (uint32_t)min(m, j), hi = (uint32_t)max(m, j);
+      const int p = pos + (int)(e - beg);
+      k1[p] = ((uint64_t)J << 32) | lo;
+      k2[p] = ((uint64_t)hi << 1) | (uint64_t)(m > j ? 1 : 0);
+      v[p] = g.val[e];
+    }
+    pos += (int)(end - beg);
+  }
+  for (int p = total + tid; p < P; p += tsz) {
+    k1[p] = ~0ull;
+    k2[p] = ~0ull;
+    v[p] = 0.0;
+  }
+  team_sync<WARP>();
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(GAL_WARPS * 32) k_galerkin_warp(GalArgs g) {
+  extern __shared__ unsigned char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint64_t* k1 = (uint64_t*)smem + (size_t)wib * GAL_WARP_CAP;
+  uint64_t* k2 = (uint64_t*)smem + (size_t)(GAL_WARPS + wib) * GAL_WARP_CAP;
+  double* v = (double*)((uint64_t*)smem + (size_t)2 * GAL_WARPS * GAL_WARP_CAP) +
+              (size_t)wib * GAL_WARP_CAP;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t I = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < g.nc; I += nw) {
+    const int64_t tot64 = gal_total(g, I);
+    if (tot64 > GAL_WARP_CAP) {
+      if (!FILL && lane == 0) {
+        const int k = atomicAdd(g.ovf_count, 1);
+        g.ovf_list[k] = (int32_t)I;
+        g.cnt[I] = 0;
+      }
+      continue;
+    }
+    const int total = (int)tot64;
+    const int P = next_pow2(total);
+    gal_stage<true>(g, I, k1, k2, v, total, P, lane, 32);
+    bitonic_sort<true>(k1, k2, v, P, lane, 32);
+    int base = 0;
+    const int64_t off = FILL ? g.rowptr_c[I] : 0;
+    for (int c = 0; c < total; c += 32) {
+      const int p = c + lane;
+      const bool st = p < total && (p == 0 || (k1[p] >> 32) != (k1[p - 1] >> 32));
+      const unsigned msk = __ballot_sync(0xffffffffu, st);
+      if (FILL && st) {
+        const int rank = base + __popc(msk & ((1u << lane) - 1u));
+        const uint64_t J = k1[p] >> 32;
+        double s = v[p];
+        for (int q = p + 1; q < total && (k1[q] >> 32) == J; ++q) s = __dadd_rn(s, v[q]);
+        g.col_c[off + rank] = (int32_t)J;
+        g.val_c[off + rank] = s;
+      }
+      base += __popc(msk);
+    }
+    if (!FILL && lane == 0) g.cnt[I] = base;
+    __syncwarp();
+  }
+}
+
+// Long rows: one block per listed row, staging up to GAL_BLOCK_CAP entries.
+template <bool FILL>
+__global__ void __launch_bounds__(GAL_BLOCK_THREADS) k_galerkin_block(GalArgs g, int nrows) {
+  extern __shared__ unsigned char smem[];
+  uint64_t* k1 = (uint64_t*)smem;
+  uint64_t* k2 = k1 + GAL_BLOCK_CAP;
+  double* v = (double*)(k2 + GAL_BLOCK_CAP);
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int64_t I = g.ovf_list[r];
+    const int64_t tot64 = gal_total(g, I);
+    if (tot64 > GAL_BLOCK_CAP) {
+      if (threadIdx.x == 0) {
+        atomicExch(g.status, AMG_ERR_UNSUPPORTED);
+        if (!FILL) g.cnt[I] = 0;
+      }
+      continue;
+    }
+    const int total = (int)tot64;
+    const int P = next_pow2(total);
+    gal_stage<false>(g, I, k1, k2, v, total, P, threadIdx.x, blockDim.x);
+    bitonic_sort<false>(k1, k2, v, P, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) {  // rare: sequential run-length pass
+      const int64_t off = FILL ? g.rowptr_c[I] : 0;
+      int rank = 0;
+      int p = 0;
+      while (p < total) {
+        const uint64_t J = k1[p] >> 32;
+        double s = v[p];
+        int q = p + 1;
+        for (; q < total && (k1[q] >> 32) == J; ++q) s = __dadd_rn(s, v[q]);
+        if (FILL) {
+          g.col_c[off + rank] = (int32_t)J;
+          g.val_c[off + rank] = s;
+        }
+        ++rank;
+        p = q;
+      }
+      if (!FILL) g.cnt[I] = rank;
+    }
+    __syncthreads();
+  }
+}
+
+// Coarse CSR of P^T A P for aggregates `agg` with member lists `members`.
+static int galerkin(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+                    const double* val, const int32_t* agg, const int32_t* members, int stride,
+                    int64_t nc, int64_t** rp_c, int32_t** col_c, double** val_c, int64_t* nnz_c,
+                    int* dev_status, int num_sms, cudaStream_t s) {
+  (void)n;
+  GalArgs g;
+  g.nc = nc;
+  g.stride = stride;
+  g.members = members;
+  g.rowptr = rowptr;
+  g.col = col;
+  g.val = val;
+  g.agg = agg;
+  g.status = dev_status;
+  AMG_TRY(ar.alloc_n(&g.cnt, nc + 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(g.cnt, 0, sizeof(int64_t) * (nc + 1), s));
+  AMG_TRY(ar.alloc_n(&g.ovf_list, nc));
+  AMG_TRY(ar.alloc_n(&g.ovf_count, 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(g.ovf_count, 0, sizeof(int), s));
+  const size_t wsm = (size_t)GAL_WARPS * GAL_WARP_CAP * 24;
+  const size_t bsm = (size_t)GAL_BLOCK_CAP * 24;
+  AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin_block<false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+  AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin_block<true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+  const int wgrid = grid_for(nc * 32, GAL_WARPS * 32, num_sms, 16);
+  g.rowptr_c = nullptr;
+  g.col_c = nullptr;
+  g.val_c = nullptr;
+  k_galerkin_warp<false><<<wgrid, GAL_WARPS * 32, wsm, s>>>(g);
+  AMG_LAUNCH_CHECK();
+  int novf = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&novf, g.ovf_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  if (novf > 0) {
+    k_galerkin_block<false><<<std::min(novf, num_sms * 2), GAL_BLOCK_THREADS, bsm, s>>>(g, novf);
+    AMG_LAUNCH_CHECK();
+  }
+  AMG_TRY(ar.alloc_n(rp_c, nc + 1));
+  int64_t total = 0;
+  AMG_TRY(scan_exclusive_i64(ar, g.cnt, *rp_c, nc + 1, &total, s));  // cnt[nc] unused -> last
+  *nnz_c = total;
+  AMG_TRY(ar.alloc_n(col_c, total));
+  AMG_TRY(ar.alloc_n(val_c, total));
+  g.rowptr_c = *rp_c;
+  g.col_c = *col_c;
+  g.val_c = *val_c;
+  k_galerkin_warp<true><<<wgrid, GAL_WARPS * 32, wsm, s>>>(g);
+  AMG_LAUNCH_CHECK();
+  if (novf > 0) {
+    k_galerkin_block<true><<<std::min(novf, num_sms * 2), GAL_BLOCK_THREADS, bsm, s>>>(g, novf);
+    AMG_LAUNCH_CHECK();
+  }
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  ar.release(g.cnt);
+  ar.release(g.ovf_list);
+  ar.release(g.ovf_count);
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------------ coarse Cholesky
+
+__global__ void k_dense(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                        double* a) {
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) a[i * n + j] = 0.0;
+    __syncthreads();
+    for (int64_t e = rowptr[i] + threadIdx.x; e < rowptr[i + 1]; e += blockDim.x)
+      a[i * n + col[e]] = val[e];
+    __syncthreads();
+  }
+}
+
+// Right-looking Cholesky in one block; a (row-major n x n) becomes L in its
+// lower triangle.  Then Linv = L^-1 (one column per thread) and its transpose.
+__global__ void k_cholesky(int n, double* a, double* Linv, double* LinvT, int* status) {
+  __shared__ int ok;
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double piv = a[(int64_t)k * n + k];
+      ok = piv > 0.0;
+      if (ok) a[(int64_t)k * n + k] = sqrt(piv);
+    }
+    __syncthreads();
+    if (!ok) {
+      if (threadIdx.x == 0) atomicExch(status, AMG_ERR_NOT_SPD);
+      return;
+    }
+    const double lkk = a[(int64_t)k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x)
+      a[(int64_t)i * n + k] = __ddiv_rn(a[(int64_t)i * n + k], lkk);
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += blockDim.x) {
+      const int ii = (int)(idx / m), jj = (int)(idx % m);
+      if (jj <= ii) {
+        const int i = k + 1 + ii, j = k + 1 + jj;
+        a[(int64_t)i * n + j] = __dsub_rn(a[(int64_t)i * n + j],
+                                          __dmul_rn(a[(int64_t)i * n + k], a[(int64_t)j * n + k]));
+      }
+    }
+    __syncthreads();
+  }
+  // column c of L^-1 by forward substitution on e_c
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int i = 0; i < c; ++i) Linv[(int64_t)i * n + c] = 0.0;
+    for (int i = c; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k)
+        s = __dsub_rn(s, __dmul_rn(a[(int64_t)i * n + k], Linv[(int64_t)k * n + c]));
+      Linv[(int64_t)i * n + c] = __ddiv_rn(s, a[(int64_t)i * n + i]);
+    }
+  }
+  __syncthreads();
+  for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) {
+    const int i = (int)(idx / n), j = (int)(idx % n);
+    LinvT[(int64_t)j * n + i] = Linv[idx];
+  }
+}
+
+// ------------------------------------------------------------------ driver
+
+int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s) {
+  Level& L = H->L[0];
+  k_smoother_scale<<<grid_for(L.n, 256, H->num_sms, 8), 256, 0, s>>>(L.n, L.d, omega, L.s64,
+                                                                     L.s32);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+static int read_status(amg_handle* H, cudaStream_t s) {
+  int h = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&h, H->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return h;
+}
+
+int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
+  const amg_options& o = H->opt;
+  Arena& ar = H->arena;
+  const int sms = H->num_sms;
+  const bool f32 = o.precision == AMG_PREC_F32;
+  H->L.clear();
+  H->L.emplace_back();
+  H->L[0].n = A->n;
+  H->L[0].nnz = A->nnz;
+  const int stride = 1 << o.sweeps;
+  for (int l = 0;; ++l) {
+    const int64_t n = H->L[l].n;
+    const int64_t* rp = l == 0 ? A->rowptr : H->L[l].rowptr;
+    const int32_t* ci = l == 0 ? A->col : H->L[l].col;
+    const double* va = l == 0 ? A->val : H->L[l].val;
+    double* diag = nullptr;
+    AMG_TRY(ar.alloc_n(&H->L[l].d, n));
+    AMG_TRY(ar.alloc_n(&H->L[l].s64, n));
+    if (f32) AMG_TRY(ar.alloc_n(&H->L[l].s32, n));
+    AMG_TRY(ar.alloc_n(&diag, n));
+    const int g1 = grid_for(n, 256, sms, 8);
+    k_l1_diag<<<g1, 256, 0, s>>>(n, rp, ci, va, H->L[l].d, diag);
+    AMG_LAUNCH_CHECK();
+    k_smoother_scale<<<g1, 256, 0, s>>>(n, H->L[l].d, nullptr, H->L[l].s64, H->L[l].s32);
+    AMG_LAUNCH_CHECK();
+    if (n <= o.max_coarse || l + 1 >= o.max_levels) {
+      ar.release(diag);
+      break;
+    }
+    // k matching sweeps; sweep s+1 matches the Galerkin matrix of the
+    // composite map after sweep s (aggregates <= 2^k).
+    int32_t* comp = nullptr;
+    AMG_TRY(ar.alloc_n(&comp, n));
+    k_iota<<<g1, 256, 0, s>>>(n, comp);
+    AMG_LAUNCH_CHECK();
+    int64_t cn = n, nc = n;
+    const int64_t* crp = rp;
+    const int32_t* cci = ci;
+    const double* cva = va;
+    double* cdiag = diag;
+    int64_t* t_rp = nullptr;
+    int32_t* t_ci = nullptr;
+    double* t_va = nullptr;
+    for (int sw = 0; sw < o.sweeps; ++sw) {
+      int32_t *mate = nullptr, *flag = nullptr, *id = nullptr;
+      AMG_TRY(ar.alloc_n(&mate, cn));
+      AMG_TRY(match_rounds(ar, cn, crp, cci, cva, cdiag, mate, nullptr, sms, s));
+      AMG_TRY(ar.alloc_n(&flag, cn));
+      AMG_TRY(ar.alloc_n(&id, cn));
+      const int gc = grid_for(cn, 256, sms, 8);
+      k_leader_flags<<<gc, 256, 0, s>>>(cn, mate, flag);
+      AMG_LAUNCH_CHECK();
+      AMG_TRY(scan_exclusive_i32(ar, flag, id, cn, &nc, s));
+      k_assign_compose<<<g1, 256, 0, s>>>(n, cn, mate, id, comp);
+      AMG_LAUNCH_CHECK();
+      AMG_CUDA_TRY(cudaStreamSynchronize(s));
+      ar.release(mate);
+      ar.release(flag);
+      ar.release(id);
+      if (sw + 1 < o.sweeps) {
+        const int st = 1 << (sw + 1);
+        int32_t* mem = nullptr;
+        AMG_TRY(ar.alloc_n(&mem, nc * st));
+        AMG_TRY(build_members(ar, n, comp, nc, st, mem, H->dev_status, sms, s));
+        int64_t* n_rp = nullptr;
+        int32_t* n_ci = nullptr;
+        double* n_va = nullptr;
+        int64_t n_nnz = 0;
+        AMG_TRY(galerkin(ar, n, rp, ci, va, comp, mem, st, nc, &n_rp, &n_ci, &n_va, &n_nnz,
+                         H->dev_status, sms, s));
+        ar.release(mem);
+        ar.release(t_rp);
+        ar.release(t_ci);
+        ar.release(t_va);
+        t_rp = n_rp;
+        t_ci = n_ci;
+        t_va = n_va;
+        if (cdiag != diag) ar.release(cdiag);
+        AMG_TRY(ar.alloc_n(&cdiag, nc));
+        k_l1_diag<<<grid_for(nc, 256, sms, 8), 256, 0, s>>>(nc, t_rp, t_ci, t_va, nullptr, cdiag);
+        AMG_LAUNCH_CHECK();
+        crp = t_rp;
+        cci = t_ci;
+        cva = t_va;
+        cn = nc;
+      }
+    }
+    ar.release(t_rp);
+    ar.release(t_ci);
+    ar.release(t_va);
+    if (cdiag != diag) ar.release(cdiag);
+    ar.release(diag);
+    int st = read_status(H, s);
+    if (st < 0) return st;
+    if ((double)nc > o.stall_ratio * (double)n) {
+      ar.release(comp);
+      break;
+    }
+    Level& L = H->L[l];
+    L.agg = comp;
+    L.nc = nc;
+    L.stride = stride;
+    AMG_TRY(ar.alloc_n(&L.members, nc * stride));
+    AMG_TRY(build_members(ar, n, L.agg, nc, stride, L.members, H->dev_status, sms, s));
+    Level next;
+    next.n = nc;
+    AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, stride, nc, &next.rowptr, &next.col,
+                     &next.val, &next.nnz, H->dev_status, sms, s));
+    st = read_status(H, s);
+    if (st < 0) return st;
+    H->L.push_back(next);
+  }
+  // coarsest level: dense Cholesky and its inverse factor
+  Level& Lc = H->L.back();
+  if (Lc.n > o.max_dense) return AMG_ERR_UNSUPPORTED;
+  H->nco = Lc.n;
+  {
+    const int64_t m = Lc.n;
+    const int64_t* rp = H->L.size() == 1 ? A->rowptr : Lc.rowptr;
+    const int32_t* ci = H->L.size() == 1 ? A->col : Lc.col;
+    const double* va = H->L.size() == 1 ? A->val : Lc.val;
+    double* dense = nullptr;
+    AMG_TRY(ar.alloc_n(&dense, m * m));
+    AMG_TRY(ar.alloc_n(&H->Linv, m * m));
+    AMG_TRY(ar.alloc_n(&H->LinvT, m * m));
+    k_dense<<<(unsigned)std::min<int64_t>(m, 1024), 256, 0, s>>>(m, rp, ci, va, dense);
+    AMG_LAUNCH_CHECK();
+    k_cholesky<<<1, 1024, 0, s>>>((int)m, dense, H->Linv, H->LinvT, H->dev_status);
+    AMG_LAUNCH_CHECK();
+    int st = read_status(H, s);
+    ar.release(dense);
+    if (st < 0) return st;
+  }
+  // sliced-ELL copies and V-cycle work vectors
+  const size_t vb = f32 ? sizeof(float) : sizeof(double);
+  for (size_t l = 0; l < H->L.size(); ++l) {
+    Level& L = H->L[l];
+    const int64_t* rp = l == 0 ? A->rowptr : L.rowptr;
+    const int32_t* ci = l == 0 ? A->col : L.col;
+    const double* va = l == 0 ? A->val : L.val;
+    int tpr = o.threads_per_row > 0 ? o.threads_per_row : 1;
+    if (o.slice_height > 0) tpr = 32 / o.slice_height;
+    AMG_TRY(sell_from_csr(ar, L.n, rp, ci, va, 32 / tpr, tpr, L.A, s));
+    L.vstore = VAL_F64;
+    if (f32) {
+      L.vstore = (o.bf16_from_level > 0 && (int)l >= o.bf16_from_level) ? VAL_BF16 : VAL_F32;
+      AMG_TRY(sell_make_copies(ar, L.A, L.vstore, s));
+    }
+    AMG_TRY(ar.alloc((void**)&L.b, vb * (size_t)L.n));
+    AMG_TRY(ar.alloc((void**)&L.x, vb * (size_t)L.n));
+    AMG_TRY(ar.alloc((void**)&L.r, vb * (size_t)L.n));
+  }
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+}  // namespace amg

@@ -98,7 +98,7 @@ def _rounds_locally_dominant(orc, A):
     E = _edges(orc, A)
     adj = {i: [] for i in range(n)}
     for (i, j), c in E.items():
-        key = (c, orc.mix64(i * n + j), -i, -j)
+        key = (c, -i, -j)
         adj[i].append((key, j))
         adj[j].append((key, i))
     mate = [-1] * n
