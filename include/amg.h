@@ -207,6 +207,27 @@ int amg_level_export(const amg_handle* H, int level, int64_t* rowptr, int32_t* c
  */
 int amg_pairwise_match(const amg_csr* A, int32_t* mate, int* rounds, amg_stream_t stream);
 
+/* Largest matrix (rows) that amg_pairwise_match_noalloc accepts. */
+#define AMG_NOALLOC_MAX_ROWS 262144
+
+/*
+ * amg_pairwise_match without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc, such as
+ * code running while a CUDA graph is being captured, applications whose
+ * device memory is owned by a pool or framework that forbids outside
+ * allocations, and real-time loops that must not allocate after start-up.
+ * Same arguments and result as amg_pairwise_match (bit-identical mate and
+ * rounds).  Its scratch is one fixed device array of 24 bytes per row for
+ * AMG_NOALLOC_MAX_ROWS rows (6 MiB), held by every GPU that loads the library
+ * until the process exits; larger matrices return AMG_ERR_UNSUPPORTED.  The
+ * first call on a device looks up that array's address (a one-time set-up);
+ * make that first call before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (other streams or host threads)
+ * race and must be serialised by the caller.  Synchronous.
+ */
+int amg_pairwise_match_noalloc(const amg_csr* A, int32_t* mate, int* rounds,
+                               amg_stream_t stream);
+
 /* ----------------------------------------------------------- test hooks */
 
 /*

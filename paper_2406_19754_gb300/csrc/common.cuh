@@ -245,6 +245,24 @@ int sell_make_copies(Arena& ar, Sell& A, int vstore, cudaStream_t s);
 int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, double* y,
                 int num_sms, cudaStream_t s);
 
+// Matching kernels (setup.cu), also launched by the allocation-free variant
+__global__ void k_l1_diag(int64_t n, const int64_t* rowptr, const int32_t* col,
+                          const double* val, double* d, double* diag);
+__global__ void k_iota(int64_t n, int32_t* a);
+__global__ void k_match_cand(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
+                             const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ diag,
+                             const int32_t* __restrict__ mate, int32_t* __restrict__ cand,
+                             int32_t* __restrict__ flag, int* rounds);
+__global__ void k_match_commit(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
+                               const int32_t* __restrict__ cand, int32_t* mate);
+__global__ void k_match_expand(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
+                               const int64_t* __restrict__ rowptr,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ mate,
+                               int32_t* __restrict__ flag, int32_t* __restrict__ wl_next,
+                               int* __restrict__ nwl_next);
+__global__ void k_match_final(int64_t n, int32_t* mate);
+
 // Setup (setup.cu)
 int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s);
 int match_pairwise(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
