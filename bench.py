@@ -254,6 +254,7 @@ def run_ours(a):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     iters = []
     for _ in range(a.steps):
@@ -262,6 +263,7 @@ def run_ours(a):
         iters.append(info["iterations"])
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     elapsed = ev0.elapsed_time(ev1) / 1e3
     if ws > 1:

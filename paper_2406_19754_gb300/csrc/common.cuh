@@ -85,6 +85,14 @@ struct Level {
   int32_t* col = nullptr;
   double* val = nullptr;
   Sell A;
+  // V-cycle operators (levels above the coarsest):
+  //   Ah = A S  (a_ij s_j; same slices and columns as A, own values)
+  //   AP = A P  (row i, column J: sum of a_ij over agg(j) = J; own slices)
+  double* ah64 = nullptr;
+  float* ah32 = nullptr;
+  __nv_bfloat16* ah16 = nullptr;
+  Sell AP;
+  int64_t ap_nnz = 0;
   int vstore = VAL_F64;
   double* d = nullptr;     // l1 row sums
   double* s64 = nullptr;   // smoother scale s_i = omega_i * (1 / d_i)
@@ -239,7 +247,7 @@ int scan_exclusive_i64(Arena& ar, const int64_t* in, int64_t* out, int64_t n, in
                        cudaStream_t s);
 
 // SELL conversion (sell.cu)
-int sell_from_csr(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* col,
                   const double* val, int C, int tpr, Sell& out, cudaStream_t s);
 int sell_make_copies(Arena& ar, Sell& A, int vstore, cudaStream_t s);
 int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, double* y,

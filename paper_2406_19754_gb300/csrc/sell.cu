@@ -20,9 +20,9 @@ __global__ void k_sell_widths(int64_t n, int64_t nslices, int C, const int64_t* 
 }
 
 // One thread per (padded) row: copy its entries into the slice, pad the rest.
-__global__ void k_sell_fill(int64_t n, int64_t nslices, int C, const int64_t* rowptr,
-                            const int32_t* col, const double* val, const int64_t* sliceptr,
-                            int32_t* ocol, double* oval) {
+__global__ void k_sell_fill(int64_t n, int64_t ncols, int64_t nslices, int C,
+                            const int64_t* rowptr, const int32_t* col, const double* val,
+                            const int64_t* sliceptr, int32_t* ocol, double* oval) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nslices * C) return;
   const int64_t s = i / C;
@@ -34,7 +34,8 @@ __global__ void k_sell_fill(int64_t n, int64_t nslices, int C, const int64_t* ro
     rb = rowptr[i];
     len = rowptr[i + 1] - rowptr[i];
   }
-  const int32_t pad_col = (int32_t)(i < n ? i : n - 1);
+  // padding reads a valid column: the row itself when it exists in x
+  const int32_t pad_col = (int32_t)(i < ncols ? i : ncols - 1);
   for (int k = 0; k < w; ++k) {
     int64_t dst = beg + (int64_t)k * C + r;
     if (k < len) {
@@ -59,8 +60,9 @@ __global__ void k_to_bf16(int64_t n, const double* in, __nv_bfloat16* out) {
     out[i] = __float2bfloat16_rn((float)in[i]);
 }
 
-int sell_from_csr(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* col,
                   const double* val, int C, int tpr, Sell& out, cudaStream_t s) {
+  if (n <= 0 || ncols <= 0) return AMG_ERR_ARG;
   if (C * tpr != 32) return AMG_ERR_ARG;
   out.n = n;
   out.C = C;
@@ -81,8 +83,9 @@ int sell_from_csr(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* co
   AMG_TRY(ar.alloc_n(&out.col, total));
   AMG_TRY(ar.alloc_n(&out.v64, total));
   int64_t rows = out.nslices * C;
-  k_sell_fill<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(n, out.nslices, C, rowptr, col, val,
-                                                             out.sliceptr, out.col, out.v64);
+  k_sell_fill<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(n, ncols, out.nslices, C, rowptr,
+                                                             col, val, out.sliceptr, out.col,
+                                                             out.v64);
   AMG_LAUNCH_CHECK();
   AMG_CUDA_TRY(cudaStreamSynchronize(s));  // `total` lives on this stack frame
   return AMG_OK;

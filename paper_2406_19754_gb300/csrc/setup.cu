@@ -154,8 +154,6 @@ __global__ void k_match_final(int64_t n, int32_t* mate) {
     if (mate[i] < 0) mate[i] = -1;
 }
 
-__global__ void k_iota(int64_t n, int32_t* a);
-
 static int match_rounds(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
                         const double* val, const double* diag, int32_t* mate, int* rounds_out,
                         int num_sms, cudaStream_t s) {
@@ -620,6 +618,101 @@ __global__ void k_cholesky(int n, double* a, double* Linv, double* LinvT, int* s
   }
 }
 
+// ------------------------------------------------------------------ V-cycle operators
+// AP = A P: row i holds every aggregate J among agg(col(i, :)) once, in order
+// of first appearance, with the sum of its entries taken in column order.
+
+__device__ __forceinline__ bool seen_before(const int64_t* rowptr_i, const int32_t* col,
+                                            const int32_t* agg, int64_t e, int32_t J) {
+  for (int64_t f = *rowptr_i; f < e; ++f)
+    if (agg[col[f]] == J) return true;
+  return false;
+}
+
+__global__ void k_ap_count(int64_t n, const int64_t* rowptr, const int32_t* col,
+                           const int32_t* agg, int64_t* cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = 0;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (!seen_before(rowptr + i, col, agg, e, agg[col[e]])) ++c;
+    cnt[i] = c;
+  }
+}
+
+__global__ void k_ap_fill(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                          const int32_t* agg, const int64_t* rp_ap, int32_t* col_ap,
+                          double* val_ap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t pos = rp_ap[i];
+    const int64_t end = rowptr[i + 1];
+    for (int64_t e = rowptr[i]; e < end; ++e) {
+      const int32_t J = agg[col[e]];
+      if (seen_before(rowptr + i, col, agg, e, J)) continue;
+      double s = val[e];
+      for (int64_t f = e + 1; f < end; ++f)
+        if (agg[col[f]] == J) s = __dadd_rn(s, val[f]);
+      col_ap[pos] = J;
+      val_ap[pos] = s;
+      ++pos;
+    }
+  }
+}
+
+// Ah values: a_ij * s_j on A's sliced-ELL slots (padding stays 0).
+__global__ void k_scale_cols(int64_t m, const int32_t* col, const double* val, const double* s,
+                             double* out64, float* out32, __nv_bfloat16* out16) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = __dmul_rn(val[e], s[col[e]]);
+    out64[e] = v;
+    if (out32) out32[e] = (float)v;
+    if (out16) out16[e] = __float2bfloat16_rn((float)v);
+  }
+}
+
+static int build_ah(Arena& ar, Level& L, int num_sms, cudaStream_t s) {
+  const int64_t m = L.A.nnz_pad;
+  if (!L.ah64) AMG_TRY(ar.alloc_n(&L.ah64, m));
+  if (L.vstore == VAL_F32 && !L.ah32) AMG_TRY(ar.alloc_n(&L.ah32, m));
+  if (L.vstore == VAL_BF16 && !L.ah16) AMG_TRY(ar.alloc_n(&L.ah16, m));
+  k_scale_cols<<<grid_for(m, 256, num_sms, 8), 256, 0, s>>>(m, L.A.col, L.A.v64, L.s64, L.ah64,
+                                                            L.ah32, L.ah16);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+static int build_ap(Arena& ar, Level& L, const int64_t* rp, const int32_t* ci, const double* va,
+                    int num_sms, cudaStream_t s) {
+  const int64_t n = L.n;
+  int64_t* cnt = nullptr;
+  int64_t* rp_ap = nullptr;
+  AMG_TRY(ar.alloc_n(&cnt, n + 1));
+  AMG_TRY(ar.alloc_n(&rp_ap, n + 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (n + 1), s));
+  const int g = grid_for(n, 256, num_sms, 8);
+  k_ap_count<<<g, 256, 0, s>>>(n, rp, ci, L.agg, cnt);
+  AMG_LAUNCH_CHECK();
+  int64_t total = 0;
+  AMG_TRY(scan_exclusive_i64(ar, cnt, rp_ap, n + 1, &total, s));
+  int32_t* ci_ap = nullptr;
+  double* va_ap = nullptr;
+  AMG_TRY(ar.alloc_n(&ci_ap, total));
+  AMG_TRY(ar.alloc_n(&va_ap, total));
+  k_ap_fill<<<g, 256, 0, s>>>(n, rp, ci, va, L.agg, rp_ap, ci_ap, va_ap);
+  AMG_LAUNCH_CHECK();
+  L.ap_nnz = total;
+  AMG_TRY(sell_from_csr(ar, n, L.nc, rp_ap, ci_ap, va_ap, L.A.C, L.A.tpr, L.AP, s));
+  if (L.vstore != VAL_F64) AMG_TRY(sell_make_copies(ar, L.AP, L.vstore, s));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  ar.release(cnt);
+  ar.release(rp_ap);
+  ar.release(ci_ap);
+  ar.release(va_ap);
+  return AMG_OK;
+}
+
 // ------------------------------------------------------------------ driver
 
 int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s) {
@@ -627,6 +720,7 @@ int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s) {
   k_smoother_scale<<<grid_for(L.n, 256, H->num_sms, 8), 256, 0, s>>>(L.n, L.d, omega, L.s64,
                                                                      L.s32);
   AMG_LAUNCH_CHECK();
+  if (L.ah64) AMG_TRY(build_ah(H->arena, L, H->num_sms, s));
   return AMG_OK;
 }
 
@@ -779,11 +873,13 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     const double* va = l == 0 ? A->val : L.val;
     int tpr = o.threads_per_row > 0 ? o.threads_per_row : 1;
     if (o.slice_height > 0) tpr = 32 / o.slice_height;
-    AMG_TRY(sell_from_csr(ar, L.n, rp, ci, va, 32 / tpr, tpr, L.A, s));
+    AMG_TRY(sell_from_csr(ar, L.n, L.n, rp, ci, va, 32 / tpr, tpr, L.A, s));
     L.vstore = VAL_F64;
-    if (f32) {
+    if (f32)
       L.vstore = (o.bf16_from_level > 0 && (int)l >= o.bf16_from_level) ? VAL_BF16 : VAL_F32;
-      AMG_TRY(sell_make_copies(ar, L.A, L.vstore, s));
+    if (l + 1 < H->L.size()) {  // smoothing operators of a level with a coarser one
+      AMG_TRY(build_ah(ar, L, sms, s));
+      AMG_TRY(build_ap(ar, L, rp, ci, va, sms, s));
     }
     AMG_TRY(ar.alloc((void**)&L.b, vb * (size_t)L.n));
     AMG_TRY(ar.alloc((void**)&L.x, vb * (size_t)L.n));

@@ -4,13 +4,16 @@
 //   x += S (b - A x),       S = diag(s), s_i = omega_i / (l1 row sum)_i,
 //
 // where P is the 0/1 aggregate map, and the coarsest level is solved by its
-// dense Cholesky factor.  Three streaming kernels per level:
-//   k_pre      r_i = b_i - sum_j a_ij (s_j b_j)          (pre-smooth fused
-//              with the residual; x = S b is recomputed, never stored)
+// dense Cholesky factor.  Each level streams two operators built at setup,
+//   Ah = A S   (a_ij s_j)  and  AP = A P  (row i, column J: sum of a_ij over
+//   agg(j) = J),
+// so that every matrix entry needs exactly one gathered vector element:
+//   k_pre      r = b - Ah b                 (= b - A (S b): pre-smooth + residual)
 //   k_restrict b_c[I] = sum of r_i over the members of I, ascending
-//   k_post     y_j = s_j b_j + x_c[agg_j];  x_i = y_i + s_i (b_i - sum_j a_ij y_j)
-//              (prolongation fused with the post-smoother; y recomputed)
-// The level-0 k_post can also reduce (r, z) and (z, q) for the PCG step.
+//   k_post     z = S b + P x_c + S (r - AP x_c)
+// The last line is y + S (b - A y) for y = S b + P x_c, because
+// b - A y = (b - A S b) - A P x_c.  The level-0 k_post can also reduce (r, z)
+// and (z, q) for the PCG step.
 #include <algorithm>
 
 #include "sellk.cuh"
@@ -21,16 +24,15 @@ namespace amg {
 
 template <int TPR, typename V, typename T, typename BT>
 __global__ void __launch_bounds__(SELL_BLOCK)
-    k_pre(SellView<V> A, const BT* __restrict__ b, const T* __restrict__ s, T* __restrict__ r) {
+    k_pre(SellView<V> Ah, const BT* __restrict__ b, T* __restrict__ r) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
        sl += nw) {
-    const T acc = sell_row<TPR, T>(A, sl, ln, [&](int j) {
-      return __ldg(s + j) * to_f(__ldg(b + j), T(0));
-    });
+    const T acc =
+        sell_row<TPR, T>(Ah, sl, ln, [&](int j) { return to_f(__ldg(b + j), T(0)); });
     const int64_t i = sl * Lanes<TPR>::C + ln.r;
-    if (ln.t == 0 && i < A.n) r[i] = to_f(b[i], T(0)) - acc;
+    if (ln.t == 0 && i < Ah.n) r[i] = to_f(b[i], T(0)) - acc;
   }
 }
 
@@ -68,25 +70,23 @@ struct VcycleDotEpi {
 
 template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT>
 __global__ void __launch_bounds__(SELL_BLOCK)
-    k_post(SellView<V> A, const BT* __restrict__ b, const T* __restrict__ s,
-           const int32_t* __restrict__ agg, const T* __restrict__ xc, XT* __restrict__ x,
-           const double* __restrict__ q, Reduce red, PcgScalars* sc) {
+    k_post(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,
+           const T* __restrict__ r, const int32_t* __restrict__ agg, const T* __restrict__ xc,
+           XT* __restrict__ x, const double* __restrict__ q, Reduce red, PcgScalars* sc) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double d[NDOT > 0 ? NDOT : 1];
 #pragma unroll
   for (int k = 0; k < (NDOT > 0 ? NDOT : 1); ++k) d[k] = 0.0;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
        sl += nw) {
-    const T acc = sell_row<TPR, T>(A, sl, ln, [&](int j) {
-      return __ldg(s + j) * to_f(__ldg(b + j), T(0)) + __ldg(xc + __ldg(agg + j));
-    });
+    const T acc = sell_row<TPR, T>(AP, sl, ln, [&](int J) { return __ldg(xc + J); });
     const int64_t i = sl * Lanes<TPR>::C + ln.r;
-    if (ln.t == 0 && i < A.n) {
+    if (ln.t == 0 && i < AP.n) {
       const T bi = to_f(b[i], T(0));
       const T si = s[i];
       const T yi = si * bi + xc[agg[i]];
-      const XT zi = to_f(yi + si * (bi - acc), XT(0));
+      const XT zi = to_f(yi + si * (r[i] - acc), XT(0));
       x[i] = zi;
       if (NDOT > 0) d[0] += (double)b[i] * (double)zi;
       if (NDOT > 1) d[NDOT > 1 ? 1 : 0] += (double)zi * q[i];
@@ -149,24 +149,23 @@ static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s)
 }
 
 template <typename V, typename T, typename BT>
-static int launch_pre(const amg_handle* H, const Level& L, const V* val, const BT* b, T* r,
+static int launch_pre(const amg_handle* H, const Level& L, const V* ah, const BT* b, T* r,
                       cudaStream_t s) {
   const int grid = sell_grid(L.A.nslices, H->num_sms);
-  const SellView<V> v = view<V>(L.A, val);
-  const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
-  AMG_DISPATCH_TPR(L.A.tpr, (k_pre<TPR, V, T, BT><<<grid, SELL_BLOCK, 0, s>>>(v, b, sc, r)));
+  const SellView<V> v = view<V>(L.A, ah);
+  AMG_DISPATCH_TPR(L.A.tpr, (k_pre<TPR, V, T, BT><<<grid, SELL_BLOCK, 0, s>>>(v, b, r)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
 
 template <typename V, typename T, typename BT, typename XT, int NDOT>
-static int launch_post(const amg_handle* H, const Level& L, const V* val, const BT* b,
+static int launch_post(const amg_handle* H, const Level& L, const V* ap, const BT* b,
                        const T* xc, XT* x, const double* q, cudaStream_t s) {
-  const int grid = sell_grid(L.A.nslices, H->num_sms);
-  const SellView<V> v = view<V>(L.A, val);
+  const int grid = sell_grid(L.AP.nslices, H->num_sms);
+  const SellView<V> v = view<V>(L.AP, ap);
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
-  AMG_DISPATCH_TPR(L.A.tpr, (k_post<TPR, V, T, BT, XT, NDOT><<<grid, SELL_BLOCK, 0, s>>>(
-                                v, b, sc, L.agg, xc, x, q, H->red, H->sc)));
+  AMG_DISPATCH_TPR(L.AP.tpr, (k_post<TPR, V, T, BT, XT, NDOT><<<grid, SELL_BLOCK, 0, s>>>(
+                                 v, b, sc, (const T*)L.r, L.agg, xc, x, q, H->red, H->sc)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -182,19 +181,19 @@ static int launch_restrict(const amg_handle* H, const Level& L, const T* r, T* b
 
 template <typename BT>
 static int pre_f32(const amg_handle* H, const Level& L, const BT* b, float* r, cudaStream_t s) {
-  if (L.vstore == VAL_BF16) return launch_pre<__nv_bfloat16, float, BT>(H, L, L.A.v16, b, r, s);
-  return launch_pre<float, float, BT>(H, L, L.A.v32, b, r, s);
+  if (L.vstore == VAL_BF16) return launch_pre<__nv_bfloat16, float, BT>(H, L, L.ah16, b, r, s);
+  return launch_pre<float, float, BT>(H, L, L.ah32, b, r, s);
 }
 
 template <typename T, typename BT, typename XT, int NDOT>
 static int post_any(const amg_handle* H, const Level& L, const BT* b, const T* xc, XT* x,
                     const double* q, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
-    return launch_post<double, T, BT, XT, NDOT>(H, L, L.A.v64, b, xc, x, q, s);
+    return launch_post<double, T, BT, XT, NDOT>(H, L, L.AP.v64, b, xc, x, q, s);
   } else {
     if (L.vstore == VAL_BF16)
-      return launch_post<__nv_bfloat16, T, BT, XT, NDOT>(H, L, L.A.v16, b, xc, x, q, s);
-    return launch_post<float, T, BT, XT, NDOT>(H, L, L.A.v32, b, xc, x, q, s);
+      return launch_post<__nv_bfloat16, T, BT, XT, NDOT>(H, L, L.AP.v16, b, xc, x, q, s);
+    return launch_post<float, T, BT, XT, NDOT>(H, L, L.AP.v32, b, xc, x, q, s);
   }
 }
 
@@ -237,17 +236,19 @@ struct Prof {
   }
 };
 
-// Algorithmic bytes of each V-cycle kernel on one level: matrix entries
-// (value + int32 column) once, every vector once.  vb = bytes of a V-cycle
-// vector entry, eb = bytes of the level's input/output entries.
+// Algorithmic bytes of each V-cycle kernel on one level: operator entries
+// (value + int32 column) once, every vector once.  mb = bytes of an operator
+// entry, vb = bytes of a V-cycle vector element, ib/ob = bytes of the level's
+// input b / output z elements (FP64 on level 0).
 static double bytes_pre(const Level& L, double mb, double vb, double ib) {
-  return (double)L.nnz * mb + (double)L.n * (ib + vb + vb);  // A, b, s, r
+  return (double)L.nnz * mb + (double)L.n * (ib + vb);  // Ah, b, r
 }
 static double bytes_restrict(const Level& L, double vb) {
   return (double)L.n * (vb + 4.0) + (double)L.nc * vb;  // r, members, b_c
 }
 static double bytes_post(const Level& L, double mb, double vb, double ib, double ob) {
-  return (double)L.nnz * mb + (double)L.n * (ib + vb + 4.0 + ob) + (double)L.nc * vb;
+  // AP, b, s, r, agg, z, x_c
+  return (double)L.ap_nnz * mb + (double)L.n * (ib + vb + vb + 4.0 + ob) + (double)L.nc * vb;
 }
 
 #define PROF_BEGIN(lvl, kind, bytes) \
@@ -285,7 +286,7 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
     PROF_BEGIN(l, 0, bytes_pre(L, mbytes(L), vb, l == 0 ? 8.0 : vb));
     if constexpr (sizeof(T) == 8) {
       const double* b = l == 0 ? r0 : (const double*)L.b;
-      AMG_TRY((launch_pre<double, double, double>(H, L, L.A.v64, b, r, s)));
+      AMG_TRY((launch_pre<double, double, double>(H, L, L.ah64, b, r, s)));
     } else {
       if (l == 0)
         AMG_TRY(pre_f32<double>(H, L, r0, r, s));
