@@ -35,6 +35,12 @@ METRIC = ("PCG-AMG seconds to 1e-8 rel. residual (256³ Poisson, 1 GB300); "
           "V-cycle HBM GB/s")
 SAMPLE_SIDE = 64     # CPU-oracle sample grid
 RHS_SEED = 2
+# other workloads (opt-in with --workload): 256^3 diffusion with k = exp(g),
+# g a Gaussian field (sigma 2, correlation length 8 cells); 48 diffusion
+# systems with sides U{24..96} and sigma U[0.5, 2]
+FIELD_ELL = 8.0
+DIFF_SIGMA, DIFF_FIELD_SEED, DIFF_RHS_SEED = 2.0, 3, 4
+BATCH_SYSTEMS, BATCH_SEED0 = 48, 200
 
 
 def _args():
@@ -46,6 +52,8 @@ def _args():
     ap.add_argument("--side", type=int, default=256)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
+    ap.add_argument("--workload", choices=["poisson", "diffusion", "batch"], default="poisson")
+    ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -224,20 +232,57 @@ def run_ours(a):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     side = a.side
-    n = side ** 3
-    A = poisson3d(side)
-    nnz = int(A[0][-1])
-    b_host = uniform01(RHS_SEED, n)
-    Ad = amg.csr_to_device(A, dev)
-    del A
+    batch = a.workload == "batch"
+    if batch:
+        from synthetic import batch_specs, diffusion_problem
+
+        specs = batch_specs(BATCH_SYSTEMS, BATCH_SEED0)
+        systems = [diffusion_problem(sd, sg, FIELD_ELL, seed) for sd, sg, seed in specs]
+        n = sum(len(S[0]) - 1 for S in systems)
+        nnz = sum(int(S[0][-1]) for S in systems)
+        b_host = uniform01(RHS_SEED, n)
+        Ad = [amg.csr_to_device(S, dev) for S in systems]
+        workload = ("batch%d_diffusion_sides%d-%d_pcg_amg_v11_tol%g"
+                    % (BATCH_SYSTEMS, min(s[0] for s in specs), max(s[0] for s in specs), a.tol))
+        del systems
+    else:
+        n = side ** 3
+        if a.workload == "diffusion":
+            from synthetic import diffusion_problem
+
+            A = diffusion_problem(side, DIFF_SIGMA, FIELD_ELL, DIFF_FIELD_SEED)
+            b_host = uniform01(DIFF_RHS_SEED, n)
+            workload = "diffusion3d_%d^3_sigma%g_ell%g_pcg_amg_v11_tol%g" % (
+                side, DIFF_SIGMA, FIELD_ELL, a.tol)
+        else:
+            A = poisson3d(side)
+            b_host = uniform01(RHS_SEED, n)
+            workload = "poisson3d_%d^3_pcg_amg_v11_tol%g" % (side, a.tol)
+        nnz = int(A[0][-1])
+        Ad = amg.csr_to_device(A, dev)
+        del A
     b = torch.as_tensor(b_host, device=dev)
     x = torch.zeros_like(b)
+
+    def make_hierarchy():
+        if batch:
+            return amg.BatchHierarchy(Ad, precision=a.precision, autotune=int(a.autotune))
+        return amg.Hierarchy(*Ad, precision=a.precision, autotune=int(a.autotune))
+
+    def solve(bv, xv):
+        if batch:
+            _, stats = H.pcg(bv, xv, tol=a.tol)
+            worst = min(s["status"] for s in stats) if any(s["status"] < 0 for s in stats) \
+                else max(s["status"] for s in stats)
+            return dict(iterations=max(s["iterations"] for s in stats), status=worst,
+                        per_system=[s["iterations"] for s in stats])
+        return H.pcg(bv, xv, tol=a.tol)[1]
 
     # warm the module on a small problem, then time the setup of the real one
     amg.Hierarchy(*amg.csr_to_device(poisson3d(16), dev), precision=a.precision).close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    H = amg.Hierarchy(*Ad, precision=a.precision)
+    H = make_hierarchy()
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     nl = H.levels
@@ -246,7 +291,7 @@ def run_ours(a):
 
     for _ in range(a.warmup):
         x.zero_()
-        _, info = H.pcg(b, x, tol=a.tol)
+        info = solve(b, x)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(dev.index)
@@ -259,7 +304,7 @@ def run_ours(a):
     iters = []
     for _ in range(a.steps):
         x.zero_()
-        _, info = H.pcg(b, x, tol=a.tol)
+        info = solve(b, x)
         iters.append(info["iterations"])
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -274,9 +319,12 @@ def run_ours(a):
     it = iters[-1]
     assert info["status"] == 0, info
 
-    # our kernel launches per solve (see pcg.cu / vcycle.cu)
+    # our kernel launches per solve (see pcg.cu, batch.cu, vcycle.cu)
     V = 2 if nl == 1 else 3 * (nl - 1) + 1
-    launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1) * a.steps
+    if batch:
+        launches = (2 + (V + 5) + (it - 1) * (V + 6) + 2) * a.steps
+    else:
+        launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1) * a.steps
 
     # per-kernel V-cycle timing (CUDA events on the launching stream)
     agg = {}
@@ -295,11 +343,11 @@ def run_ours(a):
     (dl, dk), (dms, dbytes) = max(agg.items(), key=lambda kv: kv[1][0])
     peak, peak_src = _peaks()
     dom_name = "vcycle_%s_level%d" % (dk, dl)
-    workload = "poisson%d_%s" % (side, a.precision)
+    wl_key = "%s%d_%s" % (a.workload, side, a.precision)
     roof = {"bound": "hbm", "kernel": dom_name, "achieved": dbytes / (dms * 1e-3) / 1e9,
             "peak": peak, "unit": "GB/s", "frac": dbytes / (dms * 1e-3) / 1e9 / peak,
             "peak_source": peak_src,
-            "traffic": _traffic_from_profiles(dom_name, workload),
+            "traffic": _traffic_from_profiles(dom_name, wl_key),
             "bytes_per_launch": dbytes, "ms_per_launch": dms}
 
     # SpMV (PCG operator) timed alone
@@ -326,7 +374,7 @@ def run_ours(a):
         for _ in range(a.steps):
             bd.copy_(bh, non_blocking=True)
             x.zero_()
-            H.pcg(bd, x, tol=a.tol)
+            solve(bd, x)
             xh.copy_(x, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -336,7 +384,7 @@ def run_ours(a):
         assert np.allclose(xh[:8].numpy(), x[:8].cpu().numpy())
 
     cpu = None
-    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload == "poisson":
         times, its_s = oracle_sample(min_seconds=10.0, tol=a.tol)
         per = sum(times) / len(times)
         val, it_full = scale_to_full(per, its_s, side)
@@ -353,11 +401,11 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "f64"
             else "f64 outer / f32 V-cycle", "data": "synthetic",
-            "config": {"workload": "poisson3d_%d^3_pcg_amg_v11_tol%g" % (side, a.tol),
-                       "n": n, "nnz": nnz, "levels": nl,
+            "config": {"workload": workload, "n": n, "nnz": nnz, "levels": nl,
                        "level_rows": [lv[0] for lv in levels],
                        "operator_complexity": round(oc, 4), "iterations": it,
-                       "precision": a.precision, "rhs": "uniform[0,1) seed %d" % RHS_SEED,
+                       "precision": a.precision, "autotune": bool(a.autotune),
+                       "rhs": "uniform[0,1) seed %d" % RHS_SEED,
                        "l2": "inputs larger than L2 (matrix %.2f GB)" % (12.0 * nnz / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "setup_s": setup_s, "iterations": it, "vcycle_gbs": vcycle_gbs,
@@ -371,6 +419,12 @@ def run_ours(a):
         }
         if ws > 1:
             line["solves_per_s"] = ws * a.steps / elapsed
+        if batch:
+            line["systems_per_s"] = ws * BATCH_SYSTEMS * a.steps / elapsed
+            line["config"]["per_system_iterations"] = info["per_system"]
+            line["config"]["rhs"] = "uniform[0,1) seed %d, concatenated" % RHS_SEED
+        if a.workload == "diffusion":
+            line["config"]["rhs"] = "uniform[0,1) seed %d" % DIFF_RHS_SEED
         print(json.dumps(line), flush=True)
     H.close()
     if ws > 1:

@@ -161,6 +161,62 @@ int amg_spmv(const amg_handle* H, int level, double alpha, const double* x, doub
 int pcg_solve(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
               amg_stream_t stream);
 
+/* ----------------------------------------------------------- multiple right-hand sides */
+
+/*
+ * Z = B R for nrhs right-hand sides at once (Eq. amg applied column by
+ * column).  R, Z: device float64, row-major n0 x nrhs (row i's nrhs values
+ * contiguous), distinct.  1 <= nrhs <= 64.  Every column equals what
+ * amg_vcycle_apply returns for it, bit for bit; each matrix entry is read
+ * once for all columns.  The first call for a given nrhs allocates the
+ * handle's multi-RHS workspace.  Needs a hierarchy of at least two levels
+ * built by amg_setup (AMG_ERR_UNSUPPORTED otherwise).  Asynchronous.
+ */
+int amg_vcycle_apply_multi(amg_handle* H, int nrhs, const double* R, double* Z,
+                           amg_stream_t stream);
+
+/*
+ * nrhs independent PCG solves of A X = B sharing every matrix read (blocked
+ * SpMM; Sec. 3's method per column).  B, X: device float64 row-major
+ * n0 x nrhs; X holds the initial guesses and receives the solutions.  Each
+ * column has its own alpha, beta and stopping test; converged columns are
+ * frozen.  st: host array of nrhs stats or NULL.  o->res_history and
+ * o->x_history must be NULL.  Synchronous.  Returns the worst column status.
+ */
+int pcg_solve_multi(amg_handle* H, int nrhs, const double* B, double* X, const pcg_options* o,
+                    pcg_stats* st, amg_stream_t stream);
+
+/* ----------------------------------------------------------- batched systems */
+
+/*
+ * Builds one hierarchy for nsys independent SPD systems of uneven sizes (the
+ * paper solves one system per call, Sec. 3; this batches many small ones).
+ * A: host array of nsys CSR descriptors (device pointers, conventions above).
+ * The systems are concatenated into one block-diagonal matrix; its hierarchy
+ * is block diagonal, so each system gets exactly the V-cycle it would get
+ * alone except that coarsening continues until the whole batch has at most
+ * max_coarse rows.  Every level is sliced so that no slice holds rows of two
+ * systems.  Synchronous.  Errors as amg_setup.
+ */
+int amg_setup_batch(int nsys, const amg_csr* A, const amg_options* opt, amg_stream_t stream,
+                    amg_handle** H);
+
+/* nsys (host) and, if row_offsets is not NULL, the first row of every system
+ * in the concatenated vectors (host int64[nsys + 1]). */
+int amg_batch_info(const amg_handle* H, int* nsys, int64_t* row_offsets);
+
+/*
+ * Independent PCG solves of all systems of a batched handle at once: each
+ * system has its own alpha, beta, residual norm and stopping test; converged
+ * systems are frozen while the others iterate.  b, x: device float64, the
+ * systems' vectors concatenated in order (amg_batch_info offsets); x holds the
+ * initial guesses and receives the solutions.  st: host array of nsys stats
+ * (or NULL).  o->res_history and o->x_history must be NULL.  Synchronous.
+ * Returns the worst status over the systems.
+ */
+int pcg_solve_batch(amg_handle* H, const double* b, double* x, const pcg_options* o,
+                    pcg_stats* st, amg_stream_t stream);
+
 /* ----------------------------------------------------------- inspection */
 
 /* One V-cycle kernel launch timed by amg_vcycle_profile. */

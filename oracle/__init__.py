@@ -49,6 +49,9 @@ def _declare(L):
     L.orc_setup.restype = _P
     L.orc_setup.argtypes = [_I64, _P, _P, _P, C.c_int, _I64, C.c_int, C.c_double, _I64, _P,
                             C.POINTER(C.c_int)]
+    L.orc_setup_systems.restype = _P
+    L.orc_setup_systems.argtypes = [_I64, _P, _P, _P, C.c_int, _P, C.c_int, _I64, C.c_int,
+                                    C.c_double, _I64, C.POINTER(C.c_int)]
     L.orc_free.argtypes = [_P]
     L.orc_levels.restype = C.c_int
     L.orc_levels.argtypes = [_P]
@@ -63,16 +66,72 @@ def _declare(L):
     L.orc_vcycle.argtypes = [_P, _P, _P]
     L.orc_pcg.argtypes = [_P, _I64, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int, C.c_int,
                           _P, _P, _P]
+    L.orc_pcg_block.argtypes = [_P, _I64, _I64, _P, _P, C.c_double, C.c_int, C.c_int, _P]
     if hasattr(L, "mlp_orc_forward"):
         _declare_mlp(L)
 
 
 def _declare_mlp(L):
+    L.mlp_orc_nparam.restype = C.c_int
     L.mlp_orc_features.argtypes = [_I64, _I64, _I64, _P, _P, _P, _P]
     L.mlp_orc_forward.argtypes = [_I64, _P, _P, _P, _P]
-    L.mlp_orc_backward.argtypes = [_I64, _P, _P, _P, _P, _P]
+    L.mlp_orc_backward.argtypes = [_I64, _P, _P, _P, _P]
     L.mlp_orc_adam.argtypes = [C.c_int, _P, _P, _P, _P, C.c_int, C.c_double, C.c_double,
                                C.c_double, C.c_double]
+    L.tg_orc_loss.restype = C.c_int
+    L.tg_orc_loss.argtypes = [_I64, _P, _P, _P, _P, _I64, _P, _P, _P, _P, C.c_int, C.c_int, _P,
+                              _P, _P]
+
+
+# ---------------------------------------------------------------- learned smoother
+
+def mlp_nparam():
+    return lib().mlp_orc_nparam()
+
+
+def mlp_features(A, shape):
+    """Nine features per row of a 7-point operator on a grid shape (nz, ny, nx)."""
+    nz, ny, nx = shape
+    n, rp, ci, v = csr_args(A)
+    f = np.empty((n, 9))
+    lib().mlp_orc_features(nx, ny, nz, _p(rp), _p(ci), _p(v), _p(f))
+    return f
+
+
+def mlp_forward(params, feat):
+    p, f = _f64(params), _f64(feat)
+    n = f.shape[0]
+    om, z = np.empty(n), np.empty(n)
+    lib().mlp_orc_forward(n, _p(p), _p(f), _p(om), _p(z))
+    return om, z
+
+
+def mlp_backward(params, feat, domega):
+    p, f, d = _f64(params), _f64(feat), _f64(domega)
+    g = np.empty(mlp_nparam())
+    lib().mlp_orc_backward(f.shape[0], _p(p), _p(f), _p(d), _p(g))
+    return g
+
+
+def mlp_adam(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In-place Adam step on float64 arrays params, m, v."""
+    g = _f64(grad)
+    lib().mlp_orc_adam(len(params), _p(params), _p(g), _p(m), _p(v), t, lr, b1, b2, eps)
+
+
+def twogrid_loss(A, agg, Ac, omega, e0, K=2):
+    """Two-grid error-reduction loss and d loss / d omega (exact coarse solve)."""
+    n, rp, ci, v = csr_args(A)
+    nc, rpc, cic, vc = csr_args(Ac)
+    ag, om, e = _i32(agg), _f64(omega), _f64(e0)
+    ns = e.shape[0]
+    loss = np.zeros(1)
+    dom = np.empty(n)
+    st = lib().tg_orc_loss(n, _p(rp), _p(ci), _p(v), _p(ag), nc, _p(rpc), _p(cic), _p(vc),
+                           _p(om), ns, K, _p(e), _p(loss), _p(dom))
+    if st != 0:
+        raise RuntimeError("coarse matrix not SPD")
+    return float(loss[0]), dom
 
 
 def _p(a):
@@ -176,13 +235,21 @@ class Hierarchy:
     """The oracle's AMG hierarchy (levels, aggregates, smoother scales, coarse factor)."""
 
     def __init__(self, A, sweeps=2, max_coarse=200, max_levels=30, stall=0.9,
-                 max_dense=4096, omega=None):
+                 max_dense=4096, omega=None, systems=None):
+        """systems: row offsets (nsys + 1) of independent systems stacked block
+        diagonally in A; coarsening then stops when each has <= max_coarse rows."""
         n, rp, ci, v = csr_args(A)
         self._keep = (rp, ci, v)
-        om = None if omega is None else _f64(omega)
         st = C.c_int(0)
-        self.h = lib().orc_setup(n, _p(rp), _p(ci), _p(v), sweeps, max_coarse, max_levels,
-                                 stall, max_dense, _p(om), C.byref(st))
+        if systems is not None:
+            so = _i64(systems)
+            self.h = lib().orc_setup_systems(n, _p(rp), _p(ci), _p(v), len(so) - 1, _p(so),
+                                             sweeps, max_coarse, max_levels, stall, max_dense,
+                                             C.byref(st))
+        else:
+            om = None if omega is None else _f64(omega)
+            self.h = lib().orc_setup(n, _p(rp), _p(ci), _p(v), sweeps, max_coarse, max_levels,
+                                     stall, max_dense, _p(om), C.byref(st))
         self.status = st.value
         self.n = n
         self.sweeps = sweeps
@@ -234,6 +301,31 @@ class Hierarchy:
         z = np.empty(self.n)
         lib().orc_vcycle(self.h, _p(r), _p(z))
         return z
+
+
+def block_diag(systems):
+    """Concatenates CSR systems into one block-diagonal CSR; returns (A, offsets)."""
+    rps, cis, vs, offs = [], [], [], [0]
+    nnz = 0
+    for rp, ci, v in systems:
+        rp = np.asarray(rp, dtype=np.int64)
+        rps.append(rp[:-1] - rp[0] + nnz)
+        cis.append(np.asarray(ci, dtype=np.int64) + offs[-1])
+        vs.append(np.asarray(v, dtype=np.float64))
+        nnz += int(rp[-1] - rp[0])
+        offs.append(offs[-1] + len(rp) - 1)
+    rowptr = np.concatenate(rps + [np.array([nnz], dtype=np.int64)])
+    return (rowptr, np.concatenate(cis).astype(np.int32), np.concatenate(vs)), offs
+
+
+def pcg_block(hier, r0, r1, b, x0=None, tol=1e-8, maxit=500, beta_form=0):
+    """PCG on diagonal block [r0, r1) of hier's level-0 matrix with its V-cycle."""
+    b = _f64(b)
+    x = np.zeros(r1 - r0) if x0 is None else _f64(x0).copy()
+    out = np.zeros(4)
+    lib().orc_pcg_block(hier.h, r0, r1, _p(b), _p(x), tol, maxit, beta_form, _p(out))
+    return x, dict(iterations=int(out[0]), status=int(out[1]), relres=float(out[2]),
+                   true_relres=float(out[3]))
 
 
 def pcg(A, b, x0=None, tol=1e-8, maxit=500, beta_form=0, hier=None, binv=None,

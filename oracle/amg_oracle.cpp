@@ -305,8 +305,21 @@ Csr csr_copy(int64_t n, const int64_t* rp, const int32_t* ci, const double* v) {
 }
 
 // Returns 0 or a negative status (-4 not SPD coarse matrix, -1 arguments).
+// Largest diagonal block (system) of a level; the whole level without systems.
+int64_t largest_block(const std::vector<int64_t>& sys, int64_t n) {
+  if (sys.size() < 2) return n;
+  int64_t m = 0;
+  for (size_t k = 0; k + 1 < sys.size(); ++k) m = std::max(m, sys[k + 1] - sys[k]);
+  return m;
+}
+
+// sys: first row of each of several independent systems stacked block
+// diagonally (empty for one system).  With systems, coarsening stops once
+// every system has at most max_coarse rows, so each keeps the coarsest level
+// it would get alone; the coarsest matrix stays block diagonal.
 int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
-          double stall, int64_t max_dense, const double* omega) {
+          double stall, int64_t max_dense, const double* omega,
+          std::vector<int64_t> sys = std::vector<int64_t>()) {
   H.sweeps = sweeps;
   H.lev.clear();
   const int stride = 1 << sweeps;
@@ -316,7 +329,7 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
     Level& L = H.lev[l];
     l1_scale(L.A, l == 0 ? omega : nullptr, L.dinv);
     const int64_t n = L.A.n;
-    if (n <= max_coarse || l + 1 >= max_levels) break;
+    if (largest_block(sys, n) <= max_coarse || l + 1 >= max_levels) break;
     std::vector<int32_t> comp(n);
     for (int64_t i = 0; i < n; ++i) comp[i] = (int32_t)i;
     int64_t nc = n;
@@ -340,9 +353,15 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
     Level next;
     galerkin(L.A, L.agg, nc, L.members, stride, next.A);
     H.lev.push_back(std::move(next));
+    if (sys.size() >= 2) {  // aggregates never span systems
+      std::vector<int64_t> nxt(sys.size());
+      for (size_t k = 0; k + 1 < sys.size(); ++k) nxt[k] = H.lev[l].agg[sys[k]];
+      nxt.back() = nc;
+      sys.swap(nxt);
+    }
   }
   const Csr& C = H.lev.back().A;
-  if (C.n > max_dense) return -1;
+  if (largest_block(sys, C.n) > max_dense) return -1;
   H.nco = C.n;
   return cholesky(C.n, dense_of(C), H.chol) == 0 ? 0 : -4;
 }
@@ -549,6 +568,18 @@ void* orc_setup(int64_t n, const int64_t* rp, const int32_t* ci, const double* v
   return H;
 }
 
+// Hierarchy of nsys systems stacked block diagonally (sys_off: nsys + 1 row
+// offsets); coarsening stops when every system has <= max_coarse rows.
+void* orc_setup_systems(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                        int nsys, const int64_t* sys_off, int sweeps, int64_t max_coarse,
+                        int max_levels, double stall, int64_t max_dense, int* status) {
+  Hierarchy* H = new Hierarchy();
+  std::vector<int64_t> sys(sys_off, sys_off + nsys + 1);
+  *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
+                  nullptr, sys);
+  return H;
+}
+
 void orc_free(void* h) { delete (Hierarchy*)h; }
 
 int orc_levels(void* h) { return (int)((Hierarchy*)h)->lev.size(); }
@@ -604,6 +635,43 @@ void orc_pcg(void* h, int64_t n, const int64_t* rp, const int32_t* ci, const dou
     prec = [n](const double* r, double* z) { std::memcpy(z, r, sizeof(double) * n); };
   }
   PcgOut o = pcg(A, prec, b, x, tol, maxit, beta_form, res_hist, x_hist);
+  out[0] = o.iters;
+  out[1] = o.status;
+  out[2] = o.relres;
+  out[3] = o.true_relres;
+}
+
+// PCG on the diagonal block rows/columns [r0, r1) of the hierarchy's level-0
+// matrix (which must have no entry coupling the block to other rows),
+// preconditioned by the hierarchy's V-cycle applied to the block's residual
+// padded with zeros.  Returns -1 in out[1] if the block is coupled.
+void orc_pcg_block(void* h, int64_t r0, int64_t r1, const double* b, double* x, double tol,
+                   int maxit, int beta_form, double* out) {
+  Hierarchy* H = (Hierarchy*)h;
+  const Csr& A0 = H->lev[0].A;
+  const int64_t N = A0.n, m = r1 - r0;
+  Csr S;
+  S.n = m;
+  S.rowptr.assign(m + 1, 0);
+  for (int64_t i = r0; i < r1; ++i) {
+    for (int64_t e = A0.rowptr[i]; e < A0.rowptr[i + 1]; ++e) {
+      const int64_t j = A0.col[e];
+      if (j < r0 || j >= r1) {
+        out[1] = -1;
+        return;
+      }
+      S.col.push_back((int32_t)(j - r0));
+      S.val.push_back(A0.val[e]);
+    }
+    S.rowptr[i - r0 + 1] = (int64_t)S.col.size();
+  }
+  auto prec = [H, r0, m, N](const double* r, double* z) {
+    std::vector<double> full(N, 0.0), zf(N);
+    std::memcpy(full.data() + r0, r, sizeof(double) * m);
+    vcycle(*H, 0, full.data(), zf.data());
+    std::memcpy(z, zf.data() + r0, sizeof(double) * m);
+  };
+  PcgOut o = pcg(S, prec, b, x, tol, maxit, beta_form, nullptr, nullptr);
   out[0] = o.iters;
   out[1] = o.status;
   out[2] = o.relres;

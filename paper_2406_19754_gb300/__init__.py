@@ -173,13 +173,7 @@ class Hierarchy:
         b = _dev(b, torch.float64, "b")
         if x is None:
             x = torch.zeros_like(b)
-        o = PcgOptions()
-        self._lib.pcg_default_options(C.byref(o))
-        o.tol = tol
-        o.maxit = maxit
-        o.beta_form = {"auto": PCG_BETA_AUTO, "fr": PCG_BETA_FR,
-                       "flexible": PCG_BETA_FLEXIBLE}.get(beta_form, beta_form)
-        o.use_graph = 1 if use_graph else 0
+        o = _pcg_options(self._lib, tol, maxit, beta_form, use_graph)
         hist = None
         if history:
             hist = (C.c_double * (maxit + 1))()
@@ -200,6 +194,87 @@ class Hierarchy:
         if x_history:
             info["x_hist"] = xh[:st.iterations + 1]
         return x, info
+
+    def vcycle_multi(self, R, Z=None, stream=None):
+        """Z = B R for the columns of a row-major (n, k) tensor, k <= 64."""
+        R = _dev(R, torch.float64, "R")
+        if Z is None:
+            Z = torch.empty_like(R)
+        _check(self._lib.amg_vcycle_apply_multi(self.h, R.shape[1], _ptr(R), _ptr(Z),
+                                                _stream(stream)), "amg_vcycle_apply_multi")
+        return Z
+
+    def pcg_multi(self, B, X=None, tol=1e-8, maxit=500, beta_form="auto", stream=None):
+        """Solves A X = B column by column (B row-major (n, k), k <= 64).
+        Returns (X, list of per-column stats dicts)."""
+        B = _dev(B, torch.float64, "B")
+        if X is None:
+            X = torch.zeros_like(B)
+        o = _pcg_options(self._lib, tol, maxit, beta_form, True)
+        k = B.shape[1]
+        st = (PcgStats * k)()
+        rc = self._lib.pcg_solve_multi(self.h, k, _ptr(B), _ptr(X), C.byref(o), st,
+                                       _stream(stream))
+        if rc not in (_lib.AMG_ERR_BREAKDOWN, _lib.AMG_ERR_NAN):
+            _check(rc, "pcg_solve_multi")
+        return X, _stats_list(st)
+
+
+def _pcg_options(lib, tol, maxit, beta_form, use_graph):
+    o = PcgOptions()
+    lib.pcg_default_options(C.byref(o))
+    o.tol = tol
+    o.maxit = maxit
+    o.beta_form = {"auto": PCG_BETA_AUTO, "fr": PCG_BETA_FR,
+                   "flexible": PCG_BETA_FLEXIBLE}.get(beta_form, beta_form)
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def _stats_list(st):
+    return [dict(iterations=s.iterations, status=s.status, relres=s.rel_residual,
+                 true_relres=s.true_rel_residual, solve_ms=s.solve_ms) for s in st]
+
+
+class BatchHierarchy(Hierarchy):
+    """One hierarchy for many independent systems (list of (rowptr, col, val)
+    CUDA tensors); ``pcg`` solves them all with per-system scalars."""
+
+    def __init__(self, systems, stream=None, **opts):
+        self._lib = _lib.load()
+        keep = []
+        arr = (AmgCsr * len(systems))()
+        for k, (rp, ci, v) in enumerate(systems):
+            A, kp = csr_struct(rp, ci, v)
+            arr[k] = A
+            keep.append(kp)
+        o = options(**opts)
+        self.opts = o
+        h = C.c_void_p()
+        _check(self._lib.amg_setup_batch(len(systems), arr, C.byref(o), _stream(stream),
+                                         C.byref(h)), "amg_setup_batch")
+        self.h = h
+        ns = C.c_int()
+        offs = (C.c_int64 * (len(systems) + 1))()
+        _check(self._lib.amg_batch_info(self.h, C.byref(ns), offs))
+        self.nsys = ns.value
+        self.offsets = list(offs)
+        self.n = self.offsets[-1]
+        del keep
+
+    def pcg(self, b, x=None, tol=1e-8, maxit=500, beta_form="auto", use_graph=True,
+            stream=None):
+        """Solves every system; b, x concatenated.  Returns (x, list of stats dicts)."""
+        b = _dev(b, torch.float64, "b")
+        if x is None:
+            x = torch.zeros_like(b)
+        o = _pcg_options(self._lib, tol, maxit, beta_form, use_graph)
+        st = (PcgStats * self.nsys)()
+        rc = self._lib.pcg_solve_batch(self.h, _ptr(b), _ptr(x), C.byref(o), st,
+                                       _stream(stream))
+        if rc not in (_lib.AMG_ERR_BREAKDOWN, _lib.AMG_ERR_NAN):
+            _check(rc, "pcg_solve_batch")
+        return x, _stats_list(st)
 
 
 def pairwise_match(rowptr, col, val, stream=None):

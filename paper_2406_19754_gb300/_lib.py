@@ -66,6 +66,13 @@ SIGNATURES = {
                                      C.POINTER(C.c_int), _P]),
     "amg_spmv": (C.c_int, [_P, C.c_int, C.c_double, _P, C.c_double, _P, _P]),
     "pcg_solve": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), C.POINTER(PcgStats), _P]),
+    "amg_vcycle_apply_multi": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "pcg_solve_multi": (C.c_int, [_P, C.c_int, _P, _P, C.POINTER(PcgOptions),
+                                  C.POINTER(PcgStats), _P]),
+    "amg_setup_batch": (C.c_int, [C.c_int, C.POINTER(AmgCsr), C.POINTER(AmgOptions), _P,
+                                  C.POINTER(_P)]),
+    "amg_batch_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
+    "pcg_solve_batch": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), C.POINTER(PcgStats), _P]),
     "amg_num_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "amg_level_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "amg_level_export": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),

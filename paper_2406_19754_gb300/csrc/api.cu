@@ -72,6 +72,9 @@ static int check_csr(const amg_csr* A) {
 
 static void destroy(amg_handle* H) {
   if (!H) return;
+  multi_free(H);
+  if (H->batch.sc_host) cudaFreeHost(H->batch.sc_host);
+  if (H->bgraph) cudaGraphExecDestroy(H->bgraph);
   if (H->graph) cudaGraphExecDestroy(H->graph);
   if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   if (H->ev0) cudaEventDestroy(H->ev0);
@@ -81,7 +84,8 @@ static void destroy(amg_handle* H) {
   delete H;
 }
 
-static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_handle** out) {
+static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_handle** out,
+                  int nsys = 0, const amg_csr* systems = nullptr) {
   amg_handle* H = new amg_handle();
   *out = H;
   if (opt)
@@ -89,6 +93,20 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   else
     amg_default_options(&H->opt);
   AMG_TRY(check_options(H->opt));
+  amg_csr cat;
+  int64_t* cat_rp = nullptr;
+  int32_t* cat_ci = nullptr;
+  double* cat_va = nullptr;
+  if (systems) {  // batched: one block-diagonal matrix with system-aligned slices
+    int dev = 0, sms = 0;
+    AMG_CUDA_TRY(cudaGetDevice(&dev));
+    AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    AMG_TRY(concat_systems(H->arena, nsys, systems, &cat, &cat_rp, &cat_ci, &cat_va,
+                           H->sys_off0, sms, s));
+    H->batched = true;
+    H->nsys = nsys;
+    A = &cat;
+  }
   AMG_CUDA_TRY(cudaGetDevice(&H->device));
   AMG_CUDA_TRY(cudaDeviceGetAttribute(&H->num_sms, cudaDevAttrMultiProcessorCount, H->device));
   AMG_CUDA_TRY(cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking));
@@ -110,6 +128,12 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   AMG_TRY(ar.alloc_n(&H->z, n));
   AMG_TRY(ar.alloc_n(&H->p, n));
   AMG_TRY(ar.alloc_n(&H->q, n));
+  if (H->batched) {
+    AMG_TRY(batch_init(H, s));
+    ar.release(cat_rp);  // the hierarchy keeps its own copies
+    ar.release(cat_ci);
+    ar.release(cat_va);
+  }
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   return AMG_OK;
 }
@@ -133,6 +157,52 @@ int amg_setup(const amg_csr* A, const amg_options* opt, amg_stream_t stream, amg
 int amg_destroy(amg_handle* H) {
   destroy(H);
   return AMG_OK;
+}
+
+int amg_setup_batch(int nsys, const amg_csr* A, const amg_options* opt, amg_stream_t stream,
+                    amg_handle** H) {
+  if (!H) return AMG_ERR_ARG;
+  *H = nullptr;
+  if (nsys <= 0 || !A) return AMG_ERR_ARG;
+  for (int k = 0; k < nsys; ++k) {
+    int rc = check_csr(&A[k]);
+    if (rc < 0) return rc;
+  }
+  amg_handle* h = nullptr;
+  int rc = create(nullptr, opt, (cudaStream_t)stream, &h, nsys, A);
+  if (rc < 0) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    destroy(h);
+    return rc;
+  }
+  *H = h;
+  return AMG_OK;
+}
+
+int amg_batch_info(const amg_handle* H, int* nsys, int64_t* row_offsets) {
+  if (!H || !nsys) return AMG_ERR_ARG;
+  *nsys = H->batched ? H->nsys : 1;
+  if (row_offsets) {
+    if (H->batched)
+      for (int k = 0; k <= H->nsys; ++k) row_offsets[k] = H->sys_off0[k];
+    else {
+      row_offsets[0] = 0;
+      row_offsets[1] = H->L[0].n;
+    }
+  }
+  return AMG_OK;
+}
+
+int pcg_solve_batch(amg_handle* H, const double* b, double* x, const pcg_options* o,
+                    pcg_stats* st, amg_stream_t stream) {
+  if (!H || !b || !x || !H->batched) return AMG_ERR_ARG;
+  pcg_options def;
+  pcg_default_options(&def);
+  const pcg_options* op = o ? o : &def;
+  if (op->maxit < 0 || !(op->tol >= 0.0)) return AMG_ERR_ARG;
+  if (op->beta_form < PCG_BETA_AUTO || op->beta_form > PCG_BETA_FLEXIBLE) return AMG_ERR_ARG;
+  if (op->res_history || op->x_history) return AMG_ERR_ARG;  // per-system histories: not kept
+  return pcg_batch_run(H, b, x, op, st, (cudaStream_t)stream);
 }
 
 int amg_set_smoother_weights(amg_handle* H, const float* omega, amg_stream_t stream) {
@@ -168,6 +238,26 @@ int pcg_solve(amg_handle* H, const double* b, double* x, const pcg_options* o, p
   if (op->maxit < 0 || !(op->tol >= 0.0)) return AMG_ERR_ARG;
   if (op->beta_form < PCG_BETA_AUTO || op->beta_form > PCG_BETA_FLEXIBLE) return AMG_ERR_ARG;
   return pcg_run(H, b, x, op, st, (cudaStream_t)stream);
+}
+
+int amg_vcycle_apply_multi(amg_handle* H, int nrhs, const double* R, double* Z,
+                           amg_stream_t stream) {
+  if (!H || !R || !Z || (const double*)Z == R || nrhs < 1 || nrhs > 64) return AMG_ERR_ARG;
+  if (H->L.size() < 2 || H->L[0].A.row0) return AMG_ERR_UNSUPPORTED;
+  return vcycle_multi(H, nrhs, R, Z, (cudaStream_t)stream);
+}
+
+int pcg_solve_multi(amg_handle* H, int nrhs, const double* B, double* X, const pcg_options* o,
+                    pcg_stats* st, amg_stream_t stream) {
+  if (!H || !B || !X || nrhs < 1 || nrhs > 64) return AMG_ERR_ARG;
+  if (H->L.size() < 2 || H->L[0].A.row0) return AMG_ERR_UNSUPPORTED;
+  pcg_options def;
+  pcg_default_options(&def);
+  const pcg_options* op = o ? o : &def;
+  if (op->maxit < 0 || !(op->tol >= 0.0)) return AMG_ERR_ARG;
+  if (op->beta_form < PCG_BETA_AUTO || op->beta_form > PCG_BETA_FLEXIBLE) return AMG_ERR_ARG;
+  if (op->res_history || op->x_history) return AMG_ERR_ARG;
+  return pcg_multi_run(H, nrhs, B, X, op, st, (cudaStream_t)stream);
 }
 
 int amg_num_levels(const amg_handle* H, int* levels) {

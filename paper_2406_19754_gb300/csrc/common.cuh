@@ -57,6 +57,9 @@ struct Arena {
 // each slice an ELLPACK block of width = its longest row, stored column
 // major (entry k of row r of slice s at sliceptr[s] + k * C + r).  Padding
 // entries carry val = 0 and a valid column (the row itself).
+// Batched systems: every system starts a new slice, so slice s covers rows
+// [row0[s], row0[s+1]) (at most C rows) and belongs to system sys[s].
+// Without systems row0/sys are null and slice s covers rows [s*C, s*C + C).
 struct Sell {
   int64_t n = 0, nslices = 0, nnz_pad = 0;
   int C = 32, tpr = 1;
@@ -65,6 +68,8 @@ struct Sell {
   double* v64 = nullptr;
   float* v32 = nullptr;
   __nv_bfloat16* v16 = nullptr;
+  int64_t* row0 = nullptr;  // nslices + 1, or null
+  int32_t* sys = nullptr;   // nslices, or null
 };
 
 template <typename V>
@@ -73,6 +78,17 @@ struct SellView {
   const int64_t* sliceptr;
   const int32_t* col;
   const V* val;
+  const int64_t* row0;
+  const int32_t* sys;
+  // first row of slice s and one past its last row
+  __device__ __forceinline__ int64_t rbeg(int64_t s, int C) const {
+    return row0 ? __ldg(row0 + s) : s * C;
+  }
+  __device__ __forceinline__ int64_t rend(int64_t s, int C) const {
+    if (row0) return __ldg(row0 + s + 1);
+    const int64_t e = (s + 1) * C;
+    return e < n ? e : n;
+  }
 };
 
 // Value storage of a level in the V-cycle.
@@ -105,6 +121,25 @@ struct Level {
   void* b = nullptr;
   void* x = nullptr;
   void* r = nullptr;
+  // batched systems: first row of each system on this level (nsys + 1, host)
+  std::vector<int64_t> sys_off;
+};
+
+// Batched PCG state (pcg_solve_batch): per-system scalars and per-slice
+// partial sums over the level-0 slices, which never straddle two systems.
+struct Batch {
+  int nsys = 0;
+  int64_t nslices = 0;
+  int64_t* slice_off = nullptr;  // device, nsys + 1: slices of system k
+  double* part = nullptr;        // device, 2 * nslices
+  struct Scal* sc = nullptr;     // device, nsys
+  struct Scal* sc_host = nullptr;  // pinned, nsys
+  int* nactive = nullptr;        // device counter
+};
+
+struct Scal {
+  double bb, rr, rz, pq, zq, alpha, beta, tr;
+  int status, active, iters, pq_fail;
 };
 
 // Device-resident PCG scalars.
@@ -131,8 +166,15 @@ struct amg_handle {
   amg::Arena arena;
   std::vector<amg::Level> L;
   int64_t nco = 0;
-  double* Linv = nullptr;   // coarsest: L^-1, row-major n x n
-  double* LinvT = nullptr;  // (L^-1)^T, row-major
+  // coarsest level: block diagonal (one block per batched system, else one);
+  // block b has rows [brow[b], brow[b+1]) and its L^-1 and L^-T (row-major,
+  // dense) start at bmat[b] in Linv / LinvT
+  int nblk = 1;
+  std::vector<int64_t> cblk_row;
+  int64_t* d_brow = nullptr;
+  int64_t* d_bmat = nullptr;
+  double* Linv = nullptr;
+  double* LinvT = nullptr;
   // PCG workspace
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   amg::PcgScalars* sc = nullptr;
@@ -145,6 +187,15 @@ struct amg_handle {
   double* graph_x = nullptr;
   int graph_beta = -2;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // batched systems (amg_setup_batch); nsys == 1 otherwise
+  bool batched = false;
+  int nsys = 1;
+  std::vector<int64_t> sys_off0;  // first row of each system (nsys + 1)
+  amg::Batch batch;
+  cudaGraphExec_t bgraph = nullptr;
+  double* bgraph_x = nullptr;
+  int bgraph_beta = -2;
+  void* multi = nullptr;  // multi-RHS workspace (multi.cu)
 };
 
 namespace amg {
@@ -205,22 +256,11 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
   }
 }
 
-// Grid-wide deterministic reduction: each block stores its partial sums; the
-// last block to finish adds all partials in block order (fixed tree) and
-// runs `epi(total)` in thread 0.  Requires gridDim.x <= red.max_blocks.
+// Last block of a grid reduction: adds all block partials in block order
+// (fixed tree) and runs `epi(total)` in thread 0.  Kept out of line so its
+// registers do not count against the streaming loop of the calling kernel.
 template <int NV, typename Epi>
-__device__ __forceinline__ void grid_reduce(double (&v)[NV], Reduce red, Epi epi) {
-  __shared__ bool last;
-  block_sum<NV>(v);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) red.partials[(size_t)k * red.max_blocks + blockIdx.x] = v[k];
-    __threadfence();
-    unsigned t = atomicAdd(red.ticket, 1u);
-    last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
+__device__ __noinline__ void grid_reduce_tail(Reduce red, Epi epi) {
   __threadfence();
   double acc[NV];
 #pragma unroll
@@ -236,6 +276,24 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NV], Reduce red, Epi epi
   }
 }
 
+// Grid-wide deterministic reduction: each block stores its partial sums; the
+// last block to finish reduces them (grid_reduce_tail).  Requires
+// gridDim.x <= red.max_blocks.
+template <int NV, typename Epi>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], Reduce red, Epi epi) {
+  __shared__ bool last;
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red.partials[(size_t)k * red.max_blocks + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(red.ticket, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) grid_reduce_tail<NV>(red, epi);
+}
+
 // ------------------------------------------------------------------ host helpers
 
 int grid_for(int64_t work_items, int threads, int num_sms, int blocks_per_sm);
@@ -248,7 +306,8 @@ int scan_exclusive_i64(Arena& ar, const int64_t* in, int64_t* out, int64_t n, in
 
 // SELL conversion (sell.cu)
 int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* col,
-                  const double* val, int C, int tpr, Sell& out, cudaStream_t s);
+                  const double* val, int C, int tpr, Sell& out, cudaStream_t s,
+                  const std::vector<int64_t>* sys_off = nullptr);
 int sell_make_copies(Arena& ar, Sell& A, int vstore, cudaStream_t s);
 int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, double* y,
                 int num_sms, cudaStream_t s);
@@ -279,12 +338,28 @@ int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s);
 
 // V-cycle (vcycle.cu).  dots: 0 none; 1 (r, z); 2 (r, z) and (z, q).
 int vcycle_run(const amg_handle* H, const double* r, double* z, int dots, const double* q,
-               cudaStream_t s);
+               cudaStream_t s, double* slice_part = nullptr);
 int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_time* out,
                    int max_out, int* count, cudaStream_t s);
+int time_level(const amg_handle* H, int l, int reps, const double* b64, double* z64, float* ms,
+               cudaStream_t s);
 
 // PCG (pcg.cu)
 int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
             cudaStream_t s);
+
+// Multiple right-hand sides (multi.cu)
+int vcycle_multi(amg_handle* H, int K, const double* R, double* Z, cudaStream_t s);
+int pcg_multi_run(amg_handle* H, int K, const double* B, double* X, const pcg_options* o,
+                  pcg_stats* st, cudaStream_t s);
+void multi_free(amg_handle* H);
+
+// Batched systems (batch.cu)
+int concat_systems(Arena& ar, int nsys, const amg_csr* A, amg_csr* cat, int64_t** rp,
+                   int32_t** ci, double** va, std::vector<int64_t>& off, int num_sms,
+                   cudaStream_t s);
+int batch_init(amg_handle* H, cudaStream_t s);
+int pcg_batch_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
+                  cudaStream_t s);
 
 }  // namespace amg

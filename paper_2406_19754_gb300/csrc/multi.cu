@@ -1,0 +1,728 @@
+// Multi-RHS PCG: K independent CG iterations on the same matrix, vectors
+// stored row-major N x K so one row's K values are contiguous.
+//
+// Mapping: one warp per matrix row, lane l owning right-hand sides l and
+// l + 32 (KPL = 1 or 2 columns per lane, K <= 64).  Every matrix entry is
+// loaded once per warp and applied to all K columns, so the matrix stream is
+// amortised K-fold and the kernels stream the N x K vectors.  Per column the
+// arithmetic follows the single-RHS kernels' operation order (entries in
+// slice order, one FMA each), so the blocked V-cycle reproduces K separate
+// V-cycles bit for bit.  Column dot products are reduced per block and then
+// by the last block, in fixed order.  Each column has its own alpha, beta and
+// stopping test; converged columns are frozen (alpha = 0, p unchanged).
+#include <math.h>
+
+#include <algorithm>
+
+#include "sellk.cuh"
+
+namespace amg {
+
+constexpr int MROWS_BLOCK = 256;  // 8 warps = 8 rows in flight per block
+
+struct MultiWs {
+  int K = 0;
+  double *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr;  // N x K
+  void** lb = nullptr;  // per level b, x, r (V-cycle type), host arrays of pointers
+  void** lx = nullptr;
+  void** lr = nullptr;
+  double* cy = nullptr;  // coarse scratch n_c x K
+  double* part = nullptr;  // 2 x max_blocks x K
+  unsigned* ticket = nullptr;
+  Scal* sc = nullptr;  // K
+  Scal* sc_host = nullptr;
+  int* nactive = nullptr;
+};
+
+// Entries of row i of a (non-batched) sliced-ELL matrix.
+struct RowSpan {
+  const int32_t* col;
+  int64_t stride;
+  int w;
+  int64_t off;
+};
+
+template <typename V>
+__device__ __forceinline__ RowSpan row_span(const SellView<V>& A, int64_t i, int C) {
+  const int64_t s = i / C;
+  const int64_t beg = __ldg(A.sliceptr + s);
+  RowSpan r;
+  r.w = (int)((__ldg(A.sliceptr + s + 1) - beg) / C);
+  r.off = beg + (i - s * C);
+  r.stride = C;
+  r.col = A.col;
+  return r;
+}
+
+// acc[c] = sum_k a_ik * g(col_k, c) for the lane's columns.
+template <int KPL, typename AccT, typename V, typename G>
+__device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, int K, int lane,
+                                       AccT (&acc)[KPL], G g) {
+  const RowSpan r = row_span(A, i, C);
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) acc[q] = AccT(0);
+  for (int k = 0; k < r.w; ++k) {
+    const int64_t e = r.off + (int64_t)k * r.stride;
+    const int j = __ldg(A.col + e);
+    const AccT a = to_f(__ldg(A.val + e), AccT(0));
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      if (c < K) acc[q] = fma(a, g(j, c), acc[q]);
+    }
+  }
+}
+
+// Column sums over the grid: per-block sums in fixed warp order, then the
+// last block adds the blocks in order and calls epi(c, t) for every column.
+template <int KPL, int NV, typename Epi>
+__device__ void cols_reduce(double (&v)[NV][KPL], int K, double* part, int maxb,
+                            unsigned* ticket, Epi epi) {
+  __shared__ double sh[NV][MROWS_BLOCK / 32][64];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < NV; ++m)
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) sh[m][w][lane + 32 * q] = v[m][q];
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < NV * K; t += blockDim.x) {
+    const int m = t / K, c = t % K;
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sh[m][k][c];
+    part[((size_t)m * maxb + blockIdx.x) * K + c] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    double t[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+      double s = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&part[((size_t)m * maxb + b) * K + c]);
+      t[m] = s;
+    }
+    epi(c, t);
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// ------------------------------------------------------------------ V-cycle kernels
+
+template <int KPL, typename V, typename T, typename BT>
+__global__ void __launch_bounds__(MROWS_BLOCK)
+    k_m_pre(SellView<V> Ah, int C, int K, const BT* __restrict__ B, T* __restrict__ R) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < Ah.n; i += nw) {
+    T acc[KPL];
+    row_mv<KPL, T>(Ah, i, C, K, lane, acc,
+                   [&](int j, int c) { return to_f(__ldg(B + (int64_t)j * K + c), T(0)); });
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      if (c < K) R[i * K + c] = to_f(B[i * K + c], T(0)) - acc[q];
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_m_restrict(int64_t nc, int stride, int K, const int32_t* __restrict__ members,
+                             const T* __restrict__ R, T* __restrict__ Bc) {
+  const int64_t total = nc * K;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = t / K;
+    const int c = (int)(t % K);
+    const int32_t* m = members + I * stride;
+    T acc = R[(int64_t)m[0] * K + c];
+    for (int k = 1; k < stride; ++k) {
+      const int32_t i = m[k];
+      if (i < 0) break;
+      acc = acc + R[(int64_t)i * K + c];
+    }
+    Bc[t] = acc;
+  }
+}
+
+struct MultiRzEpi {
+  Scal* sc;
+  int beta_form;
+  int first;
+  __device__ void operator()(int c, const double (&t)[2]) const {
+    Scal& S = sc[c];
+    if (first) {
+      S.rz = t[0];
+      return;
+    }
+    if (!S.active) return;
+    S.beta = beta_form == PCG_BETA_FLEXIBLE ? -t[1] / S.pq : t[0] / S.rz;
+    S.zq = t[1];
+    S.rz = t[0];
+    if (!isfinite(t[0])) {
+      S.status = AMG_ERR_NAN;
+      S.active = 0;
+    }
+  }
+};
+
+template <int KPL, typename V, typename T, typename BT, typename XT, bool DOTS>
+__global__ void __launch_bounds__(MROWS_BLOCK)
+    k_m_post(SellView<V> AP, int C, int K, const BT* __restrict__ B, const T* __restrict__ s,
+             const T* __restrict__ R, const int32_t* __restrict__ agg, const T* __restrict__ Xc,
+             XT* __restrict__ Z, const double* __restrict__ Q, double* part, int maxb,
+             unsigned* ticket, MultiRzEpi epi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double d[2][KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) d[0][q] = d[1][q] = 0.0;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < AP.n; i += nw) {
+    T acc[KPL];
+    row_mv<KPL, T>(AP, i, C, K, lane, acc,
+                   [&](int J, int c) { return __ldg(Xc + (int64_t)J * K + c); });
+    const T si = s[i];
+    const int64_t ai = agg[i];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      if (c < K) {
+        const T bi = to_f(B[i * K + c], T(0));
+        const T yi = si * bi + Xc[ai * K + c];
+        const XT zi = to_f(yi + si * (R[i * K + c] - acc[q]), XT(0));
+        Z[i * K + c] = zi;
+        if (DOTS) {
+          d[0][q] += (double)B[i * K + c] * (double)zi;
+          d[1][q] += (double)zi * Q[i * K + c];
+        }
+      }
+    }
+  }
+  if constexpr (DOTS) cols_reduce<KPL, 2>(d, K, part, maxb, ticket, epi);
+}
+
+// Coarsest level for K columns: Y = L^-1 B, then X = L^-T Y, one thread per
+// output element (n <= 3072).  Each dot product is summed exactly as the
+// single-RHS coarse kernel sums it: 32 lane partials over a stride of 32,
+// combined by the same xor-butterfly tree.
+__device__ __forceinline__ double lane_tree(double (&p)[32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int l = 0; l < o; ++l) p[l] = p[l] + p[l + o];
+  return p[0];
+}
+
+// Diagonal block of coarsest row i: b with brow[b] <= i < brow[b+1].
+__device__ __forceinline__ int coarse_block(const int64_t* brow, int nblk, int64_t i) {
+  int lo = 0, hi = nblk;  // brow[lo] <= i < brow[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (brow[mid] <= i)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+template <typename BT>
+__global__ void k_m_coarse1(int64_t n, int K, int nblk, const int64_t* __restrict__ brow,
+                            const int64_t* __restrict__ bmat, const double* __restrict__ Linv,
+                            const BT* __restrict__ B, double* __restrict__ Y) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * K;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gi = t / K;
+    const int c = (int)(t % K);
+    const int b = coarse_block(brow, nblk, gi);
+    const int64_t r0 = brow[b];
+    const int m = (int)(brow[b + 1] - r0), i = (int)(gi - r0);
+    const double* L = Linv + bmat[b];
+    double p[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) p[l] = 0.0;
+    for (int k = 0; k <= i; ++k)
+      p[k & 31] = fma(L[(int64_t)i * m + k], (double)B[(r0 + k) * K + c], p[k & 31]);
+    Y[t] = lane_tree(p);
+  }
+}
+
+template <typename XT>
+__global__ void k_m_coarse2(int64_t n, int K, int nblk, const int64_t* __restrict__ brow,
+                            const int64_t* __restrict__ bmat, const double* __restrict__ LinvT,
+                            const double* __restrict__ Y, XT* __restrict__ X) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * K;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t gk = t / K;
+    const int c = (int)(t % K);
+    const int b = coarse_block(brow, nblk, gk);
+    const int64_t r0 = brow[b];
+    const int m = (int)(brow[b + 1] - r0), k = (int)(gk - r0);
+    const double* LT = LinvT + bmat[b];
+    double p[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) p[l] = 0.0;
+    for (int i = k; i < m; ++i)
+      p[(i - k) & 31] = fma(LT[(int64_t)k * m + i], Y[(r0 + i) * K + c], p[(i - k) & 31]);
+    X[t] = (XT)lane_tree(p);
+  }
+}
+
+// ------------------------------------------------------------------ PCG kernels
+
+struct MultiInitEpi {
+  Scal* sc;
+  double tol;
+  int maxit;
+  int* nactive;
+  int mode;  // 0: initial residual, 1: true residual at exit
+  __device__ void operator()(int c, const double (&t)[2]) const {
+    Scal& S = sc[c];
+    if (mode == 1) {
+      S.tr = t[0];
+      return;
+    }
+    S.rr = t[0];
+    S.bb = t[1];
+    S.iters = 0;
+    S.pq_fail = 0;
+    const double bn = t[1] > 0.0 ? sqrt(t[1]) : 1.0;
+    const bool done = sqrt(t[0]) / bn <= tol;
+    S.status = done ? AMG_OK : AMG_NOT_CONVERGED;
+    S.active = (!done && maxit > 0) ? 1 : 0;
+    if (S.active) atomicAdd(nactive, 1);
+  }
+};
+
+template <int KPL>
+__global__ void __launch_bounds__(MROWS_BLOCK)
+    k_m_residual(SellView<double> A, int C, int K, const double* __restrict__ B,
+                 const double* __restrict__ X, double* __restrict__ R, double* part, int maxb,
+                 unsigned* ticket, MultiInitEpi epi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double d[2][KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) d[0][q] = d[1][q] = 0.0;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n; i += nw) {
+    double acc[KPL];
+    row_mv<KPL, double>(A, i, C, K, lane, acc,
+                        [&](int j, int c) { return __ldg(X + (int64_t)j * K + c); });
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      if (c < K) {
+        const double bi = B[i * K + c];
+        const double ri = bi - acc[q];
+        R[i * K + c] = ri;
+        d[0][q] += ri * ri;
+        d[1][q] += bi * bi;
+      }
+    }
+  }
+  cols_reduce<KPL, 2>(d, K, part, maxb, ticket, epi);
+}
+
+struct MultiPqEpi {
+  Scal* sc;
+  __device__ void operator()(int c, const double (&t)[1]) const {
+    Scal& S = sc[c];
+    if (!S.active) {
+      S.alpha = 0.0;
+      return;
+    }
+    S.pq = t[0];
+    S.alpha = S.rz / t[0];
+    if (!(t[0] > 0.0)) {
+      S.status = isfinite(t[0]) ? AMG_ERR_BREAKDOWN : AMG_ERR_NAN;
+      S.pq_fail = 1;
+      S.active = 0;
+      S.alpha = 0.0;
+    }
+  }
+};
+
+template <int KPL>
+__global__ void __launch_bounds__(MROWS_BLOCK)
+    k_m_spmm_dot(SellView<double> A, int C, int K, const double* __restrict__ P,
+                 double* __restrict__ Q, double* part, int maxb, unsigned* ticket, MultiPqEpi epi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double d[1][KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) d[0][q] = 0.0;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n; i += nw) {
+    double acc[KPL];
+    row_mv<KPL, double>(A, i, C, K, lane, acc,
+                        [&](int j, int c) { return __ldg(P + (int64_t)j * K + c); });
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      if (c < K) {
+        Q[i * K + c] = acc[q];
+        d[0][q] += P[i * K + c] * acc[q];
+      }
+    }
+  }
+  cols_reduce<KPL, 1>(d, K, part, maxb, ticket, epi);
+}
+
+struct MultiRrEpi {
+  Scal* sc;
+  double tol;
+  int maxit;
+  int* nactive;
+  __device__ void operator()(int c, const double (&t)[1]) const {
+    Scal& S = sc[c];
+    if (!S.active) return;
+    S.rr = t[0];
+    S.iters += 1;
+    const double bn = S.bb > 0.0 ? sqrt(S.bb) : 1.0;
+    const double rel = sqrt(t[0]) / bn;
+    if (!isfinite(t[0])) {
+      S.status = AMG_ERR_NAN;
+      S.active = 0;
+    } else if (rel <= tol) {
+      S.status = AMG_OK;
+      S.active = 0;
+    } else if (S.iters >= maxit) {
+      S.status = AMG_NOT_CONVERGED;
+      S.active = 0;
+    }
+    if (S.active) atomicAdd(nactive, 1);
+  }
+};
+
+// x += alpha_c p; r -= alpha_c q; (r, r) per column (alpha_c = 0 when frozen).
+template <int KPL>
+__global__ void __launch_bounds__(MROWS_BLOCK)
+    k_m_update(int64_t n, int K, double* __restrict__ X, double* __restrict__ R,
+               const double* __restrict__ P, const double* __restrict__ Q, const Scal* sc,
+               double* part, int maxb, unsigned* ticket, MultiRrEpi epi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double al[KPL], d[1][KPL];
+  bool act[KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int c = lane + 32 * q;
+    act[q] = c < K && sc[c].active;
+    al[q] = act[q] ? sc[c].alpha : 0.0;
+    d[0][q] = 0.0;
+  }
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      if (act[q]) {
+        const int64_t e = i * K + c;
+        X[e] = X[e] + al[q] * P[e];
+        const double ri = R[e] - al[q] * Q[e];
+        R[e] = ri;
+        d[0][q] += ri * ri;
+      }
+    }
+  }
+  cols_reduce<KPL, 1>(d, K, part, maxb, ticket, epi);
+}
+
+// p = z + beta_c p for columns still iterating.
+template <int KPL>
+__global__ void k_m_p_update(int64_t n, int K, double* __restrict__ P, const double* __restrict__ Z,
+                             const Scal* sc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double be[KPL];
+  bool act[KPL];
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) {
+    const int c = lane + 32 * q;
+    act[q] = c < K && sc[c].active;
+    be[q] = act[q] ? sc[c].beta : 0.0;
+  }
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw)
+#pragma unroll
+    for (int q = 0; q < KPL; ++q)
+      if (act[q]) {
+        const int64_t e = i * K + lane + 32 * q;
+        P[e] = Z[e] + be[q] * P[e];
+      }
+}
+
+// ------------------------------------------------------------------ driver
+
+#define AMG_DISPATCH_KPL(K, ...)          \
+  if ((K) <= 32) {                        \
+    constexpr int KPL = 1;                \
+    __VA_ARGS__;                          \
+  } else {                                \
+    constexpr int KPL = 2;                \
+    __VA_ARGS__;                          \
+  }
+
+static int mgrid(const amg_handle* H, int64_t rows) {
+  return grid_for(rows * 32, MROWS_BLOCK, H->num_sms, 8);
+}
+
+template <typename T>
+static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, double* Z0,
+                    bool dots, const double* Q, int beta_form, bool first, cudaStream_t s) {
+  const int K = W.K;
+  const int nl = (int)H->L.size();
+  const int maxb = H->red.max_blocks;
+  MultiRzEpi epi{W.sc, beta_form, first ? 1 : 0};
+  auto coarse = [&](const auto* b, auto* x) -> int {
+    const int64_t n = H->nco;
+    const int g = grid_for(n * K, 256, H->num_sms, 4);
+    k_m_coarse1<<<g, 256, 0, s>>>(n, K, H->nblk, H->d_brow, H->d_bmat, H->Linv, b, W.cy);
+    AMG_LAUNCH_CHECK();
+    k_m_coarse2<<<g, 256, 0, s>>>(n, K, H->nblk, H->d_brow, H->d_bmat, H->LinvT, W.cy, x);
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+  };
+  if (nl == 1) return AMG_ERR_UNSUPPORTED;  // single-level hierarchies: use pcg_solve
+  for (int l = 0; l < nl - 1; ++l) {
+    const Level& L = H->L[l];
+    T* r = (T*)W.lr[l];
+    const int g = mgrid(H, L.n);
+    if constexpr (sizeof(T) == 8) {
+      const double* b = l == 0 ? R0 : (const double*)W.lb[l];
+      const SellView<double> v = view<double>(L.A, L.ah64);
+      AMG_DISPATCH_KPL(K, (k_m_pre<KPL, double, double, double><<<g, MROWS_BLOCK, 0, s>>>(
+                              v, L.A.C, K, b, r)));
+    } else {
+      if (L.vstore == VAL_BF16) {
+        const SellView<__nv_bfloat16> v = view<__nv_bfloat16>(L.A, L.ah16);
+        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, __nv_bfloat16, float, float><<<g, MROWS_BLOCK, 0, s>>>(
+                                v, L.A.C, K, (const float*)W.lb[l], r)));
+      } else if (l == 0) {
+        const SellView<float> v = view<float>(L.A, L.ah32);
+        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, float, float, double><<<g, MROWS_BLOCK, 0, s>>>(
+                                v, L.A.C, K, R0, r)));
+      } else {
+        const SellView<float> v = view<float>(L.A, L.ah32);
+        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, float, float, float><<<g, MROWS_BLOCK, 0, s>>>(
+                                v, L.A.C, K, (const float*)W.lb[l], r)));
+      }
+    }
+    AMG_LAUNCH_CHECK();
+    k_m_restrict<T><<<grid_for(L.nc * K, 256, H->num_sms, 8), 256, 0, s>>>(
+        L.nc, L.stride, K, L.members, r, (T*)W.lb[l + 1]);
+    AMG_LAUNCH_CHECK();
+  }
+  AMG_TRY(coarse((const T*)W.lb[nl - 1], (T*)W.lx[nl - 1]));
+  for (int l = nl - 2; l >= 0; --l) {
+    const Level& L = H->L[l];
+    const int g = mgrid(H, L.n);
+    const T* xc = (const T*)W.lx[l + 1];
+    const T* sv = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
+    const T* rv = (const T*)W.lr[l];
+    if constexpr (sizeof(T) == 8) {
+      const SellView<double> v = view<double>(L.AP, L.AP.v64);
+      if (l == 0 && dots) {
+        AMG_DISPATCH_KPL(K, (k_m_post<KPL, double, double, double, double, true>
+                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0, Q,
+                                                        W.part, maxb, W.ticket, epi)));
+      } else if (l == 0) {
+        AMG_DISPATCH_KPL(K, (k_m_post<KPL, double, double, double, double, false>
+                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0, Q,
+                                                        W.part, maxb, W.ticket, epi)));
+      } else {
+        AMG_DISPATCH_KPL(K, (k_m_post<KPL, double, double, double, double, false>
+                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, (const double*)W.lb[l], sv,
+                                                        rv, L.agg, xc, (double*)W.lx[l], Q, W.part,
+                                                        maxb, W.ticket, epi)));
+      }
+    } else {
+      if (l == 0) {
+        const SellView<float> v = view<float>(L.AP, L.AP.v32);
+        if (dots) {
+          AMG_DISPATCH_KPL(K, (k_m_post<KPL, float, float, double, double, true>
+                               <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0,
+                                                          Q, W.part, maxb, W.ticket, epi)));
+        } else {
+          AMG_DISPATCH_KPL(K, (k_m_post<KPL, float, float, double, double, false>
+                               <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0,
+                                                          Q, W.part, maxb, W.ticket, epi)));
+        }
+      } else if (L.vstore == VAL_BF16) {
+        const SellView<__nv_bfloat16> v = view<__nv_bfloat16>(L.AP, L.AP.v16);
+        AMG_DISPATCH_KPL(K, (k_m_post<KPL, __nv_bfloat16, float, float, float, false>
+                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, (const float*)W.lb[l], sv,
+                                                        rv, L.agg, xc, (float*)W.lx[l], Q, W.part,
+                                                        maxb, W.ticket, epi)));
+      } else {
+        const SellView<float> v = view<float>(L.AP, L.AP.v32);
+        AMG_DISPATCH_KPL(K, (k_m_post<KPL, float, float, float, float, false>
+                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, (const float*)W.lb[l], sv,
+                                                        rv, L.agg, xc, (float*)W.lx[l], Q, W.part,
+                                                        maxb, W.ticket, epi)));
+      }
+    }
+    AMG_LAUNCH_CHECK();
+  }
+  return AMG_OK;
+}
+
+static int m_vcycle_any(const amg_handle* H, const MultiWs& W, const double* R0, double* Z0,
+                        bool dots, const double* Q, int beta_form, bool first, cudaStream_t s) {
+  if (H->opt.precision == AMG_PREC_F32)
+    return m_vcycle<float>(H, W, R0, Z0, dots, Q, beta_form, first, s);
+  return m_vcycle<double>(H, W, R0, Z0, dots, Q, beta_form, first, s);
+}
+
+// Workspace for K right-hand sides, kept in the handle (reallocated if K grows).
+static int multi_ws(amg_handle* H, int K, MultiWs** out) {
+  MultiWs* W = (MultiWs*)H->multi;
+  if (W && W->K >= K) {
+    W->K = K;
+    *out = W;
+    return AMG_OK;
+  }
+  if (W) {  // grow: drop the old buffers
+    Arena& ar = H->arena;
+    for (void* p : {(void*)W->R, (void*)W->Z, (void*)W->P, (void*)W->Q, (void*)W->cy,
+                    (void*)W->part, (void*)W->ticket, (void*)W->sc, (void*)W->nactive})
+      ar.release(p);
+    for (size_t l = 0; l < H->L.size(); ++l) {
+      ar.release(W->lb[l]);
+      ar.release(W->lx[l]);
+      ar.release(W->lr[l]);
+    }
+    delete[] W->lb;
+    delete[] W->lx;
+    delete[] W->lr;
+    if (W->sc_host) cudaFreeHost(W->sc_host);
+    delete W;
+    H->multi = nullptr;
+  }
+  W = new MultiWs();
+  H->multi = W;
+  W->K = K;
+  Arena& ar = H->arena;
+  const int64_t n = H->L[0].n;
+  const size_t vb = H->opt.precision == AMG_PREC_F32 ? 4 : 8;
+  AMG_TRY(ar.alloc_n(&W->R, n * K));
+  AMG_TRY(ar.alloc_n(&W->Z, n * K));
+  AMG_TRY(ar.alloc_n(&W->P, n * K));
+  AMG_TRY(ar.alloc_n(&W->Q, n * K));
+  AMG_TRY(ar.alloc_n(&W->cy, H->nco * K));
+  AMG_TRY(ar.alloc_n(&W->part, (int64_t)2 * H->red.max_blocks * K));
+  AMG_TRY(ar.alloc_n(&W->ticket, 1));
+  AMG_TRY(ar.alloc_n(&W->sc, K));
+  AMG_TRY(ar.alloc_n(&W->nactive, 1));
+  AMG_CUDA_TRY(cudaMemset(W->ticket, 0, sizeof(unsigned)));
+  AMG_CUDA_TRY(cudaMallocHost((void**)&W->sc_host, sizeof(Scal) * K));
+  const size_t nl = H->L.size();
+  W->lb = new void*[nl]();
+  W->lx = new void*[nl]();
+  W->lr = new void*[nl]();
+  for (size_t l = 0; l < nl; ++l) {
+    const size_t bytes = vb * (size_t)H->L[l].n * K;
+    AMG_TRY(ar.alloc(&W->lb[l], bytes));
+    AMG_TRY(ar.alloc(&W->lx[l], bytes));
+    AMG_TRY(ar.alloc(&W->lr[l], bytes));
+  }
+  *out = W;
+  return AMG_OK;
+}
+
+void multi_free(amg_handle* H) {
+  MultiWs* W = (MultiWs*)H->multi;
+  if (!W) return;
+  delete[] W->lb;
+  delete[] W->lx;
+  delete[] W->lr;
+  if (W->sc_host) cudaFreeHost(W->sc_host);
+  delete W;
+  H->multi = nullptr;
+}
+
+int vcycle_multi(amg_handle* H, int K, const double* R, double* Z, cudaStream_t s) {
+  MultiWs* W = nullptr;
+  AMG_TRY(multi_ws(H, K, &W));
+  return m_vcycle_any(H, *W, R, Z, false, nullptr, PCG_BETA_FR, true, s);
+}
+
+int pcg_multi_run(amg_handle* H, int K, const double* B, double* X, const pcg_options* o,
+                  pcg_stats* st, cudaStream_t s) {
+  MultiWs* W = nullptr;
+  AMG_TRY(multi_ws(H, K, &W));
+  const int64_t n = H->L[0].n;
+  const Level& L0 = H->L[0];
+  if (L0.A.row0) return AMG_ERR_UNSUPPORTED;  // batched handles: use pcg_solve_batch
+  int beta_form = o->beta_form;
+  if (beta_form == PCG_BETA_AUTO)
+    beta_form = H->opt.precision == AMG_PREC_F32 ? PCG_BETA_FLEXIBLE : PCG_BETA_FR;
+  const int maxb = H->red.max_blocks;
+  const SellView<double> A = view<double>(L0.A, L0.A.v64);
+  const int C = L0.A.C;
+  const int g = mgrid(H, n);
+  AMG_CUDA_TRY(cudaEventRecord(H->ev0, s));
+  AMG_CUDA_TRY(cudaMemsetAsync(W->nactive, 0, sizeof(int), s));
+  MultiInitEpi ie{W->sc, o->tol, o->maxit, W->nactive, 0};
+  AMG_DISPATCH_KPL(K, (k_m_residual<KPL><<<g, MROWS_BLOCK, 0, s>>>(A, C, K, B, X, W->R, W->part,
+                                                                  maxb, W->ticket, ie)));
+  AMG_LAUNCH_CHECK();
+  int act = 0;
+  auto read_act = [&]() -> int {
+    AMG_CUDA_TRY(cudaMemcpyAsync(&act, W->nactive, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return AMG_OK;
+  };
+  AMG_TRY(read_act());
+  MultiPqEpi pe{W->sc};
+  MultiRrEpi re{W->sc, o->tol, o->maxit, W->nactive};
+  int k = 0;
+  if (act > 0) {
+    AMG_TRY(m_vcycle_any(H, *W, W->R, W->Z, true, W->Q, beta_form, true, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(W->P, W->Z, sizeof(double) * n * K, cudaMemcpyDeviceToDevice, s));
+    for (;;) {
+      AMG_DISPATCH_KPL(K, (k_m_spmm_dot<KPL><<<g, MROWS_BLOCK, 0, s>>>(A, C, K, W->P, W->Q, W->part,
+                                                                      maxb, W->ticket, pe)));
+      AMG_LAUNCH_CHECK();
+      AMG_CUDA_TRY(cudaMemsetAsync(W->nactive, 0, sizeof(int), s));
+      AMG_DISPATCH_KPL(K, (k_m_update<KPL><<<g, MROWS_BLOCK, 0, s>>>(n, K, X, W->R, W->P, W->Q,
+                                                                    W->sc, W->part, maxb,
+                                                                    W->ticket, re)));
+      AMG_LAUNCH_CHECK();
+      ++k;
+      AMG_TRY(read_act());
+      if (act == 0 || k >= o->maxit) break;
+      AMG_TRY(m_vcycle_any(H, *W, W->R, W->Z, true, W->Q, beta_form, false, s));
+      AMG_DISPATCH_KPL(K, (k_m_p_update<KPL><<<g, MROWS_BLOCK, 0, s>>>(n, K, W->P, W->Z, W->sc)));
+      AMG_LAUNCH_CHECK();
+    }
+  }
+  AMG_CUDA_TRY(cudaEventRecord(H->ev1, s));
+  MultiInitEpi te{W->sc, o->tol, o->maxit, W->nactive, 1};
+  AMG_DISPATCH_KPL(K, (k_m_residual<KPL><<<g, MROWS_BLOCK, 0, s>>>(A, C, K, B, X, W->Z, W->part,
+                                                                  maxb, W->ticket, te)));
+  AMG_LAUNCH_CHECK();
+  AMG_CUDA_TRY(cudaMemcpyAsync(W->sc_host, W->sc, sizeof(Scal) * K, cudaMemcpyDeviceToHost, s));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  AMG_CUDA_TRY(cudaEventElapsedTime(&ms, H->ev0, H->ev1));
+  int worst = AMG_OK;
+  for (int c = 0; c < K; ++c) {
+    const Scal& S = W->sc_host[c];
+    const double bn = S.bb > 0.0 ? sqrt(S.bb) : 1.0;
+    if (st) {
+      st[c].iterations = S.iters;
+      st[c].status = S.status;
+      st[c].rel_residual = sqrt(S.rr) / bn;
+      st[c].true_rel_residual = sqrt(S.tr) / bn;
+      st[c].solve_ms = ms;
+    }
+    if (S.status < 0 && (worst >= 0 || S.status < worst)) worst = S.status;
+    if (S.status == AMG_NOT_CONVERGED && worst == AMG_OK) worst = AMG_NOT_CONVERGED;
+  }
+  return worst;
+}
+
+}  // namespace amg

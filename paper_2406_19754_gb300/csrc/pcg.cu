@@ -33,7 +33,7 @@ struct TrueResEpi {
 
 // r = b - A x with (r, r) and (b, b); mode 1 writes (r, r) to sc->zq only.
 template <int TPR, int MODE>
-__global__ void __launch_bounds__(SELL_BLOCK)
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_residual(SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
                double* __restrict__ r, Reduce red, PcgScalars* sc) {
   const Lanes<TPR> ln;
@@ -74,7 +74,7 @@ struct PqEpi {
 
 // q = A p and (p, q); the last block sets alpha = (r, z) / (p, q).
 template <int TPR>
-__global__ void __launch_bounds__(SELL_BLOCK)
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_spmv_dot(SellView<double> A, const double* __restrict__ p, double* __restrict__ q,
                Reduce red, PcgScalars* sc) {
   const Lanes<TPR> ln;

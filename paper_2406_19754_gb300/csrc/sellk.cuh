@@ -13,6 +13,9 @@
 namespace amg {
 
 constexpr int SELL_BLOCK = 256;  // threads per block (8 slices in flight)
+// 8 resident blocks per SM (64 warps, full occupancy): at most 32 registers,
+// which the streaming kernels need to keep enough loads in flight.
+#define SELL_MIN_BLOCKS 8
 
 template <int TPR>
 struct Lanes {
@@ -76,7 +79,18 @@ inline SellView<V> view(const Sell& A, const V* val) {
   v.sliceptr = A.sliceptr;
   v.col = A.col;
   v.val = val;
+  v.row0 = A.row0;
+  v.sys = A.sys;
   return v;
+}
+
+// Row handled by this lane in slice sl, or -1 (padding lane / sub-row lane).
+template <int TPR, typename V>
+__device__ __forceinline__ int64_t lane_row(const SellView<V>& A, int64_t sl,
+                                            const Lanes<TPR>& ln) {
+  constexpr int C = Lanes<TPR>::C;
+  const int64_t i = A.rbeg(sl, C) + ln.r;
+  return (ln.t == 0 && i < A.rend(sl, C)) ? i : -1;
 }
 
 // Grid for one-warp-per-slice kernels: enough blocks to fill the GPU, capped

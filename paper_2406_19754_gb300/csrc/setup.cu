@@ -10,6 +10,8 @@
 // reproducible run to run and against a sequential FP64 evaluation in the
 // same order.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 #include "sellk.cuh"
@@ -560,20 +562,34 @@ static int galerkin(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* 
 
 // ------------------------------------------------------------------ coarse Cholesky
 
-__global__ void k_dense(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
-                        double* a) {
-  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) a[i * n + j] = 0.0;
-    __syncthreads();
-    for (int64_t e = rowptr[i] + threadIdx.x; e < rowptr[i + 1]; e += blockDim.x)
-      a[i * n + col[e]] = val[e];
-    __syncthreads();
-  }
+// The coarsest matrix is block diagonal: one block (system) per CUDA block.
+// Block b covers rows [brow[b], brow[b+1]); its dense row-major copy, L^-1
+// and L^-T start at bmat[b].
+__global__ void k_dense_blocks(const int64_t* rowptr, const int32_t* col, const double* val,
+                               const int64_t* brow, const int64_t* bmat, double* dense,
+                               int* status) {
+  const int64_t r0 = brow[blockIdx.x], n = brow[blockIdx.x + 1] - r0;
+  double* a = dense + bmat[blockIdx.x];
+  for (int64_t t = threadIdx.x; t < n * n; t += blockDim.x) a[t] = 0.0;
+  __syncthreads();
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rowptr[r0 + i] + threadIdx.x; e < rowptr[r0 + i + 1]; e += blockDim.x) {
+      const int64_t j = col[e] - r0;
+      if (j >= 0 && j < n)
+        a[i * n + j] = val[e];
+      else
+        atomicExch(status, AMG_ERR_DEVICE_CHECK);  // an entry coupling two blocks
+    }
 }
 
-// Right-looking Cholesky in one block; a (row-major n x n) becomes L in its
-// lower triangle.  Then Linv = L^-1 (one column per thread) and its transpose.
-__global__ void k_cholesky(int n, double* a, double* Linv, double* LinvT, int* status) {
+// Right-looking Cholesky of each block; the dense copy becomes L in its lower
+// triangle.  Then L^-1 (one column per thread) and its transpose.
+__global__ void k_cholesky(const int64_t* brow, const int64_t* bmat, double* dense,
+                           double* Linv_all, double* LinvT_all, int* status) {
+  const int n = (int)(brow[blockIdx.x + 1] - brow[blockIdx.x]);
+  double* a = dense + bmat[blockIdx.x];
+  double* Linv = Linv_all + bmat[blockIdx.x];
+  double* LinvT = LinvT_all + bmat[blockIdx.x];
   __shared__ int ok;
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
@@ -703,7 +719,8 @@ static int build_ap(Arena& ar, Level& L, const int64_t* rp, const int32_t* ci, c
   k_ap_fill<<<g, 256, 0, s>>>(n, rp, ci, va, L.agg, rp_ap, ci_ap, va_ap);
   AMG_LAUNCH_CHECK();
   L.ap_nnz = total;
-  AMG_TRY(sell_from_csr(ar, n, L.nc, rp_ap, ci_ap, va_ap, L.A.C, L.A.tpr, L.AP, s));
+  AMG_TRY(sell_from_csr(ar, n, L.nc, rp_ap, ci_ap, va_ap, L.A.C, L.A.tpr, L.AP, s,
+                        L.sys_off.empty() ? nullptr : &L.sys_off));
   if (L.vstore != VAL_F64) AMG_TRY(sell_make_copies(ar, L.AP, L.vstore, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   ar.release(cnt);
@@ -711,6 +728,59 @@ static int build_ap(Arena& ar, Level& L, const int64_t* rp, const int32_t* ci, c
   ar.release(ci_ap);
   ar.release(va_ap);
   return AMG_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Threads per row (and so slice height 32/tpr) per level, chosen by timing the
+// level's smoother kernels in every layout; choices are remembered for the
+// process, keyed by (rows, 10 x entries per row, value type, batched).
+
+struct TuneKey {
+  int64_t n;
+  int nnz10;
+  int vstore;
+  bool batched;
+  bool operator<(const TuneKey& o) const {
+    if (n != o.n) return n < o.n;
+    if (nnz10 != o.nnz10) return nnz10 < o.nnz10;
+    if (vstore != o.vstore) return vstore < o.vstore;
+    return batched < o.batched;
+  }
+};
+
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;
+
+static bool tune_lookup(const TuneKey& k, int* tpr) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *tpr = it->second;
+  return true;
+}
+
+static void tune_store(const TuneKey& k, int tpr) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[k] = tpr;
+}
+
+static void release_sell(Arena& ar, Sell& A) {
+  for (void* p : {(void*)A.sliceptr, (void*)A.col, (void*)A.v64, (void*)A.v32, (void*)A.v16,
+                  (void*)A.row0, (void*)A.sys})
+    ar.release(p);
+  A = Sell();
+}
+
+static void release_level_ops(Arena& ar, Level& L) {
+  release_sell(ar, L.A);
+  release_sell(ar, L.AP);
+  ar.release(L.ah64);
+  ar.release(L.ah32);
+  ar.release(L.ah16);
+  L.ah64 = nullptr;
+  L.ah32 = nullptr;
+  L.ah16 = nullptr;
+  L.ap_nnz = 0;
 }
 
 // ------------------------------------------------------------------ driver
@@ -722,6 +792,16 @@ int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s) {
   AMG_LAUNCH_CHECK();
   if (L.ah64) AMG_TRY(build_ah(H->arena, L, H->num_sms, s));
   return AMG_OK;
+}
+
+// Largest system of a batched level (each keeps the coarsest level it would
+// get alone); the whole level otherwise.
+static int64_t largest_block(const Level& L, int64_t n) {
+  if (L.sys_off.size() < 2) return n;
+  int64_t m = 0;
+  for (size_t k = 0; k + 1 < L.sys_off.size(); ++k)
+    m = std::max(m, L.sys_off[k + 1] - L.sys_off[k]);
+  return m;
 }
 
 static int read_status(amg_handle* H, cudaStream_t s) {
@@ -740,6 +820,7 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
   H->L.emplace_back();
   H->L[0].n = A->n;
   H->L[0].nnz = A->nnz;
+  if (H->batched) H->L[0].sys_off = H->sys_off0;
   const int stride = 1 << o.sweeps;
   for (int l = 0;; ++l) {
     const int64_t n = H->L[l].n;
@@ -756,7 +837,7 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     AMG_LAUNCH_CHECK();
     k_smoother_scale<<<g1, 256, 0, s>>>(n, H->L[l].d, nullptr, H->L[l].s64, H->L[l].s32);
     AMG_LAUNCH_CHECK();
-    if (n <= o.max_coarse || l + 1 >= o.max_levels) {
+    if (largest_block(H->L[l], n) <= o.max_coarse || l + 1 >= o.max_levels) {
       ar.release(diag);
       break;
     }
@@ -837,6 +918,16 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     AMG_TRY(build_members(ar, n, L.agg, nc, stride, L.members, H->dev_status, sms, s));
     Level next;
     next.n = nc;
+    if (H->batched) {  // aggregates never span systems: system k starts at agg(first row)
+      next.sys_off.assign(H->nsys + 1, nc);
+      for (int k = 0; k < H->nsys; ++k) {
+        int32_t a = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&a, L.agg + L.sys_off[k], sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        next.sys_off[k] = a;
+      }
+    }
     AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, stride, nc, &next.rowptr, &next.col,
                      &next.val, &next.nnz, H->dev_status, sms, s));
     st = read_status(H, s);
@@ -844,47 +935,99 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     H->L.push_back(next);
   }
   // coarsest level: dense Cholesky and its inverse factor
+  // (block diagonal for batched systems: one dense factor per system)
   Level& Lc = H->L.back();
-  if (Lc.n > o.max_dense) return AMG_ERR_UNSUPPORTED;
+  if (largest_block(Lc, Lc.n) > o.max_dense) return AMG_ERR_UNSUPPORTED;
   H->nco = Lc.n;
   {
-    const int64_t m = Lc.n;
+    std::vector<int64_t> brow = Lc.sys_off.size() >= 2 ? Lc.sys_off
+                                                        : std::vector<int64_t>{0, Lc.n};
+    const int nb = (int)brow.size() - 1;
+    std::vector<int64_t> bmat(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) bmat[b + 1] = bmat[b] + (brow[b + 1] - brow[b]) * (brow[b + 1] - brow[b]);
+    H->nblk = nb;
+    H->cblk_row = brow;
     const int64_t* rp = H->L.size() == 1 ? A->rowptr : Lc.rowptr;
     const int32_t* ci = H->L.size() == 1 ? A->col : Lc.col;
     const double* va = H->L.size() == 1 ? A->val : Lc.val;
     double* dense = nullptr;
-    AMG_TRY(ar.alloc_n(&dense, m * m));
-    AMG_TRY(ar.alloc_n(&H->Linv, m * m));
-    AMG_TRY(ar.alloc_n(&H->LinvT, m * m));
-    k_dense<<<(unsigned)std::min<int64_t>(m, 1024), 256, 0, s>>>(m, rp, ci, va, dense);
+    AMG_TRY(ar.alloc_n(&dense, bmat.back()));
+    AMG_TRY(ar.alloc_n(&H->Linv, bmat.back()));
+    AMG_TRY(ar.alloc_n(&H->LinvT, bmat.back()));
+    AMG_TRY(ar.alloc_n(&H->d_brow, nb + 1));
+    AMG_TRY(ar.alloc_n(&H->d_bmat, nb + 1));
+    AMG_CUDA_TRY(cudaMemcpyAsync(H->d_brow, brow.data(), sizeof(int64_t) * (nb + 1),
+                                 cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(H->d_bmat, bmat.data(), sizeof(int64_t) * (nb + 1),
+                                 cudaMemcpyHostToDevice, s));
+    k_dense_blocks<<<nb, 256, 0, s>>>(rp, ci, va, H->d_brow, H->d_bmat, dense, H->dev_status);
     AMG_LAUNCH_CHECK();
-    k_cholesky<<<1, 1024, 0, s>>>((int)m, dense, H->Linv, H->LinvT, H->dev_status);
+    k_cholesky<<<nb, 1024, 0, s>>>(H->d_brow, H->d_bmat, dense, H->Linv, H->LinvT,
+                                   H->dev_status);
     AMG_LAUNCH_CHECK();
-    int st = read_status(H, s);
+    int st = read_status(H, s);  // synchronises: brow/bmat copies are done
     ar.release(dense);
     if (st < 0) return st;
   }
-  // sliced-ELL copies and V-cycle work vectors
+  // V-cycle work vectors (zeroed: the autotuner times kernels on them)
   const size_t vb = f32 ? sizeof(float) : sizeof(double);
+  for (size_t l = 0; l < H->L.size(); ++l) {
+    Level& L = H->L[l];
+    L.vstore = VAL_F64;
+    if (f32)
+      L.vstore = (o.bf16_from_level > 0 && (int)l >= o.bf16_from_level) ? VAL_BF16 : VAL_F32;
+    for (void** v : {&L.b, &L.x, &L.r}) {
+      AMG_TRY(ar.alloc(v, vb * (size_t)L.n));
+      AMG_CUDA_TRY(cudaMemsetAsync(*v, 0, vb * (size_t)L.n, s));
+    }
+  }
+  // sliced-ELL operators of every level, in the layout the options or the
+  // autotuner choose
+  const int64_t n0 = H->L[0].n;
+  double *tb = nullptr, *tz = nullptr;  // FP64 level-0 vectors for timing
+  if (o.autotune) {
+    AMG_TRY(ar.alloc_n(&tb, n0));
+    AMG_TRY(ar.alloc_n(&tz, n0));
+    AMG_CUDA_TRY(cudaMemsetAsync(tb, 0, sizeof(double) * n0, s));
+  }
   for (size_t l = 0; l < H->L.size(); ++l) {
     Level& L = H->L[l];
     const int64_t* rp = l == 0 ? A->rowptr : L.rowptr;
     const int32_t* ci = l == 0 ? A->col : L.col;
     const double* va = l == 0 ? A->val : L.val;
+    const bool smooth = l + 1 < H->L.size();  // a level with a coarser one
+    auto build = [&](int tpr) -> int {
+      AMG_TRY(sell_from_csr(ar, L.n, L.n, rp, ci, va, 32 / tpr, tpr, L.A, s,
+                            H->batched ? &L.sys_off : nullptr));
+      if (smooth) {
+        AMG_TRY(build_ah(ar, L, sms, s));
+        AMG_TRY(build_ap(ar, L, rp, ci, va, sms, s));
+      }
+      return AMG_OK;
+    };
     int tpr = o.threads_per_row > 0 ? o.threads_per_row : 1;
     if (o.slice_height > 0) tpr = 32 / o.slice_height;
-    AMG_TRY(sell_from_csr(ar, L.n, L.n, rp, ci, va, 32 / tpr, tpr, L.A, s));
-    L.vstore = VAL_F64;
-    if (f32)
-      L.vstore = (o.bf16_from_level > 0 && (int)l >= o.bf16_from_level) ? VAL_BF16 : VAL_F32;
-    if (l + 1 < H->L.size()) {  // smoothing operators of a level with a coarser one
-      AMG_TRY(build_ah(ar, L, sms, s));
-      AMG_TRY(build_ap(ar, L, rp, ci, va, sms, s));
+    if (o.autotune && smooth) {
+      const TuneKey key{L.n, (int)(10 * L.nnz / L.n), L.vstore, H->batched};
+      if (!tune_lookup(key, &tpr)) {
+        float best = 1e30f;
+        for (int cand : {1, 2, 4, 8}) {
+          AMG_TRY(build(cand));
+          float ms = 0.f;
+          AMG_TRY(time_level(H, (int)l, 3, tb, tz, &ms, s));
+          if (ms < best) {
+            best = ms;
+            tpr = cand;
+          }
+          release_level_ops(ar, L);
+        }
+        tune_store(key, tpr);
+      }
     }
-    AMG_TRY(ar.alloc((void**)&L.b, vb * (size_t)L.n));
-    AMG_TRY(ar.alloc((void**)&L.x, vb * (size_t)L.n));
-    AMG_TRY(ar.alloc((void**)&L.r, vb * (size_t)L.n));
+    AMG_TRY(build(tpr));
   }
+  ar.release(tb);
+  ar.release(tz);
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   return AMG_OK;
 }

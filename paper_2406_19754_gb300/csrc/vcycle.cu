@@ -23,7 +23,7 @@ namespace amg {
 // ------------------------------------------------------------------ kernels
 
 template <int TPR, typename V, typename T, typename BT>
-__global__ void __launch_bounds__(SELL_BLOCK)
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_pre(SellView<V> Ah, const BT* __restrict__ b, T* __restrict__ r) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(SELL_BLOCK)
        sl += nw) {
     const T acc =
         sell_row<TPR, T>(Ah, sl, ln, [&](int j) { return to_f(__ldg(b + j), T(0)); });
-    const int64_t i = sl * Lanes<TPR>::C + ln.r;
-    if (ln.t == 0 && i < Ah.n) r[i] = to_f(b[i], T(0)) - acc;
+    const int64_t i = lane_row(Ah, sl, ln);
+    if (i >= 0) r[i] = to_f(b[i], T(0)) - acc;
   }
 }
 
@@ -69,30 +69,50 @@ struct VcycleDotEpi {
 };
 
 template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT>
-__global__ void __launch_bounds__(SELL_BLOCK)
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_post(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,
            const T* __restrict__ r, const int32_t* __restrict__ agg, const T* __restrict__ xc,
-           XT* __restrict__ x, const double* __restrict__ q, Reduce red, PcgScalars* sc) {
+           XT* __restrict__ x, const double* __restrict__ q, Reduce red, PcgScalars* sc,
+           double* __restrict__ slice_part) {
+  // slice_part != null (batched systems): per-slice dot partials instead of
+  // one grid-wide reduction; they are reduced per system afterwards.
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double d[NDOT > 0 ? NDOT : 1];
+  constexpr int ND = NDOT > 0 ? NDOT : 1;
+  double d[ND];
 #pragma unroll
-  for (int k = 0; k < (NDOT > 0 ? NDOT : 1); ++k) d[k] = 0.0;
+  for (int k = 0; k < ND; ++k) d[k] = 0.0;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
        sl += nw) {
     const T acc = sell_row<TPR, T>(AP, sl, ln, [&](int J) { return __ldg(xc + J); });
-    const int64_t i = sl * Lanes<TPR>::C + ln.r;
-    if (ln.t == 0 && i < AP.n) {
+    const int64_t i = lane_row(AP, sl, ln);
+    double ds[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) ds[k] = 0.0;
+    if (i >= 0) {
       const T bi = to_f(b[i], T(0));
       const T si = s[i];
       const T yi = si * bi + xc[agg[i]];
       const XT zi = to_f(yi + si * (r[i] - acc), XT(0));
       x[i] = zi;
-      if (NDOT > 0) d[0] += (double)b[i] * (double)zi;
-      if (NDOT > 1) d[NDOT > 1 ? 1 : 0] += (double)zi * q[i];
+      if (NDOT > 0) ds[0] = (double)b[i] * (double)zi;
+      if (NDOT > 1) ds[NDOT > 1 ? 1 : 0] = (double)zi * q[i];
+    }
+    if constexpr (NDOT > 0) {
+      if (slice_part) {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) {
+          const double v = warp_sum(ds[k]);
+          if ((threadIdx.x & 31) == 0) slice_part[sl * 2 + k] = v;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NDOT; ++k) d[k] += ds[k];
+      }
     }
   }
-  if constexpr (NDOT > 0) grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
+  if constexpr (NDOT > 0)
+    if (!slice_part) grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
 }
 
 // Dots for the single-level case (the whole preconditioner is the coarse solve).
@@ -110,11 +130,59 @@ __global__ void k_dots_rz(int64_t n, const double* r, const double* z, const dou
   grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
 }
 
-// Coarsest level: x = L^-T (L^-1 b), one block, vectors staged in shared memory.
+// Per-slice (r, z) and (z, q) partials over the level-0 slices (batched
+// systems whose whole hierarchy is one level).
+template <int NDOT>
+__global__ void k_slice_dots(SellView<double> A, const double* r, const double* z,
+                             const double* q, double* slice_part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+       sl += nw) {
+    const int64_t b0 = A.rbeg(sl, 32), b1 = A.rend(sl, 32);
+    double d0 = 0.0, d1 = 0.0;
+    for (int64_t i = b0 + lane; i < b1; i += 32) {
+      d0 += r[i] * z[i];
+      if (NDOT > 1) d1 += z[i] * q[i];
+    }
+    d0 = warp_sum(d0);
+    if (NDOT > 1) d1 = warp_sum(d1);
+    if (lane == 0) {  // two slots per slice, as every batched reduction uses
+      slice_part[sl * 2] = d0;
+      if (NDOT > 1) slice_part[sl * 2 + 1] = d1;
+    }
+  }
+}
+
+static int slice_dots(const amg_handle* H, const double* r, const double* z, const double* q,
+                      int dots, double* slice_part, cudaStream_t s) {
+  // rbeg/rend with C = 32 are exact for system-aligned slices (row0 set)
+  const Level& L = H->L[0];
+  if (!L.A.row0) return AMG_ERR_ARG;
+  const SellView<double> v = view<double>(L.A, L.A.v64);
+  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  if (dots == 1)
+    k_slice_dots<1><<<grid, SELL_BLOCK, 0, s>>>(v, r, z, q, slice_part);
+  else
+    k_slice_dots<2><<<grid, SELL_BLOCK, 0, s>>>(v, r, z, q, slice_part);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+// Coarsest level: x = L^-T (L^-1 b) for each diagonal block (one CUDA block
+// per block, vectors staged in shared memory).
 template <typename BT, typename XT>
-__global__ void k_coarse(int n, const double* __restrict__ Linv, const double* __restrict__ LinvT,
-                         const BT* __restrict__ b, XT* __restrict__ x) {
+__global__ void k_coarse(const int64_t* __restrict__ brow, const int64_t* __restrict__ bmat,
+                         const double* __restrict__ Linv_all,
+                         const double* __restrict__ LinvT_all, const BT* __restrict__ b_all,
+                         XT* __restrict__ x_all) {
   extern __shared__ double csh[];
+  const int64_t r0 = brow[blockIdx.x];
+  const int n = (int)(brow[blockIdx.x + 1] - r0);
+  const double* Linv = Linv_all + bmat[blockIdx.x];
+  const double* LinvT = LinvT_all + bmat[blockIdx.x];
+  const BT* b = b_all + r0;
+  XT* x = x_all + r0;
   double* bs = csh;
   double* ys = csh + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = (double)b[i];
@@ -123,7 +191,7 @@ __global__ void k_coarse(int n, const double* __restrict__ Linv, const double* _
   for (int i = w; i < n; i += nw) {
     double acc = 0.0;
     const double* row = Linv + (int64_t)i * n;
-    for (int k = lane; k <= i; k += 32) acc += row[k] * bs[k];
+    for (int k = lane; k <= i; k += 32) acc = fma(row[k], bs[k], acc);
     acc = warp_sum(acc);
     if (lane == 0) ys[i] = acc;
   }
@@ -131,7 +199,7 @@ __global__ void k_coarse(int n, const double* __restrict__ Linv, const double* _
   for (int k = w; k < n; k += nw) {
     double acc = 0.0;
     const double* row = LinvT + (int64_t)k * n;
-    for (int i = k + lane; i < n; i += 32) acc += row[i] * ys[i];
+    for (int i = k + lane; i < n; i += 32) acc = fma(row[i], ys[i], acc);
     acc = warp_sum(acc);
     if (lane == 0) x[k] = (XT)acc;
   }
@@ -141,9 +209,10 @@ __global__ void k_coarse(int n, const double* __restrict__ Linv, const double* _
 
 template <typename BT, typename XT>
 static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s) {
-  const int n = (int)H->nco;
-  const size_t sm = sizeof(double) * 2 * (size_t)n;  // n <= 3072 keeps this under 48 KB
-  k_coarse<BT, XT><<<1, 1024, sm, s>>>(n, H->Linv, H->LinvT, b, x);
+  int64_t m = 0;  // largest block; <= max_dense <= 3072 keeps 2m doubles under 48 KB
+  for (int k = 0; k < H->nblk; ++k) m = std::max(m, H->cblk_row[k + 1] - H->cblk_row[k]);
+  const size_t sm = sizeof(double) * 2 * (size_t)m;
+  k_coarse<BT, XT><<<H->nblk, 1024, sm, s>>>(H->d_brow, H->d_bmat, H->Linv, H->LinvT, b, x);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -160,12 +229,13 @@ static int launch_pre(const amg_handle* H, const Level& L, const V* ah, const BT
 
 template <typename V, typename T, typename BT, typename XT, int NDOT>
 static int launch_post(const amg_handle* H, const Level& L, const V* ap, const BT* b,
-                       const T* xc, XT* x, const double* q, cudaStream_t s) {
+                       const T* xc, XT* x, const double* q, cudaStream_t s,
+                       double* slice_part) {
   const int grid = sell_grid(L.AP.nslices, H->num_sms);
   const SellView<V> v = view<V>(L.AP, ap);
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
   AMG_DISPATCH_TPR(L.AP.tpr, (k_post<TPR, V, T, BT, XT, NDOT><<<grid, SELL_BLOCK, 0, s>>>(
-                                 v, b, sc, (const T*)L.r, L.agg, xc, x, q, H->red, H->sc)));
+                                 v, b, sc, (const T*)L.r, L.agg, xc, x, q, H->red, H->sc, slice_part)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -187,13 +257,13 @@ static int pre_f32(const amg_handle* H, const Level& L, const BT* b, float* r, c
 
 template <typename T, typename BT, typename XT, int NDOT>
 static int post_any(const amg_handle* H, const Level& L, const BT* b, const T* xc, XT* x,
-                    const double* q, cudaStream_t s) {
+                    const double* q, cudaStream_t s, double* slice_part = nullptr) {
   if constexpr (sizeof(T) == 8) {
-    return launch_post<double, T, BT, XT, NDOT>(H, L, L.AP.v64, b, xc, x, q, s);
+    return launch_post<double, T, BT, XT, NDOT>(H, L, L.AP.v64, b, xc, x, q, s, slice_part);
   } else {
     if (L.vstore == VAL_BF16)
-      return launch_post<__nv_bfloat16, T, BT, XT, NDOT>(H, L, L.AP.v16, b, xc, x, q, s);
-    return launch_post<float, T, BT, XT, NDOT>(H, L, L.AP.v32, b, xc, x, q, s);
+      return launch_post<__nv_bfloat16, T, BT, XT, NDOT>(H, L, L.AP.v16, b, xc, x, q, s, slice_part);
+    return launch_post<float, T, BT, XT, NDOT>(H, L, L.AP.v32, b, xc, x, q, s, slice_part);
   }
 }
 
@@ -251,6 +321,17 @@ static double bytes_post(const Level& L, double mb, double vb, double ib, double
   return (double)L.ap_nnz * mb + (double)L.n * (ib + vb + vb + 4.0 + ob) + (double)L.nc * vb;
 }
 
+// Triangles of L^-1 and L^-T read by the coarse solve (lower/upper halves of
+// every diagonal block).
+static double coarse_factor_bytes(const amg_handle* H) {
+  double t = 0.0;
+  for (int k = 0; k < H->nblk; ++k) {
+    const double m = (double)(H->cblk_row[k + 1] - H->cblk_row[k]);
+    t += m * (m + 1.0) * 8.0;  // two triangles of m(m+1)/2 doubles
+  }
+  return t;
+}
+
 #define PROF_BEGIN(lvl, kind, bytes) \
   if (prof) AMG_TRY(prof->begin((lvl), (kind), (bytes)))
 #define PROF_END() \
@@ -258,7 +339,7 @@ static double bytes_post(const Level& L, double mb, double vb, double ib, double
 
 template <typename T>
 static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int dots,
-                         const double* q, cudaStream_t s, Prof* prof) {
+                         const double* q, cudaStream_t s, Prof* prof, double* slice_part) {
   const int nl = (int)H->L.size();
   const double vb = sizeof(T);
   auto mbytes = [&](const Level& L) {
@@ -266,10 +347,12 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
   };
   if (nl == 1) {
     const double m = (double)H->nco;
-    PROF_BEGIN(0, 3, m * m * 8.0 + m * 16.0);
+    PROF_BEGIN(0, 3, coarse_factor_bytes(H) + m * 16.0);
     AMG_TRY(coarse_solve<double, double>(H, r0, z0, s));
     PROF_END();
-    if (dots > 0) {
+    if (dots > 0 && slice_part) {
+      AMG_TRY(slice_dots(H, r0, z0, q, dots, slice_part, s));
+    } else if (dots > 0) {
       const int grid = grid_for(H->L[0].n, 256, H->num_sms, 8);
       if (dots == 1)
         k_dots_rz<1><<<grid, 256, 0, s>>>(H->L[0].n, r0, z0, q, H->red, H->sc);
@@ -300,7 +383,7 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
   }
   {
     const double m = (double)H->nco;
-    PROF_BEGIN(nl - 1, 3, m * m * 8.0 + m * 2.0 * vb);
+    PROF_BEGIN(nl - 1, 3, coarse_factor_bytes(H) + m * 2.0 * vb);
     AMG_TRY((coarse_solve<T, T>(H, (const T*)H->L[nl - 1].b, (T*)H->L[nl - 1].x, s)));
     PROF_END();
   }
@@ -316,20 +399,64 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
   PROF_BEGIN(0, 2, bytes_post(L0, mbytes(L0), vb, 8.0, 8.0));
   int rc;
   if (dots == 0)
-    rc = post_any<T, double, double, 0>(H, L0, r0, xc, z0, q, s);
+    rc = post_any<T, double, double, 0>(H, L0, r0, xc, z0, q, s, slice_part);
   else if (dots == 1)
-    rc = post_any<T, double, double, 1>(H, L0, r0, xc, z0, q, s);
+    rc = post_any<T, double, double, 1>(H, L0, r0, xc, z0, q, s, slice_part);
   else
-    rc = post_any<T, double, double, 2>(H, L0, r0, xc, z0, q, s);
+    rc = post_any<T, double, double, 2>(H, L0, r0, xc, z0, q, s, slice_part);
   AMG_TRY(rc);
   PROF_END();
   return AMG_OK;
 }
 
 int vcycle_run(const amg_handle* H, const double* r, double* z, int dots, const double* q,
+               cudaStream_t s, double* slice_part) {
+  if (H->opt.precision == AMG_PREC_F32)
+    return vcycle_levels<float>(H, r, z, dots, q, s, nullptr, slice_part);
+  return vcycle_levels<double>(H, r, z, dots, q, s, nullptr, slice_part);
+}
+
+// Device time of one pre- plus one post-smoothing pass of level l in its
+// current layout (plus the FP64 SpMV of the PCG on level 0), averaged over
+// `reps` after one warm-up.  b64/z64: FP64 level-0 vectors.
+int time_level(const amg_handle* H, int l, int reps, const double* b64, double* z64, float* ms,
                cudaStream_t s) {
-  if (H->opt.precision == AMG_PREC_F32) return vcycle_levels<float>(H, r, z, dots, q, s, nullptr);
-  return vcycle_levels<double>(H, r, z, dots, q, s, nullptr);
+  const Level& L = H->L[l];
+  const bool f32 = H->opt.precision == AMG_PREC_F32;
+  auto once = [&]() -> int {
+    if (!f32) {
+      const double* b = l == 0 ? b64 : (const double*)L.b;
+      double* x = l == 0 ? z64 : (double*)L.x;
+      AMG_TRY((launch_pre<double, double, double>(H, L, L.ah64, b, (double*)L.r, s)));
+      AMG_TRY((post_any<double, double, double, 0>(H, L, b, (const double*)H->L[l + 1].x, x,
+                                                    nullptr, s)));
+    } else if (l == 0) {
+      AMG_TRY(pre_f32<double>(H, L, b64, (float*)L.r, s));
+      AMG_TRY((post_any<float, double, double, 0>(H, L, b64, (const float*)H->L[1].x, z64,
+                                                   nullptr, s)));
+    } else {
+      AMG_TRY(pre_f32<float>(H, L, (const float*)L.b, (float*)L.r, s));
+      AMG_TRY((post_any<float, float, float, 0>(H, L, (const float*)L.b,
+                                                 (const float*)H->L[l + 1].x, (float*)L.x,
+                                                 nullptr, s)));
+    }
+    if (l == 0) AMG_TRY(sell_spmv64(L.A, 1.0, b64, 0.0, z64, H->num_sms, s));
+    return AMG_OK;
+  };
+  cudaEvent_t e0, e1;
+  AMG_CUDA_TRY(cudaEventCreate(&e0));
+  AMG_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = once();
+  if (rc == AMG_OK) rc = cudaEventRecord(e0, s) == cudaSuccess ? AMG_OK : AMG_ERR_CUDA;
+  for (int k = 0; k < reps && rc == AMG_OK; ++k) rc = once();
+  if (rc == AMG_OK) rc = cudaEventRecord(e1, s) == cudaSuccess ? AMG_OK : AMG_ERR_CUDA;
+  if (rc == AMG_OK) rc = cudaEventSynchronize(e1) == cudaSuccess ? AMG_OK : AMG_ERR_CUDA;
+  float t = 0.f;
+  if (rc == AMG_OK) rc = cudaEventElapsedTime(&t, e0, e1) == cudaSuccess ? AMG_OK : AMG_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / (reps > 0 ? reps : 1);
+  return rc;
 }
 
 int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_time* out,
@@ -337,8 +464,8 @@ int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_t
   Prof prof;
   prof.s = s;
   int rc = H->opt.precision == AMG_PREC_F32
-               ? vcycle_levels<float>(H, r, z, 0, nullptr, s, &prof)
-               : vcycle_levels<double>(H, r, z, 0, nullptr, s, &prof);
+               ? vcycle_levels<float>(H, r, z, 0, nullptr, s, &prof, nullptr)
+               : vcycle_levels<double>(H, r, z, 0, nullptr, s, &prof, nullptr);
   AMG_TRY(rc);
   AMG_TRY(prof.finish());
   const int m = (int)prof.rec.size();

@@ -239,3 +239,22 @@ def test_allocation_failure_is_clean(amg):
     lib.amg_debug_fail_alloc_after(-1)
     H = m.Hierarchy(*A)  # the library still works afterwards
     assert H.levels >= 2
+
+
+def test_autotuned_layouts_keep_results(amg, orc):
+    # the autotuner only changes slice height / threads per row: the hierarchy
+    # stays bit-exact and the V-cycle agrees to rounding
+    A = diffusion3d(np.exp(gaussian_field((24, 20, 16), 2.0, 4.0, 13)))
+    n = 24 * 20 * 16
+    H = amg.Hierarchy(*_dev(A), autotune=1, max_coarse=50)
+    Ho = orc.Hierarchy(A, max_coarse=50)
+    assert H.levels == Ho.levels
+    for l in range(1, H.levels):
+        assert np.array_equal(_np(H.level_export(l)["val"]), Ho.level_csr(l)[2])
+    r = uniform01(5, n)
+    z = _np(H.vcycle(torch.as_tensor(r, device="cuda")))
+    zo = Ho.vcycle(r)
+    assert np.linalg.norm(z - zo) <= 1e-13 * np.linalg.norm(zo)
+    _, info = H.pcg(torch.as_tensor(r, device="cuda"), tol=1e-8)
+    _, io = orc.pcg(A, r, tol=1e-8, hier=Ho)
+    assert info["status"] == 0 and abs(info["iterations"] - io["iterations"]) <= 1

@@ -342,3 +342,50 @@ def test_pcg_amg_poisson_32(orc, beta_form):
     r = b - to_scipy(A) @ x
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1.01e-6
     assert 10 <= info["iterations"] <= 40
+
+
+# ------------------------------------------------------------------ batched systems
+
+def _batch_systems():
+    return [poisson3d(5, 4, 3), diffusion3d(np.exp(gaussian_field((4, 5, 6), 1.5, 2.0, 31))),
+            poisson3d(6), random_spd_graph(40, 0.1, 77, positive_offdiag=True)]
+
+
+def test_block_diagonal_hierarchy_gives_block_diagonal_vcycle(orc):
+    A, offs = orc.block_diag(_batch_systems())
+    H = orc.Hierarchy(A, max_coarse=8)
+    assert H.levels >= 3
+    B = dense_operator(H.vcycle, offs[-1])
+    for a in range(len(offs) - 1):
+        for c in range(len(offs) - 1):
+            blk = B[offs[a]:offs[a + 1], offs[c]:offs[c + 1]]
+            if a != c:
+                assert np.all(blk == 0.0)  # exactly: every operator is block diagonal
+    for l in range(H.levels - 1):  # no aggregate spans two systems
+        agg = H.level_agg(l)
+        sysof = np.searchsorted(offs[1:], np.arange(offs[-1]), side="right") if l == 0 else None
+        if sysof is not None:
+            for I in range(H.level_n(l + 1)):
+                assert len(set(sysof[agg == I])) == 1
+
+
+def test_block_pcg_solves_each_block(orc):
+    systems = _batch_systems()
+    A, offs = orc.block_diag(systems)
+    H = orc.Hierarchy(A, max_coarse=8)
+    for k, S in enumerate(systems):
+        n = offs[k + 1] - offs[k]
+        b = uniform01(50 + k, n)
+        x, info = orc.pcg_block(H, offs[k], offs[k + 1], b, tol=1e-10)
+        assert info["status"] == 0
+        np.testing.assert_allclose(x, np.linalg.solve(dense(S), b), rtol=1e-8)
+    # a single block is the plain solve
+    S = systems[2]
+    b = uniform01(9, 216)
+    Hs = orc.Hierarchy(S, max_coarse=8)
+    A1, o1 = orc.block_diag([S])
+    H1 = orc.Hierarchy(A1, max_coarse=8)
+    xa, ia = orc.pcg(S, b, tol=1e-10, hier=Hs)
+    xb, ib = orc.pcg_block(H1, 0, 216, b, tol=1e-10)
+    assert ia["iterations"] == ib["iterations"]
+    np.testing.assert_allclose(xa, xb, rtol=1e-13)
