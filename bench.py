@@ -54,6 +54,9 @@ def _args():
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
     ap.add_argument("--workload", choices=["poisson", "diffusion", "batch"], default="poisson")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--tail-rows", type=int, default=None,
+                    help="levels with at most this many rows run as one persistent launch "
+                         "(0 = one launch per step; default: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -264,10 +267,13 @@ def run_ours(a):
     b = torch.as_tensor(b_host, device=dev)
     x = torch.zeros_like(b)
 
+    tail = {} if a.tail_rows is None else {"tail_rows": a.tail_rows}
+
     def make_hierarchy():
         if batch:
-            return amg.BatchHierarchy(Ad, precision=a.precision, autotune=int(a.autotune))
-        return amg.Hierarchy(*Ad, precision=a.precision, autotune=int(a.autotune))
+            return amg.BatchHierarchy(Ad, precision=a.precision, autotune=int(a.autotune),
+                                      **tail)
+        return amg.Hierarchy(*Ad, precision=a.precision, autotune=int(a.autotune), **tail)
 
     def solve(bv, xv):
         if batch:
@@ -319,18 +325,26 @@ def run_ours(a):
     it = iters[-1]
     assert info["status"] == 0, info
 
-    # our kernel launches per solve (see pcg.cu, batch.cu, vcycle.cu)
-    V = 2 if nl == 1 else 3 * (nl - 1) + 1
-    if batch:
-        launches = (2 + (V + 5) + (it - 1) * (V + 6) + 2) * a.steps
-    else:
-        launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1) * a.steps
-
     # per-kernel V-cycle timing (CUDA events on the launching stream)
     agg = {}
     for _ in range(3):
         H.vcycle_profile(b)
     reps = 5
+    _, recs = H.vcycle_profile(b)
+
+    # our kernel launches per solve (see pcg.cu, batch.cu, vcycle.cu, tail.cu):
+    # one per V-cycle profile record, plus the second phase of a coarse solve
+    # over a block larger than 1024 rows and the level-0 dot kernel of a
+    # one-level hierarchy
+    V = len(recs)
+    if any(r_["kind"] == "coarse" for r_ in recs) and H.level_info(nl - 1)[0] > 1024:
+        V += 1
+    if nl == 1:
+        V += 1
+    if batch:
+        launches = (2 + (V + 5) + (it - 1) * (V + 6) + 2) * a.steps
+    else:
+        launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1) * a.steps
     for _ in range(reps):
         _, recs = H.vcycle_profile(b)
         for r_ in recs:
@@ -405,6 +419,7 @@ def run_ours(a):
                        "level_rows": [lv[0] for lv in levels],
                        "operator_complexity": round(oc, 4), "iterations": it,
                        "precision": a.precision, "autotune": bool(a.autotune),
+                       "tail_rows": int(H.opts.tail_rows),
                        "rhs": "uniform[0,1) seed %d" % RHS_SEED,
                        "l2": "inputs larger than L2 (matrix %.2f GB)" % (12.0 * nnz / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},

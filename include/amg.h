@@ -79,13 +79,21 @@ typedef struct amg_options {
   int max_levels;        /* level cap, default 30 */
   int64_t max_coarse;    /* stop once a level has <= max_coarse rows, default 200 */
   double stall_ratio;    /* stop when n_{l+1} > stall_ratio * n_l, default 0.9 */
-  int64_t max_dense;     /* largest coarsest level factored densely, default 4096 */
+  int64_t max_dense;     /* largest coarsest block (system) factored densely,
+                            default 8192, at most 16384 */
   int precision;         /* AMG_PREC_F64 (default) or AMG_PREC_F32 */
   int bf16_from_level;   /* with F32: levels >= this keep BF16 values; 0 = off */
   int slice_height;      /* sliced-ELL slice height 8/16/32/64; 0 = default 32 */
   int threads_per_row;   /* 1/2/4/8 threads per row; 0 = default */
   int autotune;          /* 1: choose slice height / threads per row per level by
                             timing the kernels at setup */
+  int64_t tail_rows;     /* levels (other than level 0) with at most this many
+                            rows, and the coarsest solve, run as one persistent
+                            launch instead of one launch per step: one CTA when
+                            the largest of them has at most 16384 rows (and the
+                            coarsest level is one block), else a cooperative
+                            grid with bounded grid barriers.  Same results bit
+                            for bit.  0 = off; default 4096 */
 } amg_options;
 
 /* PCG controls (Sec. 3, psb_krylov arguments). */
@@ -217,13 +225,82 @@ int amg_batch_info(const amg_handle* H, int* nsys, int64_t* row_offsets);
 int pcg_solve_batch(amg_handle* H, const double* b, double* x, const pcg_options* o,
                     pcg_stats* st, amg_stream_t stream);
 
+/* ----------------------------------------------------------- learned smoother weights */
+/*
+ * A 9 -> 32 -> 32 -> 1 MLP (GELU hidden layers, sigmoid output clamped to
+ * [1e-3, 1)) maps each row's stencil features to the l1-Jacobi damping weight
+ * omega_i, so s_i = omega_i / d_i stays an A-convergent smoother and the
+ * V-cycle stays SPD (Sec. 2.3, l1-Jacobi; the network itself is not in the
+ * paper).  Weights are FP32 on the device; 1409 parameters laid out as
+ * W1[32][9], b1[32], W2[32][32], b2[32], W3[32], b3.
+ */
+typedef struct mlp_handle mlp_handle;
+
+/* Number of parameters (1409). */
+int mlp_num_params(void);
+
+/* New network with N(0, 1/fan_in) weights from splitmix64 stream `seed`,
+ * zero biases and output bias 4 (omega ~ 0.98).  Synchronous. */
+int mlp_create(uint64_t seed, mlp_handle** M);
+int mlp_destroy(mlp_handle* M);
+
+/* Copy the parameters to / from host float[1409] (set also resets the Adam
+ * state and the accumulated gradient).  Synchronous. */
+int mlp_get_params(const mlp_handle* M, float* host);
+int mlp_set_params(mlp_handle* M, const float* host);
+
+/* Accumulated gradient (host double[1409]).  Synchronous. */
+int mlp_get_grad(const mlp_handle* M, double* host);
+
+/*
+ * Nine features per row of a 7-point operator on an nx x ny x nz grid with
+ * lexicographic rows (x fastest): a_ij / a_ii towards -x, +x, -y, +y, -z, +z
+ * (0 where absent), sum_{j!=i} |a_ij| / a_ii, log(max |a_ij| / min |a_ij|)
+ * over present neighbours, and the neighbour count / 6.  A: device CSR with
+ * A->n == nx*ny*nz.  feat: device float[n][9].  Asynchronous.
+ */
+int mlp_features(const amg_csr* A, int64_t nx, int64_t ny, int64_t nz, float* feat,
+                 amg_stream_t stream);
+
+/* omega[i] = network(feat[i]) for n rows (device float arrays).  Asynchronous. */
+int mlp_forward(const mlp_handle* M, int64_t n, const float* feat, float* omega,
+                amg_stream_t stream);
+
+/*
+ * Gradient of sum_i domega[i] * omega[i] with respect to the parameters
+ * (device float feat[n][9], domega[n]); added to the accumulated gradient if
+ * accumulate != 0, else replaces it.  Summed in FP64 in a fixed order
+ * (reproducible).  Asynchronous.
+ */
+int mlp_backward(mlp_handle* M, int64_t n, const float* feat, const float* domega,
+                 int accumulate, amg_stream_t stream);
+
+/* One Adam step (Kingma & Ba) on grad_scale * accumulated gradient, then
+ * clears the gradient.  Asynchronous. */
+int mlp_adam_step(mlp_handle* M, double lr, double beta1, double beta2, double eps,
+                  double grad_scale, amg_stream_t stream);
+
+/*
+ * Two-grid loss of the level-0 smoother weights currently set on H and its
+ * gradient: L = mean_j log(||E^K e0_j||_A / ||e0_j||_A) / K with
+ * E = S (I - P A_1^-1 P^T A) S, S = I - diag(s) A (Eq. amg with two levels).
+ * A_1^-1 is applied by PCG-AMG on levels >= 1 to 1e-12 (exactly when level 1
+ * is the coarsest).  e0: device float64[nsamples][n0] initial errors.
+ * loss: host.  domega: device float[n0] receiving dL/domega, or NULL.  Needs
+ * >= 2 levels (AMG_ERR_UNSUPPORTED otherwise).  The first call builds the
+ * inner solver.  Synchronous.
+ */
+int amg_twogrid_loss(amg_handle* H, int nsamples, int ncycles, const double* e0, double* loss,
+                     float* domega, amg_stream_t stream);
+
 /* ----------------------------------------------------------- inspection */
 
 /* One V-cycle kernel launch timed by amg_vcycle_profile. */
 typedef struct amg_kernel_time {
   int level;     /* hierarchy level */
   int kind;      /* 0 pre-smooth+residual, 1 restriction, 2 prolongation+post-smooth,
-                    3 coarsest-level Cholesky solve */
+                    3 coarsest-level Cholesky solve, 4 the persistent launch of
+                    levels >= `level` (all their steps and the coarsest solve) */
   double bytes;  /* algorithmic bytes: each matrix entry (value + int32 column) and
                     each vector entry read or written once */
   double ms;     /* device time between CUDA events around the launch */
@@ -294,6 +371,17 @@ int amg_pairwise_match_noalloc(const amg_csr* A, int32_t* mate, int* rounds,
  * paths without faulting a GPU.
  */
 int amg_debug_fail_alloc_after(long count);
+
+/*
+ * Barrier-timeout injection for the persistent small-level launch (the
+ * `tail_rows` option): while `on` is 1, that launch's grid barrier waits for
+ * one arrival that never comes, every CTA gives up after 10 ms, and the
+ * next pcg_solve / pcg_solve_batch returns AMG_ERR_DEVICE_CHECK (clearing
+ * the failure state).  No GPU fault is involved: the waits are bounded and
+ * the kernel returns.  No counterpart in the paper; used to test the
+ * timeout path.  Errors: AMG_ERR_ARG (H NULL).
+ */
+int amg_debug_tail_timeout(amg_handle* H, int on);
 
 #ifdef __cplusplus
 }

@@ -235,7 +235,7 @@ class Hierarchy:
     """The oracle's AMG hierarchy (levels, aggregates, smoother scales, coarse factor)."""
 
     def __init__(self, A, sweeps=2, max_coarse=200, max_levels=30, stall=0.9,
-                 max_dense=4096, omega=None, systems=None):
+                 max_dense=8192, omega=None, systems=None):
         """systems: row offsets (nsys + 1) of independent systems stacked block
         diagonally in A; coarsening then stops when each has <= max_coarse rows."""
         n, rp, ci, v = csr_args(A)

@@ -154,7 +154,7 @@ class Hierarchy:
         cnt = C.c_int()
         _check(self._lib.amg_vcycle_profile(self.h, _ptr(r), _ptr(z), recs, 256, C.byref(cnt),
                                             _stream(stream)), "amg_vcycle_profile")
-        kinds = ("pre", "restrict", "post", "coarse")
+        kinds = ("pre", "restrict", "post", "coarse", "tail")
         out = [dict(level=k.level, kind=kinds[k.kind], bytes=k.bytes, ms=k.ms)
                for k in recs[:min(cnt.value, 256)]]
         return z, out

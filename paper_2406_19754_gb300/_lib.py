@@ -35,7 +35,8 @@ class AmgOptions(C.Structure):
     _fields_ = [("sweeps", C.c_int), ("max_levels", C.c_int), ("max_coarse", C.c_int64),
                 ("stall_ratio", C.c_double), ("max_dense", C.c_int64), ("precision", C.c_int),
                 ("bf16_from_level", C.c_int), ("slice_height", C.c_int),
-                ("threads_per_row", C.c_int), ("autotune", C.c_int)]
+                ("threads_per_row", C.c_int), ("autotune", C.c_int),
+                ("tail_rows", C.c_int64)]
 
 
 class PcgOptions(C.Structure):
@@ -73,12 +74,25 @@ SIGNATURES = {
                                   C.POINTER(_P)]),
     "amg_batch_info": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "pcg_solve_batch": (C.c_int, [_P, _P, _P, C.POINTER(PcgOptions), C.POINTER(PcgStats), _P]),
+    "mlp_num_params": (C.c_int, []),
+    "mlp_create": (C.c_int, [C.c_uint64, C.POINTER(_P)]),
+    "mlp_destroy": (C.c_int, [_P]),
+    "mlp_get_params": (C.c_int, [_P, _P]),
+    "mlp_set_params": (C.c_int, [_P, _P]),
+    "mlp_get_grad": (C.c_int, [_P, _P]),
+    "mlp_features": (C.c_int, [C.POINTER(AmgCsr), C.c_int64, C.c_int64, C.c_int64, _P, _P]),
+    "mlp_forward": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
+    "mlp_backward": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int, _P]),
+    "mlp_adam_step": (C.c_int, [_P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                C.c_double, _P]),
+    "amg_twogrid_loss": (C.c_int, [_P, C.c_int, C.c_int, _P, C.POINTER(C.c_double), _P, _P]),
     "amg_num_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "amg_level_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "amg_level_export": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "amg_pairwise_match": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_pairwise_match_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_debug_fail_alloc_after": (C.c_int, [C.c_long]),
+    "amg_debug_tail_timeout": (C.c_int, [_P, C.c_int]),
 }
 
 _lib = None

@@ -15,12 +15,13 @@ int amg_default_options(amg_options* o) {
   o->max_levels = 30;
   o->max_coarse = 200;
   o->stall_ratio = 0.9;
-  o->max_dense = 2048;
+  o->max_dense = 8192;
   o->precision = AMG_PREC_F64;
   o->bf16_from_level = 0;
   o->slice_height = 0;
   o->threads_per_row = 0;
   o->autotune = 0;
+  o->tail_rows = 4096;
   return AMG_OK;
 }
 
@@ -52,11 +53,11 @@ const char* amg_status_string(int s) {
 
 static int check_options(const amg_options& o) {
   if (o.sweeps < 1 || o.sweeps > 3) return AMG_ERR_ARG;
-  if (o.max_levels < 1 || o.max_coarse < 1 || o.max_dense < 1 || o.max_dense > 3072)
+  if (o.max_levels < 1 || o.max_coarse < 1 || o.max_dense < 1 || o.max_dense > 16384)
     return AMG_ERR_ARG;
   if (!(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0)) return AMG_ERR_ARG;
   if (o.precision != AMG_PREC_F64 && o.precision != AMG_PREC_F32) return AMG_ERR_ARG;
-  if (o.bf16_from_level < 0) return AMG_ERR_ARG;
+  if (o.bf16_from_level < 0 || o.tail_rows < 0) return AMG_ERR_ARG;
   const int C = o.slice_height, t = o.threads_per_row;
   if (C != 0 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
   if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8) return AMG_ERR_ARG;
@@ -73,9 +74,11 @@ static int check_csr(const amg_csr* A) {
 static void destroy(amg_handle* H) {
   if (!H) return;
   multi_free(H);
+  tg_free(H);
   if (H->batch.sc_host) cudaFreeHost(H->batch.sc_host);
   if (H->bgraph) cudaGraphExecDestroy(H->bgraph);
   if (H->graph) cudaGraphExecDestroy(H->graph);
+  if (H->loop) cudaGraphExecDestroy(H->loop);
   if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   if (H->ev0) cudaEventDestroy(H->ev0);
   if (H->ev1) cudaEventDestroy(H->ev1);
@@ -128,12 +131,15 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   AMG_TRY(ar.alloc_n(&H->z, n));
   AMG_TRY(ar.alloc_n(&H->p, n));
   AMG_TRY(ar.alloc_n(&H->q, n));
+  if (H->opt.precision == AMG_PREC_F32 && H->L.size() > 1 && !H->batched)
+    AMG_TRY(ar.alloc_n(&H->r32, n));
   if (H->batched) {
     AMG_TRY(batch_init(H, s));
     ar.release(cat_rp);  // the hierarchy keeps its own copies
     ar.release(cat_ci);
     ar.release(cat_va);
   }
+  AMG_TRY(tail_init(H, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   return AMG_OK;
 }
@@ -258,6 +264,12 @@ int pcg_solve_multi(amg_handle* H, int nrhs, const double* B, double* X, const p
   if (op->beta_form < PCG_BETA_AUTO || op->beta_form > PCG_BETA_FLEXIBLE) return AMG_ERR_ARG;
   if (op->res_history || op->x_history) return AMG_ERR_ARG;
   return pcg_multi_run(H, nrhs, B, X, op, st, (cudaStream_t)stream);
+}
+
+int amg_twogrid_loss(amg_handle* H, int nsamples, int ncycles, const double* e0, double* loss,
+                     float* domega, amg_stream_t stream) {
+  if (!H || nsamples < 1 || ncycles < 1 || !e0 || !loss) return AMG_ERR_ARG;
+  return twogrid_loss(H, nsamples, ncycles, e0, loss, domega, (cudaStream_t)stream);
 }
 
 int amg_num_levels(const amg_handle* H, int* levels) {

@@ -315,7 +315,8 @@ int pcg_batch_run(amg_handle* H, const double* b, double* x, const pcg_options* 
     if (S.status < 0 && (worst >= 0 || S.status < worst)) worst = S.status;
     if (S.status == AMG_NOT_CONVERGED && worst == AMG_OK) worst = AMG_NOT_CONVERGED;
   }
-  return worst;
+  const int tc = tail_check(H, s);
+  return tc < 0 ? tc : worst;
 }
 
 // Batch bookkeeping after the hierarchy exists: tile ranges per system.

@@ -148,7 +148,28 @@ struct PcgScalars {
   int status;
   int beta_form;
   int pq_fail;
+  // device-side stopping test of the graph-resident loop (pcg.cu)
+  double tol;
+  int maxit;
+  int iter;
 };
+
+// Coarsest blocks up to this many rows are factored and solved by one CUDA
+// block each; larger ones use kernels spread over the whole GPU.
+constexpr int64_t COARSE_SMALL = 1024;
+
+// Diagonal block of coarsest row i: b with brow[b] <= i < brow[b+1].
+__device__ __forceinline__ int coarse_block(const int64_t* brow, int nblk, int64_t i) {
+  int lo = 0, hi = nblk;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (brow[mid] <= i)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
 
 // Deterministic grid reduction scratch: per-block partials + ticket.
 struct Reduce {
@@ -175,8 +196,10 @@ struct amg_handle {
   int64_t* d_bmat = nullptr;
   double* Linv = nullptr;
   double* LinvT = nullptr;
+  double* coarse_y = nullptr;  // nco: intermediate of the large-block coarse solve
   // PCG workspace
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  float* r32 = nullptr;  // FP32 copy of r for an FP32 V-cycle (else null)
   amg::PcgScalars* sc = nullptr;
   amg::PcgScalars* sc_host = nullptr;  // pinned
   amg::Reduce red;
@@ -186,6 +209,12 @@ struct amg_handle {
   const double* graph_b = nullptr;
   double* graph_x = nullptr;
   int graph_beta = -2;
+  // the whole PCG loop as one graph (device-side stopping test in a
+  // conditional while node); loop_state 0 untried, 1 built, -1 unavailable
+  cudaGraphExec_t loop = nullptr;
+  double* loop_x = nullptr;
+  int loop_beta = -2;
+  int loop_state = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // batched systems (amg_setup_batch); nsys == 1 otherwise
   bool batched = false;
@@ -196,6 +225,13 @@ struct amg_handle {
   double* bgraph_x = nullptr;
   int bgraph_beta = -2;
   void* multi = nullptr;  // multi-RHS workspace (multi.cu)
+  void* tg = nullptr;     // two-grid loss workspace and inner solver (twogrid.cu)
+  // persistent small-level launch (tail.cu): grid-barrier word, sticky
+  // failure flag, and the largest co-resident grid (0: not available)
+  unsigned* tail_bar = nullptr;
+  int* tail_fail = nullptr;
+  int tail_grid = 0;
+  int tail_debug = 0;  // amg_debug_tail_timeout
 };
 
 namespace amg {
@@ -337,12 +373,28 @@ int match_pairwise(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* c
 int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s);
 
 // V-cycle (vcycle.cu).  dots: 0 none; 1 (r, z); 2 (r, z) and (z, q).
+// r32 (optional, FP32 hierarchies): the same r rounded to float, gathered by
+// the level-0 pre-smoother instead of converting every FP64 element.
 int vcycle_run(const amg_handle* H, const double* r, double* z, int dots, const double* q,
-               cudaStream_t s, double* slice_part = nullptr);
+               cudaStream_t s, double* slice_part = nullptr, const float* r32 = nullptr);
 int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_time* out,
                    int max_out, int* count, cudaStream_t s);
 int time_level(const amg_handle* H, int l, int reps, const double* b64, double* z64, float* ms,
                cudaStream_t s);
+
+// Persistent launch of the small levels (tail.cu): levels lt .. coarsest of
+// one V-cycle (pre, restrict, coarse solve, post) separated by grid barriers.
+// tail_init sizes the grid after setup; tail_start gives lt, or -1 when the
+// per-level kernels run every level.  tail_reset clears the barrier after a
+// reported timeout.
+int tail_init(amg_handle* H, cudaStream_t s);
+int tail_start(const amg_handle* H);
+template <typename T>
+int tail_launch(const amg_handle* H, int lt, cudaStream_t s);
+int tail_reset(amg_handle* H, cudaStream_t s);
+// Synchronous: AMG_ERR_DEVICE_CHECK (and a reset) if a persistent launch gave
+// up waiting at a barrier since the last check, else AMG_OK.
+int tail_check(amg_handle* H, cudaStream_t s);
 
 // PCG (pcg.cu)
 int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,
@@ -353,6 +405,11 @@ int vcycle_multi(amg_handle* H, int K, const double* R, double* Z, cudaStream_t 
 int pcg_multi_run(amg_handle* H, int K, const double* B, double* X, const pcg_options* o,
                   pcg_stats* st, cudaStream_t s);
 void multi_free(amg_handle* H);
+
+// Two-grid loss for the learned smoother (twogrid.cu)
+int twogrid_loss(amg_handle* H, int nsamples, int K, const double* e0, double* loss,
+                 float* domega, cudaStream_t s);
+void tg_free(amg_handle* H);
 
 // Batched systems (batch.cu)
 int concat_systems(Arena& ar, int nsys, const amg_csr* A, amg_csr* cat, int64_t** rp,

@@ -1,0 +1,362 @@
+// Learned smoother weights: a 9 -> 32 -> 32 -> 1 MLP (GELU, sigmoid output
+// clamped to [1e-3, 1)) maps per-row stencil features to the l1-Jacobi
+// damping weight omega_i (s_i = omega_i / d_i, Sec. 2.3 l1-Jacobi; the network
+// is not in the paper).  FP32 weights and activations; gradients are summed
+// in FP64 with a fixed order (per-block partials, then blocks in order), so
+// training is reproducible run to run.
+//
+// Parameter layout (1409 floats): W1[32][9], b1[32], W2[32][32], b2[32],
+// W3[32], b3.
+#include <math.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace amg {
+
+constexpr int NF = 9, NH = 32;
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NF, OFF_W2 = OFF_B1 + NH,
+              OFF_B2 = OFF_W2 + NH * NH, OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH,
+              NPARAM = OFF_B3 + 1;
+constexpr float OMEGA_MIN = 1e-3f;
+constexpr int BW_ROWS = 64;  // rows staged per backward chunk (one thread each)
+constexpr int BW_BLOCKS_MAX = 1024;
+
+}  // namespace amg
+
+struct mlp_handle {
+  float* params = nullptr;
+  double* grad = nullptr;   // accumulated gradient (FP64)
+  double* gpart = nullptr;  // per-block partial gradients
+  double* m = nullptr;      // Adam moments
+  double* v = nullptr;
+  int t = 0;
+  int num_sms = 0;
+  amg::Arena arena;
+};
+
+namespace amg {
+
+__device__ __forceinline__ float gelu_f(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678f)); }
+__device__ __forceinline__ float gelu_df(float u) {
+  return 0.5f * (1.0f + erff(u * 0.70710678f)) + u * expf(-0.5f * u * u) * 0.39894228f;
+}
+
+// Features of row i of a 7-point operator on an nx x ny x nz grid:
+// a_ij / a_ii towards -x, +x, -y, +y, -z, +z (0 if absent), the l1 ratio,
+// log(max|a_ij| / min|a_ij|) and the neighbour count / 6.
+__global__ void k_features(int64_t n, int64_t nx, int64_t nxy, const int64_t* __restrict__ rp,
+                           const int32_t* __restrict__ ci, const double* __restrict__ v,
+                           float* __restrict__ feat) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double aii = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+      if (ci[e] == i) aii = v[e];
+    double off[6] = {0, 0, 0, 0, 0, 0}, l1 = 0.0, amax = 0.0, amin = 0.0;
+    int cnt = 0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int64_t d = (int64_t)ci[e] - i;
+      if (d == 0) continue;
+      int slot = -1;
+      if (d == -1) slot = 0;
+      else if (d == 1) slot = 1;
+      else if (d == -nx) slot = 2;
+      else if (d == nx) slot = 3;
+      else if (d == -nxy) slot = 4;
+      else if (d == nxy) slot = 5;
+      if (slot >= 0) off[slot] = v[e] / aii;
+      const double m = fabs(v[e]);
+      l1 += m;
+      amax = cnt == 0 ? m : fmax(amax, m);
+      amin = cnt == 0 ? m : fmin(amin, m);
+      ++cnt;
+    }
+    float* f = feat + i * NF;
+    for (int k = 0; k < 6; ++k) f[k] = (float)off[k];
+    f[6] = (float)(l1 / aii);
+    f[7] = (cnt > 0 && amin > 0.0) ? (float)log(amax / amin) : 0.0f;
+    f[8] = (float)cnt / 6.0f;
+  }
+}
+
+struct RowAct {
+  float u1[NH], h1[NH], u2[NH], h2[NH], z, sg;
+};
+
+__device__ __forceinline__ void mlp_row(const float* __restrict__ p, const float* f, RowAct& a) {
+#pragma unroll 4
+  for (int o = 0; o < NH; ++o) {
+    float s = p[OFF_B1 + o];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) s = fmaf(p[OFF_W1 + o * NF + i], f[i], s);
+    a.u1[o] = s;
+    a.h1[o] = gelu_f(s);
+  }
+  for (int o = 0; o < NH; ++o) {
+    float s = p[OFF_B2 + o];
+#pragma unroll 8
+    for (int i = 0; i < NH; ++i) s = fmaf(p[OFF_W2 + o * NH + i], a.h1[i], s);
+    a.u2[o] = s;
+    a.h2[o] = gelu_f(s);
+  }
+  float z = p[OFF_B3];
+#pragma unroll 8
+  for (int i = 0; i < NH; ++i) z = fmaf(p[OFF_W3 + i], a.h2[i], z);
+  a.z = z;
+  a.sg = 1.0f / (1.0f + expf(-z));
+}
+
+__global__ void k_mlp_forward(int64_t n, const float* __restrict__ params,
+                              const float* __restrict__ feat, float* __restrict__ omega) {
+  __shared__ float p[NPARAM];
+  for (int k = threadIdx.x; k < NPARAM; k += blockDim.x) p[k] = params[k];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float f[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) f[k] = feat[i * NF + k];
+    RowAct a;
+    mlp_row(p, f, a);
+    omega[i] = fmaxf(a.sg, OMEGA_MIN);
+  }
+}
+
+// Gradient of sum_i domega_i * omega_i with respect to the parameters.
+// Each chunk of BW_ROWS rows: thread r computes row r's activations and
+// backpropagated signals into shared memory; then every thread owns a set of
+// parameters and adds their per-row terms in row order.  Per-block sums go to
+// gpart[block][param].
+__global__ void __launch_bounds__(BW_ROWS)
+    k_mlp_backward(int64_t n, const float* __restrict__ params, const float* __restrict__ feat,
+                   const float* __restrict__ domega, double* __restrict__ gpart) {
+  __shared__ float p[NPARAM];
+  __shared__ float sf[BW_ROWS][NF], sh1[BW_ROWS][NH], sh2[BW_ROWS][NH], sdu1[BW_ROWS][NH],
+      sdu2[BW_ROWS][NH], sdz[BW_ROWS];
+  for (int k = threadIdx.x; k < NPARAM; k += blockDim.x) p[k] = params[k];
+  constexpr int PER = (NPARAM + BW_ROWS - 1) / BW_ROWS;
+  double acc[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) acc[q] = 0.0;
+  __syncthreads();
+  const int64_t nchunks = (n + BW_ROWS - 1) / BW_ROWS;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const int r = threadIdx.x;
+    const int64_t i = c * BW_ROWS + r;
+    if (i < n) {
+      float f[NF];
+#pragma unroll
+      for (int k = 0; k < NF; ++k) f[k] = sf[r][k] = feat[i * NF + k];
+      RowAct a;
+      mlp_row(p, f, a);
+      const float dz = a.sg > OMEGA_MIN ? domega[i] * a.sg * (1.0f - a.sg) : 0.0f;
+      sdz[r] = dz;
+      float dh1[NH];
+#pragma unroll
+      for (int k = 0; k < NH; ++k) dh1[k] = 0.0f;
+      for (int o = 0; o < NH; ++o) {
+        const float du2 = dz * p[OFF_W3 + o] * gelu_df(a.u2[o]);
+        sdu2[r][o] = du2;
+        sh2[r][o] = a.h2[o];
+        sh1[r][o] = a.h1[o];
+#pragma unroll 8
+        for (int k = 0; k < NH; ++k) dh1[k] = fmaf(p[OFF_W2 + o * NH + k], du2, dh1[k]);
+      }
+      for (int o = 0; o < NH; ++o) sdu1[r][o] = dh1[o] * gelu_df(a.u1[o]);
+    } else {
+      sdz[r] = 0.0f;
+      for (int k = 0; k < NF; ++k) sf[r][k] = 0.0f;
+      for (int o = 0; o < NH; ++o) sdu1[r][o] = sdu2[r][o] = sh1[r][o] = sh2[r][o] = 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int k = threadIdx.x + q * BW_ROWS;
+      if (k >= NPARAM) break;
+      double s = 0.0;
+      for (int rr = 0; rr < BW_ROWS; ++rr) {
+        float t;
+        if (k < OFF_B1) t = sdu1[rr][k / NF] * sf[rr][k % NF];
+        else if (k < OFF_W2) t = sdu1[rr][k - OFF_B1];
+        else if (k < OFF_B2) t = sdu2[rr][(k - OFF_W2) / NH] * sh1[rr][(k - OFF_W2) % NH];
+        else if (k < OFF_W3) t = sdu2[rr][k - OFF_B2];
+        else if (k < OFF_B3) t = sdz[rr] * sh2[rr][k - OFF_W3];
+        else t = sdz[rr];
+        s += (double)t;
+      }
+      acc[q] += s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int k = threadIdx.x + q * BW_ROWS;
+    if (k < NPARAM) gpart[(int64_t)blockIdx.x * NPARAM + k] = acc[q];
+  }
+}
+
+// grad (+)= sum over blocks of gpart, in block order.
+__global__ void k_mlp_grad_reduce(int nblocks, const double* __restrict__ gpart, double* grad,
+                                  int accumulate) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NPARAM; k += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += gpart[(int64_t)b * NPARAM + k];
+    grad[k] = accumulate ? grad[k] + s : s;
+  }
+}
+
+// Adam (Kingma & Ba 2015) on FP32 parameters with FP64 moments; clears grad.
+__global__ void k_adam(float* params, double* grad, double* m, double* v, int t, double lr,
+                       double b1, double b2, double eps, double scale) {
+  const double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < NPARAM; k += gridDim.x * blockDim.x) {
+    const double g = grad[k] * scale;
+    m[k] = b1 * m[k] + (1.0 - b1) * g;
+    v[k] = b2 * v[k] + (1.0 - b2) * g * g;
+    params[k] = (float)((double)params[k] - lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps));
+    grad[k] = 0.0;
+  }
+}
+
+// Host-side initial weights: N(0, 1/fan_in) from splitmix64 (Steele, Lea,
+// Flood 2014) with the Box-Muller transform; biases zero, output bias 4
+// (omega ~ 0.98 at start, next to plain l1-Jacobi's omega = 1, so training
+// moves away from the fallback only where the loss improves).
+static void init_params(uint64_t seed, std::vector<float>& p) {
+  p.assign(NPARAM, 0.0f);
+  uint64_t state = seed;
+  auto next = [&]() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto normal = [&]() {
+    const double u1 = (double)(next() >> 11) * (1.0 / 9007199254740992.0);
+    const double u2 = (double)(next() >> 11) * (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log1p(-u1)) * cos(6.283185307179586 * u2);
+  };
+  for (int k = 0; k < NH * NF; ++k) p[OFF_W1 + k] = (float)(normal() / sqrt((double)NF));
+  for (int k = 0; k < NH * NH; ++k) p[OFF_W2 + k] = (float)(normal() / sqrt((double)NH));
+  for (int k = 0; k < NH; ++k) p[OFF_W3 + k] = (float)(normal() / sqrt((double)NH));
+  p[OFF_B3] = 4.0f;
+}
+
+}  // namespace amg
+
+using namespace amg;
+
+extern "C" {
+
+int mlp_num_params(void) { return NPARAM; }
+
+int mlp_create(uint64_t seed, mlp_handle** M) {
+  if (!M) return AMG_ERR_ARG;
+  *M = nullptr;
+  mlp_handle* h = new mlp_handle();
+  auto fail = [&](int rc) {
+    h->arena.release_all();
+    delete h;
+    return rc;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(AMG_ERR_CUDA);
+  int rc;
+  if ((rc = h->arena.alloc_n(&h->params, NPARAM)) < 0) return fail(rc);
+  if ((rc = h->arena.alloc_n(&h->grad, NPARAM)) < 0) return fail(rc);
+  if ((rc = h->arena.alloc_n(&h->m, NPARAM)) < 0) return fail(rc);
+  if ((rc = h->arena.alloc_n(&h->v, NPARAM)) < 0) return fail(rc);
+  if ((rc = h->arena.alloc_n(&h->gpart, (int64_t)BW_BLOCKS_MAX * NPARAM)) < 0) return fail(rc);
+  std::vector<float> p;
+  init_params(seed, p);
+  if (cudaMemcpy(h->params, p.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemset(h->grad, 0, sizeof(double) * NPARAM) != cudaSuccess ||
+      cudaMemset(h->m, 0, sizeof(double) * NPARAM) != cudaSuccess ||
+      cudaMemset(h->v, 0, sizeof(double) * NPARAM) != cudaSuccess)
+    return fail(AMG_ERR_CUDA);
+  *M = h;
+  return AMG_OK;
+}
+
+int mlp_destroy(mlp_handle* M) {
+  if (M) {
+    M->arena.release_all();
+    delete M;
+  }
+  return AMG_OK;
+}
+
+int mlp_get_params(const mlp_handle* M, float* host) {
+  if (!M || !host) return AMG_ERR_ARG;
+  AMG_CUDA_TRY(cudaMemcpy(host, M->params, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+  return AMG_OK;
+}
+
+int mlp_set_params(mlp_handle* M, const float* host) {
+  if (!M || !host) return AMG_ERR_ARG;
+  AMG_CUDA_TRY(cudaMemcpy(M->params, host, sizeof(float) * NPARAM, cudaMemcpyHostToDevice));
+  AMG_CUDA_TRY(cudaMemset(M->grad, 0, sizeof(double) * NPARAM));
+  AMG_CUDA_TRY(cudaMemset(M->m, 0, sizeof(double) * NPARAM));
+  AMG_CUDA_TRY(cudaMemset(M->v, 0, sizeof(double) * NPARAM));
+  M->t = 0;
+  return AMG_OK;
+}
+
+int mlp_get_grad(const mlp_handle* M, double* host) {
+  if (!M || !host) return AMG_ERR_ARG;
+  AMG_CUDA_TRY(cudaMemcpy(host, M->grad, sizeof(double) * NPARAM, cudaMemcpyDeviceToHost));
+  return AMG_OK;
+}
+
+int mlp_features(const amg_csr* A, int64_t nx, int64_t ny, int64_t nz, float* feat,
+                 amg_stream_t stream) {
+  if (!A || !feat || nx < 1 || ny < 1 || nz < 1 || A->n != nx * ny * nz) return AMG_ERR_ARG;
+  int dev = 0, sms = 0;
+  AMG_CUDA_TRY(cudaGetDevice(&dev));
+  AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  k_features<<<grid_for(A->n, 256, sms, 8), 256, 0, (cudaStream_t)stream>>>(
+      A->n, nx, nx * ny, A->rowptr, A->col, A->val, feat);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+int mlp_forward(const mlp_handle* M, int64_t n, const float* feat, float* omega,
+                amg_stream_t stream) {
+  if (!M || n < 0 || !feat || !omega) return AMG_ERR_ARG;
+  if (n == 0) return AMG_OK;
+  k_mlp_forward<<<grid_for(n, 128, M->num_sms, 8), 128, 0, (cudaStream_t)stream>>>(
+      n, M->params, feat, omega);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+int mlp_backward(mlp_handle* M, int64_t n, const float* feat, const float* domega,
+                 int accumulate, amg_stream_t stream) {
+  if (!M || n < 0 || !feat || !domega) return AMG_ERR_ARG;
+  const int64_t chunks = (n + BW_ROWS - 1) / BW_ROWS;
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, BW_BLOCKS_MAX));
+  cudaStream_t s = (cudaStream_t)stream;
+  k_mlp_backward<<<nb, BW_ROWS, 0, s>>>(n, M->params, feat, domega, M->gpart);
+  AMG_LAUNCH_CHECK();
+  k_mlp_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s>>>(nb, M->gpart, M->grad, accumulate);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+int mlp_adam_step(mlp_handle* M, double lr, double beta1, double beta2, double eps,
+                  double grad_scale, amg_stream_t stream) {
+  if (!M || !(lr > 0.0)) return AMG_ERR_ARG;
+  M->t += 1;
+  k_adam<<<(NPARAM + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+      M->params, M->grad, M->m, M->v, M->t, lr, beta1, beta2, eps, grad_scale);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+}  // extern "C"

@@ -218,19 +218,6 @@ __device__ __forceinline__ double lane_tree(double (&p)[32]) {
   return p[0];
 }
 
-// Diagonal block of coarsest row i: b with brow[b] <= i < brow[b+1].
-__device__ __forceinline__ int coarse_block(const int64_t* brow, int nblk, int64_t i) {
-  int lo = 0, hi = nblk;  // brow[lo] <= i < brow[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) / 2;
-    if (brow[mid] <= i)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
 template <typename BT>
 __global__ void k_m_coarse1(int64_t n, int K, int nblk, const int64_t* __restrict__ brow,
                             const int64_t* __restrict__ bmat, const double* __restrict__ Linv,

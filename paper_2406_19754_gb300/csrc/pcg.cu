@@ -13,6 +13,7 @@
 // captured CUDA graph; the host reads the scalars once per iteration for the
 // convergence test.
 #include <math.h>
+#include <string.h>
 
 #include "sellk.cuh"
 
@@ -35,18 +36,19 @@ struct TrueResEpi {
 template <int TPR, int MODE>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_residual(SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
-               double* __restrict__ r, Reduce red, PcgScalars* sc) {
+               double* __restrict__ r, Reduce red, PcgScalars* sc, float* __restrict__ r32) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double d[2] = {0.0, 0.0};
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
        sl += nw) {
     const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(x + j); });
-    const int64_t i = sl * Lanes<TPR>::C + ln.r;
-    if (ln.t == 0 && i < A.n) {
+    const int64_t i = lane_row(A, sl, ln);
+    if (i >= 0) {
       const double bi = b[i];
       const double ri = bi - acc;
       r[i] = ri;
+      if (r32) r32[i] = (float)ri;
       d[0] += ri * ri;
       d[1] += bi * bi;
     }
@@ -83,8 +85,8 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
        sl += nw) {
     const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(p + j); });
-    const int64_t i = sl * Lanes<TPR>::C + ln.r;
-    if (ln.t == 0 && i < A.n) {
+    const int64_t i = lane_row(A, sl, ln);
+    if (i >= 0) {
       q[i] = acc;
       d[0] += p[i] * acc;
     }
@@ -100,10 +102,12 @@ struct RrEpi {
   }
 };
 
-// x += alpha p; r -= alpha q; (r, r).  Skipped after a breakdown.
+// x += alpha p; r -= alpha q; (r, r); r32 (if set) = (float) r for an FP32
+// V-cycle, so it gathers 4-byte values without converting each one.
+// Skipped after a breakdown.
 __global__ void k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
                             const double* __restrict__ p, const double* __restrict__ q, Reduce red,
-                            PcgScalars* sc) {
+                            PcgScalars* sc, float* __restrict__ r32) {
   if (sc->status < 0) return;  // uniform across the grid: no block reduces
   const double alpha = sc->alpha;
   double d[1] = {0.0};
@@ -112,6 +116,7 @@ __global__ void k_cg_update(int64_t n, double* __restrict__ x, double* __restric
     x[i] = x[i] + alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
+    if (r32) r32[i] = (float)ri;
     d[0] += ri * ri;
   }
   grid_reduce<1>(d, red, RrEpi{sc});
@@ -133,11 +138,11 @@ static int launch_residual(const amg_handle* H, int mode, const double* b, const
   const int grid = sell_grid(L.A.nslices, H->num_sms);
   const SellView<double> v = view<double>(L.A, L.A.v64);
   if (mode == 0) {
-    AMG_DISPATCH_TPR(L.A.tpr,
-                     (k_residual<TPR, 0><<<grid, SELL_BLOCK, 0, s>>>(v, b, x, r, H->red, H->sc)));
+    AMG_DISPATCH_TPR(L.A.tpr, (k_residual<TPR, 0><<<grid, SELL_BLOCK, 0, s>>>(
+                                  v, b, x, r, H->red, H->sc, H->r32)));
   } else {
-    AMG_DISPATCH_TPR(L.A.tpr,
-                     (k_residual<TPR, 1><<<grid, SELL_BLOCK, 0, s>>>(v, b, x, r, H->red, H->sc)));
+    AMG_DISPATCH_TPR(L.A.tpr, (k_residual<TPR, 1><<<grid, SELL_BLOCK, 0, s>>>(
+                                  v, b, x, r, H->red, H->sc, nullptr)));
   }
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -156,7 +161,7 @@ static int launch_spmv_dot(const amg_handle* H, cudaStream_t s) {
 static int launch_update(const amg_handle* H, double* x, cudaStream_t s) {
   const int64_t n = H->L[0].n;
   k_cg_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, x, H->r, H->p, H->q, H->red,
-                                                              H->sc);
+                                                              H->sc, H->r32);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -165,7 +170,7 @@ static int launch_update(const amg_handle* H, double* x, cudaStream_t s) {
 // q = A p (+ alpha), x/r update (+ (r, r)).
 static int iteration_body(const amg_handle* H, double* x, int dots, cudaStream_t s) {
   const int64_t n = H->L[0].n;
-  AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s));
+  AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s, nullptr, H->r32));
   k_p_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, H->p, H->z, H->sc);
   AMG_LAUNCH_CHECK();
   AMG_TRY(launch_spmv_dot(H, s));
@@ -196,6 +201,89 @@ static int ensure_graph(amg_handle* H, double* x, int dots, int beta_form) {
   return AMG_OK;
 }
 
+// The stopping test of one iteration, on the device: the same decisions as
+// the host loop in pcg_run (a failed (p, q) ends the solve without counting
+// the step; otherwise count it, then stop on an error, on ||r||/||b|| <= tol
+// or at maxit).  Sets the while-node condition: 1 = run another iteration.
+__global__ void k_pcg_control(PcgScalars* sc, cudaGraphConditionalHandle h) {
+  unsigned go = 0;
+  if (!sc->pq_fail) {
+    const int k = ++sc->iter;
+    double bnorm = sqrt(sc->bb);
+    if (bnorm == 0.0) bnorm = 1.0;
+    const double rel = sqrt(sc->rr) / bnorm;
+    go = (sc->status < 0 || rel <= sc->tol || k >= sc->maxit) ? 0u : 1u;
+  }
+  cudaGraphSetConditional(h, go);
+}
+
+// The remaining iterations of a solve as one graph: the stopping test, then
+// a conditional while node whose body is one iteration plus the test.  The
+// host waits once per solve instead of once per iteration.
+static int build_loop(amg_handle* H, double* x, int dots, cudaGraphExec_t* out) {
+  cudaStream_t cs = H->cap_stream;
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraph_t g = nullptr;
+  AMG_CUDA_TRY(cudaGraphCreate(&g, 0));
+  int rc = AMG_OK;
+  cudaGraphConditionalHandle h;
+  cudaGraphNode_t ctl = nullptr, wnode = nullptr;
+  size_t nn = 1;
+  cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+  cudaGraph_t body = nullptr, cap = nullptr;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode);
+  if (e == cudaSuccess) {
+    k_pcg_control<<<1, 1, 0, cs>>>(H->sc, h);
+    e = cudaStreamEndCapture(cs, &cap);
+  }
+  if (e == cudaSuccess) e = cudaGraphGetNodes(g, &ctl, &nn);
+  if (e == cudaSuccess && nn != 1) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) {
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&wnode, g, &ctl, nullptr, 1, &cp);
+  }
+  if (e == cudaSuccess) {
+    body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode);
+  }
+  if (e == cudaSuccess) {
+    rc = iteration_body(H, x, dots, cs);
+    if (rc == AMG_OK) k_pcg_control<<<1, 1, 0, cs>>>(H->sc, h);
+    cudaGraph_t bcap = nullptr;
+    e = cudaStreamEndCapture(cs, &bcap);
+  }
+  if (e == cudaSuccess && rc == AMG_OK) e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (rc < 0) return rc;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *out = nullptr;
+    return AMG_ERR_UNSUPPORTED;
+  }
+  return AMG_OK;
+}
+
+// Loop graph for (x, beta form); AMG_ERR_UNSUPPORTED (once, remembered) if
+// the runtime cannot build it, and the caller uses one graph per iteration.
+static int ensure_loop(amg_handle* H, double* x, int dots, int beta_form) {
+  if (H->loop_state < 0) return AMG_ERR_UNSUPPORTED;
+  if (H->loop && H->loop_x == x && H->loop_beta == beta_form) return AMG_OK;
+  if (H->loop) {
+    cudaGraphExecDestroy(H->loop);
+    H->loop = nullptr;
+  }
+  const int rc = build_loop(H, x, dots, &H->loop);
+  if (rc == AMG_ERR_UNSUPPORTED) H->loop_state = -1;
+  if (rc < 0) return rc;
+  H->loop_state = 1;
+  H->loop_x = x;
+  H->loop_beta = beta_form;
+  return AMG_OK;
+}
+
 static int read_scalars(amg_handle* H, cudaStream_t s) {
   AMG_CUDA_TRY(cudaMemcpyAsync(H->sc_host, H->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -209,10 +297,19 @@ int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg
   if (beta_form == PCG_BETA_AUTO)
     beta_form = H->opt.precision == AMG_PREC_F32 ? PCG_BETA_FLEXIBLE : PCG_BETA_FR;
   const int dots = beta_form == PCG_BETA_FLEXIBLE ? 2 : 1;
-  if (o->use_graph) AMG_TRY(ensure_graph(H, x, dots, beta_form));
+  // one graph for the whole loop unless per-iteration histories are kept
+  bool use_loop = false;
+  if (o->use_graph && !o->res_history && !o->x_history) {
+    const int rc = ensure_loop(H, x, dots, beta_form);
+    if (rc < 0 && rc != AMG_ERR_UNSUPPORTED) return rc;
+    use_loop = rc == AMG_OK;
+  }
+  if (o->use_graph && !use_loop) AMG_TRY(ensure_graph(H, x, dots, beta_form));
 
   PcgScalars init = {};
   init.beta_form = beta_form;
+  init.tol = o->tol;
+  init.maxit = o->maxit;
   *H->sc_host = init;
   AMG_CUDA_TRY(cudaMemcpyAsync(H->sc, H->sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
   AMG_CUDA_TRY(cudaEventRecord(H->ev0, s));
@@ -229,11 +326,22 @@ int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg
   if (relres <= o->tol) {
     status = AMG_OK;
   } else if (o->maxit > 0) {
-    AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s));
+    AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s, nullptr, H->r32));
     AMG_CUDA_TRY(cudaMemcpyAsync(H->p, H->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     AMG_TRY(launch_spmv_dot(H, s));
     AMG_TRY(launch_update(H, x, s));
-    for (;;) {
+    if (use_loop) {
+      AMG_CUDA_TRY(cudaGraphLaunch(H->loop, s));
+      AMG_TRY(read_scalars(H, s));
+      const PcgScalars& S = *H->sc_host;
+      k = S.iter;
+      relres = sqrt(S.rr) / bnorm;  // rr is left unchanged by a failed step
+      if (S.pq_fail || S.status < 0)
+        status = S.status;
+      else if (relres <= o->tol)
+        status = AMG_OK;
+    }
+    for (; !use_loop;) {
       AMG_TRY(read_scalars(H, s));
       const int dstat = H->sc_host->status;
       if (H->sc_host->pq_fail) {  // x and r were not updated in this step
@@ -266,6 +374,8 @@ int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg
   // true residual ||b - A x|| / ||b|| (outside the timed region)
   AMG_TRY(launch_residual(H, 1, b, x, H->z, s));
   AMG_TRY(read_scalars(H, s));
+  const int tc = tail_check(H, s);
+  if (tc < 0) status = tc;
   float ms = 0.f;
   AMG_CUDA_TRY(cudaEventElapsedTime(&ms, H->ev0, H->ev1));
   if (st) {

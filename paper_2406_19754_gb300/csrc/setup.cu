@@ -634,6 +634,112 @@ __global__ void k_cholesky(const int64_t* brow, const int64_t* bmat, double* den
   }
 }
 
+// Blocked right-looking Cholesky for large coarsest blocks (several CUDA
+// blocks per step).  Every entry receives the same rank-1 updates, in the
+// same column order and with the same explicitly rounded operations, as in
+// the one-block kernel above, so both produce the same factor bit for bit.
+constexpr int CHOL_NB = 32;
+
+// Factor the diagonal tile [kb, kb+nb) in place (one CUDA block).
+__global__ void k_chol_diag(double* a, int64_t n, int64_t kb, int nb, int* status) {
+  __shared__ int ok;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t kk = kb + k;
+    if (threadIdx.x == 0) {
+      const double piv = a[kk * n + kk];
+      ok = piv > 0.0;
+      if (ok) a[kk * n + kk] = sqrt(piv);
+    }
+    __syncthreads();
+    if (!ok) {
+      if (threadIdx.x == 0) atomicExch(status, AMG_ERR_NOT_SPD);
+      return;
+    }
+    const double lkk = a[kk * n + kk];
+    for (int i = k + 1 + threadIdx.x; i < nb; i += blockDim.x)
+      a[(kb + i) * n + kk] = __ddiv_rn(a[(kb + i) * n + kk], lkk);
+    __syncthreads();
+    const int m = nb - k - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int ii = idx / m, jj = idx % m;
+      if (jj <= ii) {
+        const int64_t i = kb + k + 1 + ii, j = kb + k + 1 + jj;
+        a[i * n + j] = __dsub_rn(a[i * n + j], __dmul_rn(a[i * n + kk], a[j * n + kk]));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Panel below the tile: row i >= kb+nb, columns k = kb..kb+nb-1 in order.
+__global__ void k_chol_panel(double* a, int64_t n, int64_t kb, int nb) {
+  for (int64_t i = kb + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int k = 0; k < nb; ++k) {
+      const int64_t kk = kb + k;
+      double v = a[i * n + kk];
+      for (int q = 0; q < k; ++q)
+        v = __dsub_rn(v, __dmul_rn(a[i * n + kb + q], a[kk * n + kb + q]));
+      a[i * n + kk] = __ddiv_rn(v, a[kk * n + kk]);
+    }
+  }
+}
+
+// Trailing update: a_ij -= l_ik l_jk for k = kb..kb+nb-1 in order, j <= i.
+__global__ void k_chol_update(double* a, int64_t n, int64_t kb, int nb) {
+  const int64_t t0 = kb + nb, m = n - t0;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < m * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ii = idx / m, jj = idx % m;
+    if (jj > ii) continue;
+    const int64_t i = t0 + ii, j = t0 + jj;
+    double v = a[i * n + j];
+    for (int k = 0; k < nb; ++k)
+      v = __dsub_rn(v, __dmul_rn(a[i * n + kb + k], a[j * n + kb + k]));
+    a[i * n + j] = v;
+  }
+}
+
+// Column c of L^-1 per thread (forward substitution on e_c), then L^-T.
+__global__ void k_tri_inverse(const double* a, int64_t n, double* Linv) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = 0; i < c; ++i) Linv[i * n + c] = 0.0;
+    for (int64_t i = c; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int64_t k = c; k < i; ++k) s = __dsub_rn(s, __dmul_rn(a[i * n + k], Linv[k * n + c]));
+      Linv[i * n + c] = __ddiv_rn(s, a[i * n + i]);
+    }
+  }
+}
+
+__global__ void k_transpose(const double* in, int64_t n, double* out) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n * n;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    out[(idx % n) * n + idx / n] = in[idx];
+}
+
+static int chol_blocked(double* a, int64_t n, double* Linv, double* LinvT, int* status,
+                        int num_sms, cudaStream_t s) {
+  for (int64_t kb = 0; kb < n; kb += CHOL_NB) {
+    const int nb = (int)std::min<int64_t>(CHOL_NB, n - kb);
+    k_chol_diag<<<1, 256, 0, s>>>(a, n, kb, nb, status);
+    AMG_LAUNCH_CHECK();
+    if (kb + nb < n) {
+      k_chol_panel<<<grid_for(n - kb - nb, 128, num_sms, 4), 128, 0, s>>>(a, n, kb, nb);
+      AMG_LAUNCH_CHECK();
+      const int64_t m = n - kb - nb;
+      k_chol_update<<<grid_for(m * m, 256, num_sms, 8), 256, 0, s>>>(a, n, kb, nb);
+      AMG_LAUNCH_CHECK();
+    }
+  }
+  k_tri_inverse<<<grid_for(n, 64, num_sms, 8), 64, 0, s>>>(a, n, Linv);
+  AMG_LAUNCH_CHECK();
+  k_transpose<<<grid_for(n * n, 256, num_sms, 8), 256, 0, s>>>(Linv, n, LinvT);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
 // ------------------------------------------------------------------ V-cycle operators
 // AP = A P: row i holds every aggregate J among agg(col(i, :)) once, in order
 // of first appearance, with the sum of its entries taken in column order.
@@ -956,15 +1062,22 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     AMG_TRY(ar.alloc_n(&H->LinvT, bmat.back()));
     AMG_TRY(ar.alloc_n(&H->d_brow, nb + 1));
     AMG_TRY(ar.alloc_n(&H->d_bmat, nb + 1));
+    AMG_TRY(ar.alloc_n(&H->coarse_y, Lc.n));
     AMG_CUDA_TRY(cudaMemcpyAsync(H->d_brow, brow.data(), sizeof(int64_t) * (nb + 1),
                                  cudaMemcpyHostToDevice, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(H->d_bmat, bmat.data(), sizeof(int64_t) * (nb + 1),
                                  cudaMemcpyHostToDevice, s));
     k_dense_blocks<<<nb, 256, 0, s>>>(rp, ci, va, H->d_brow, H->d_bmat, dense, H->dev_status);
     AMG_LAUNCH_CHECK();
-    k_cholesky<<<nb, 1024, 0, s>>>(H->d_brow, H->d_bmat, dense, H->Linv, H->LinvT,
-                                   H->dev_status);
-    AMG_LAUNCH_CHECK();
+    if (largest_block(Lc, Lc.n) <= COARSE_SMALL) {  // one CUDA block per diagonal block
+      k_cholesky<<<nb, 1024, 0, s>>>(H->d_brow, H->d_bmat, dense, H->Linv, H->LinvT,
+                                     H->dev_status);
+      AMG_LAUNCH_CHECK();
+    } else {  // large blocks: blocked factorization over the whole GPU, block by block
+      for (int b = 0; b < nb; ++b)
+        AMG_TRY(chol_blocked(dense + bmat[b], brow[b + 1] - brow[b], H->Linv + bmat[b],
+                             H->LinvT + bmat[b], H->dev_status, sms, s));
+    }
     int st = read_status(H, s);  // synchronises: brow/bmat copies are done
     ar.release(dense);
     if (st < 0) return st;

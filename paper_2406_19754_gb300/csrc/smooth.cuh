@@ -1,0 +1,149 @@
+// Per-row bodies of the V(1,1) cycle shared by the one-kernel-per-step path
+// (vcycle.cu) and the persistent launch that runs the small levels between
+// grid barriers (tail.cu).  Both call the same code, so a row's result is the
+// same bits whichever kernel computes it.
+//
+//   pre_slice      r_i = b_i - (Ah b)_i                  (Ah = A S)
+//   restrict_sum   b_c[I] = sum of r_i over the members of I, ascending
+//   post_slice     z_i = s_i b_i + x_c[agg(i)] + s_i (r_i - (AP x_c)_i)
+//   coarse_*       x = L^-T (L^-1 b) on a diagonal block of the coarsest level
+//
+// Ld picks the load path for vectors: LdRO (read-only cache) where no CTA of
+// the launch writes them, LdL2 (L2-coherent) where another CTA of the same
+// launch wrote them before a grid barrier, LdPlain where only the calling CTA
+// wrote them before a __syncthreads.
+#pragma once
+
+#include "sellk.cuh"
+
+namespace amg {
+
+struct LdRO {
+  template <typename X>
+  __device__ __forceinline__ static X ld(const X* p) {
+    return __ldg(p);
+  }
+};
+// Plain loads: within one CTA, __syncthreads makes the CTA's own global
+// writes visible to them (L1 stays coherent for the SM's own stores).
+struct LdPlain {
+  template <typename X>
+  __device__ __forceinline__ static X ld(const X* p) {
+    return *p;
+  }
+};
+struct LdL2 {
+  template <typename X>
+  __device__ __forceinline__ static X ld(const X* p) {
+    return __ldcg(p);
+  }
+};
+
+template <int TPR, typename Ld, typename V, typename T, typename BT>
+__device__ __forceinline__ void pre_slice(const SellView<V>& Ah, const BT* b, T* r, int64_t sl,
+                                          const Lanes<TPR>& ln) {
+  const T acc = sell_row<TPR, T>(Ah, sl, ln, [&](int j) { return to_f(Ld::ld(b + j), T(0)); });
+  const int64_t i = lane_row(Ah, sl, ln);
+  if (i >= 0) r[i] = to_f(Ld::ld(b + i), T(0)) - acc;
+}
+
+template <typename Ld, typename T>
+__device__ __forceinline__ T restrict_sum(const int32_t* m, int stride, const T* r) {
+  T acc = Ld::ld(r + m[0]);
+  for (int k = 1; k < stride; ++k) {
+    const int32_t i = m[k];
+    if (i < 0) break;
+    acc = acc + Ld::ld(r + i);
+  }
+  return acc;
+}
+
+// Writes x[i] = z_i for this lane's row and returns i (or -1, z untouched).
+template <int TPR, typename Ld, typename V, typename T, typename BT, typename XT>
+__device__ __forceinline__ int64_t post_slice(const SellView<V>& AP, const BT* b, const T* s,
+                                              const T* r, const int32_t* agg, const T* xc, XT* x,
+                                              int64_t sl, const Lanes<TPR>& ln, XT& z) {
+  const T acc = sell_row<TPR, T>(AP, sl, ln, [&](int J) { return Ld::ld(xc + J); });
+  const int64_t i = lane_row(AP, sl, ln);
+  if (i >= 0) {
+    const T bi = to_f(Ld::ld(b + i), T(0));
+    const T si = s[i];
+    const T yi = si * bi + Ld::ld(xc + agg[i]);
+    z = to_f(yi + si * (Ld::ld(r + i) - acc), XT(0));
+    x[i] = z;
+  }
+  return i;
+}
+
+// One diagonal block of the coarsest level solved by the calling CTA:
+// y = L^-1 b, then x = L^-T y, one warp per row, vectors staged in shared
+// memory (2n doubles).  Every thread of the CTA must call it.
+template <typename Ld, typename BT, typename XT>
+__device__ __forceinline__ void coarse_block_solve(int blk, const int64_t* brow,
+                                                   const int64_t* bmat, const double* Linv_all,
+                                                   const double* LinvT_all, const BT* b_all,
+                                                   XT* x_all, double* csh) {
+  const int64_t r0 = brow[blk];
+  const int n = (int)(brow[blk + 1] - r0);
+  const double* Linv = Linv_all + bmat[blk];
+  const double* LinvT = LinvT_all + bmat[blk];
+  const BT* b = b_all + r0;
+  XT* x = x_all + r0;
+  double* bs = csh;
+  double* ys = csh + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = (double)Ld::ld(b + i);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = w; i < n; i += nw) {
+    double acc = 0.0;
+    const double* row = Linv + (int64_t)i * n;
+    for (int k = lane; k <= i; k += 32) acc = fma(row[k], bs[k], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) ys[i] = acc;
+  }
+  __syncthreads();
+  for (int k = w; k < n; k += nw) {
+    double acc = 0.0;
+    const double* row = LinvT + (int64_t)k * n;
+    for (int i = k + lane; i < n; i += 32) acc = fma(row[i], ys[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) x[k] = (XT)acc;
+  }
+  __syncthreads();  // bs/ys are reused by the CTA's next block
+}
+
+// Large coarsest blocks: row g of y = L^-1 b and of x = L^-T y, one warp
+// each.  Each dot product is summed like coarse_block_solve sums it (lane
+// partials over a stride of 32, then the xor tree), so results agree bit for
+// bit.
+template <typename Ld, typename BT>
+__device__ __forceinline__ void coarse_y_row(int64_t g, int nblk, const int64_t* brow,
+                                             const int64_t* bmat, const double* Linv_all,
+                                             const BT* b, double* y) {
+  const int lane = threadIdx.x & 31;
+  const int blk = coarse_block(brow, nblk, g);
+  const int64_t r0 = brow[blk];
+  const int64_t n = brow[blk + 1] - r0, i = g - r0;
+  const double* row = Linv_all + bmat[blk] + i * n;
+  double acc = 0.0;
+  for (int64_t k = lane; k <= i; k += 32) acc = fma(row[k], (double)Ld::ld(b + r0 + k), acc);
+  acc = warp_sum(acc);
+  if (lane == 0) y[g] = acc;
+}
+
+template <typename Ld, typename XT>
+__device__ __forceinline__ void coarse_x_row(int64_t g, int nblk, const int64_t* brow,
+                                             const int64_t* bmat, const double* LinvT_all,
+                                             const double* y, XT* x) {
+  const int lane = threadIdx.x & 31;
+  const int blk = coarse_block(brow, nblk, g);
+  const int64_t r0 = brow[blk];
+  const int64_t n = brow[blk + 1] - r0, k = g - r0;
+  const double* row = LinvT_all + bmat[blk] + k * n;
+  double acc = 0.0;
+  for (int64_t i = k + lane; i < n; i += 32) acc = fma(row[i], Ld::ld(y + r0 + i), acc);
+  acc = warp_sum(acc);
+  if (lane == 0) x[g] = (XT)acc;
+}
+
+}  // namespace amg

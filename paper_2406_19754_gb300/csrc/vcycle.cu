@@ -16,7 +16,7 @@
 // and (z, q) for the PCG step.
 #include <algorithm>
 
-#include "sellk.cuh"
+#include "smooth.cuh"
 
 namespace amg {
 
@@ -28,28 +28,16 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
-       sl += nw) {
-    const T acc =
-        sell_row<TPR, T>(Ah, sl, ln, [&](int j) { return to_f(__ldg(b + j), T(0)); });
-    const int64_t i = lane_row(Ah, sl, ln);
-    if (i >= 0) r[i] = to_f(b[i], T(0)) - acc;
-  }
+       sl += nw)
+    pre_slice<TPR, LdRO>(Ah, b, r, sl, ln);
 }
 
 template <typename T>
 __global__ void k_restrict(int64_t nc, int stride, const int32_t* __restrict__ members,
                            const T* __restrict__ r, T* __restrict__ bc) {
   for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < nc;
-       I += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t* m = members + I * stride;
-    T acc = r[m[0]];
-    for (int k = 1; k < stride; ++k) {
-      const int32_t i = m[k];
-      if (i < 0) break;
-      acc = acc + r[i];
-    }
-    bc[I] = acc;
-  }
+       I += (int64_t)gridDim.x * blockDim.x)
+    bc[I] = restrict_sum<LdRO>(members + I * stride, stride, r);
 }
 
 // Epilogue of the level-0 post-smoother when it feeds PCG: t[0] = (r, z),
@@ -84,17 +72,12 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   for (int k = 0; k < ND; ++k) d[k] = 0.0;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
        sl += nw) {
-    const T acc = sell_row<TPR, T>(AP, sl, ln, [&](int J) { return __ldg(xc + J); });
-    const int64_t i = lane_row(AP, sl, ln);
+    XT zi;
+    const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi);
     double ds[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) ds[k] = 0.0;
     if (i >= 0) {
-      const T bi = to_f(b[i], T(0));
-      const T si = s[i];
-      const T yi = si * bi + xc[agg[i]];
-      const XT zi = to_f(yi + si * (r[i] - acc), XT(0));
-      x[i] = zi;
       if (NDOT > 0) ds[0] = (double)b[i] * (double)zi;
       if (NDOT > 1) ds[NDOT > 1 ? 1 : 0] = (double)zi * q[i];
     }
@@ -113,6 +96,13 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   }
   if constexpr (NDOT > 0)
     if (!slice_part) grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
+}
+
+static __global__ void k_vec_to_f32(int64_t n, const double* __restrict__ v,
+                                    float* __restrict__ w) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = (float)v[i];
 }
 
 // Dots for the single-level case (the whole preconditioner is the coarse solve).
@@ -169,50 +159,55 @@ static int slice_dots(const amg_handle* H, const double* r, const double* z, con
   return AMG_OK;
 }
 
-// Coarsest level: x = L^-T (L^-1 b) for each diagonal block (one CUDA block
-// per block, vectors staged in shared memory).
+// Coarsest level: x = L^-T (L^-1 b), one CUDA block per diagonal block.
 template <typename BT, typename XT>
 __global__ void k_coarse(const int64_t* __restrict__ brow, const int64_t* __restrict__ bmat,
                          const double* __restrict__ Linv_all,
                          const double* __restrict__ LinvT_all, const BT* __restrict__ b_all,
                          XT* __restrict__ x_all) {
   extern __shared__ double csh[];
-  const int64_t r0 = brow[blockIdx.x];
-  const int n = (int)(brow[blockIdx.x + 1] - r0);
-  const double* Linv = Linv_all + bmat[blockIdx.x];
-  const double* LinvT = LinvT_all + bmat[blockIdx.x];
-  const BT* b = b_all + r0;
-  XT* x = x_all + r0;
-  double* bs = csh;
-  double* ys = csh + n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) bs[i] = (double)b[i];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = w; i < n; i += nw) {
-    double acc = 0.0;
-    const double* row = Linv + (int64_t)i * n;
-    for (int k = lane; k <= i; k += 32) acc = fma(row[k], bs[k], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) ys[i] = acc;
-  }
-  __syncthreads();
-  for (int k = w; k < n; k += nw) {
-    double acc = 0.0;
-    const double* row = LinvT + (int64_t)k * n;
-    for (int i = k + lane; i < n; i += 32) acc = fma(row[i], ys[i], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) x[k] = (XT)acc;
-  }
+  coarse_block_solve<LdRO>(blockIdx.x, brow, bmat, Linv_all, LinvT_all, b_all, x_all, csh);
+}
+
+// Large coarsest blocks: y = L^-1 b, then x = L^-T y, one warp per row over
+// the whole GPU.
+template <typename BT>
+__global__ void k_coarse_y(int64_t nco, int nblk, const int64_t* __restrict__ brow,
+                           const int64_t* __restrict__ bmat, const double* __restrict__ Linv_all,
+                           const BT* __restrict__ b, double* __restrict__ y) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nco; g += nw)
+    coarse_y_row<LdRO>(g, nblk, brow, bmat, Linv_all, b, y);
+}
+
+template <typename XT>
+__global__ void k_coarse_x(int64_t nco, int nblk, const int64_t* __restrict__ brow,
+                           const int64_t* __restrict__ bmat,
+                           const double* __restrict__ LinvT_all, const double* __restrict__ y,
+                           XT* __restrict__ x) {
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < nco; g += nw)
+    coarse_x_row<LdRO>(g, nblk, brow, bmat, LinvT_all, y, x);
 }
 
 // ------------------------------------------------------------------ driver
 
 template <typename BT, typename XT>
 static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s) {
-  int64_t m = 0;  // largest block; <= max_dense <= 3072 keeps 2m doubles under 48 KB
+  int64_t m = 0;  // largest block
   for (int k = 0; k < H->nblk; ++k) m = std::max(m, H->cblk_row[k + 1] - H->cblk_row[k]);
-  const size_t sm = sizeof(double) * 2 * (size_t)m;
-  k_coarse<BT, XT><<<H->nblk, 1024, sm, s>>>(H->d_brow, H->d_bmat, H->Linv, H->LinvT, b, x);
+  if (m <= COARSE_SMALL) {  // one CUDA block per diagonal block; 2m doubles <= 16 KB
+    const size_t sm = sizeof(double) * 2 * (size_t)m;
+    k_coarse<BT, XT><<<H->nblk, 1024, sm, s>>>(H->d_brow, H->d_bmat, H->Linv, H->LinvT, b, x);
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+  }
+  const int grid = grid_for(H->nco * 32, 256, H->num_sms, 8);
+  k_coarse_y<BT><<<grid, 256, 0, s>>>(H->nco, H->nblk, H->d_brow, H->d_bmat, H->Linv, b,
+                                      H->coarse_y);
+  AMG_LAUNCH_CHECK();
+  k_coarse_x<XT><<<grid, 256, 0, s>>>(H->nco, H->nblk, H->d_brow, H->d_bmat, H->LinvT,
+                                      H->coarse_y, x);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -339,7 +334,8 @@ static double coarse_factor_bytes(const amg_handle* H) {
 
 template <typename T>
 static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int dots,
-                         const double* q, cudaStream_t s, Prof* prof, double* slice_part) {
+                         const double* q, cudaStream_t s, Prof* prof, double* slice_part,
+                         const float* r32 = nullptr) {
   const int nl = (int)H->L.size();
   const double vb = sizeof(T);
   auto mbytes = [&](const Level& L) {
@@ -362,17 +358,21 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
     }
     return AMG_OK;
   }
+  // Levels lt .. coarsest run in one persistent launch (tail.cu) when the
+  // handle allows it; the others get one launch per step.
+  const int lt = tail_start(H);
+  const int ldown = lt >= 0 ? lt : nl - 1;
   // downward: pre-smooth + residual, restriction
-  for (int l = 0; l < nl - 1; ++l) {
+  for (int l = 0; l < ldown; ++l) {
     const Level& L = H->L[l];
     T* r = (T*)L.r;
-    PROF_BEGIN(l, 0, bytes_pre(L, mbytes(L), vb, l == 0 ? 8.0 : vb));
+    PROF_BEGIN(l, 0, bytes_pre(L, mbytes(L), vb, l > 0 ? vb : r32 ? 4.0 : 8.0));
     if constexpr (sizeof(T) == 8) {
       const double* b = l == 0 ? r0 : (const double*)L.b;
       AMG_TRY((launch_pre<double, double, double>(H, L, L.ah64, b, r, s)));
     } else {
       if (l == 0)
-        AMG_TRY(pre_f32<double>(H, L, r0, r, s));
+        AMG_TRY(r32 ? pre_f32<float>(H, L, r32, r, s) : pre_f32<double>(H, L, r0, r, s));
       else
         AMG_TRY(pre_f32<float>(H, L, (const float*)L.b, r, s));
     }
@@ -381,14 +381,24 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
     AMG_TRY(launch_restrict<T>(H, L, r, (T*)H->L[l + 1].b, s));
     PROF_END();
   }
-  {
-    const double m = (double)H->nco;
-    PROF_BEGIN(nl - 1, 3, coarse_factor_bytes(H) + m * 2.0 * vb);
+  const double mc = (double)H->nco;
+  if (lt >= 0) {
+    double bytes = coarse_factor_bytes(H) + mc * 2.0 * vb;
+    for (int l = lt; l < nl - 1; ++l) {
+      const Level& L = H->L[l];
+      bytes += bytes_pre(L, mbytes(L), vb, vb) + bytes_restrict(L, vb) +
+               bytes_post(L, mbytes(L), vb, vb, vb);
+    }
+    PROF_BEGIN(lt, 4, bytes);
+    AMG_TRY(tail_launch<T>(H, lt, s));
+    PROF_END();
+  } else {
+    PROF_BEGIN(nl - 1, 3, coarse_factor_bytes(H) + mc * 2.0 * vb);
     AMG_TRY((coarse_solve<T, T>(H, (const T*)H->L[nl - 1].b, (T*)H->L[nl - 1].x, s)));
     PROF_END();
   }
   // upward: prolongation + post-smooth
-  for (int l = nl - 2; l >= 1; --l) {
+  for (int l = ldown - 1; l >= 1; --l) {
     const Level& L = H->L[l];
     PROF_BEGIN(l, 2, bytes_post(L, mbytes(L), vb, vb, vb));
     AMG_TRY((post_any<T, T, T, 0>(H, L, (const T*)L.b, (const T*)H->L[l + 1].x, (T*)L.x, q, s)));
@@ -410,9 +420,9 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
 }
 
 int vcycle_run(const amg_handle* H, const double* r, double* z, int dots, const double* q,
-               cudaStream_t s, double* slice_part) {
+               cudaStream_t s, double* slice_part, const float* r32) {
   if (H->opt.precision == AMG_PREC_F32)
-    return vcycle_levels<float>(H, r, z, dots, q, s, nullptr, slice_part);
+    return vcycle_levels<float>(H, r, z, dots, q, s, nullptr, slice_part, r32);
   return vcycle_levels<double>(H, r, z, dots, q, s, nullptr, slice_part);
 }
 
@@ -463,8 +473,17 @@ int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_t
                    int max_out, int* count, cudaStream_t s) {
   Prof prof;
   prof.s = s;
+  // An FP32 V-cycle inside PCG reads the FP32 copy of r that the CG update
+  // writes; the profile does the same (the copy is made before, untimed).
+  const float* r32 = nullptr;
+  if (H->opt.precision == AMG_PREC_F32 && H->r32) {
+    const int64_t n = H->L[0].n;
+    k_vec_to_f32<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, r, H->r32);
+    AMG_LAUNCH_CHECK();
+    r32 = H->r32;
+  }
   int rc = H->opt.precision == AMG_PREC_F32
-               ? vcycle_levels<float>(H, r, z, 0, nullptr, s, &prof, nullptr)
+               ? vcycle_levels<float>(H, r, z, 0, nullptr, s, &prof, nullptr, r32)
                : vcycle_levels<double>(H, r, z, 0, nullptr, s, &prof, nullptr);
   AMG_TRY(rc);
   AMG_TRY(prof.finish());
