@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
     ap.add_argument("--workload", choices=["poisson", "diffusion", "batch"], default="poisson")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--compress", action="store_true",
+                    help="2-byte column offsets in the kernels (compress_columns=1)")
     ap.add_argument("--tail-rows", type=int, default=None,
                     help="levels with at most this many rows run as one persistent launch "
                          "(0 = one launch per step; default: the library's)")
@@ -268,6 +270,8 @@ def run_ours(a):
     x = torch.zeros_like(b)
 
     tail = {} if a.tail_rows is None else {"tail_rows": a.tail_rows}
+    if a.compress:
+        tail["compress_columns"] = 1
 
     def make_hierarchy():
         if batch:
@@ -375,7 +379,9 @@ def run_ours(a):
     e1.record(stream)
     torch.cuda.synchronize()
     spmv_ms = e0.elapsed_time(e1) / 10
-    spmv_gbs = (12.0 * nnz + 16.0 * n) / (spmv_ms * 1e-3) / 1e9
+    lay = H.level_layout(0)
+    idx_bytes = 2.0 + 4.0 / lay["slice_height"] if lay["compressed"] else 4.0
+    spmv_gbs = ((8.0 + idx_bytes) * nnz + 16.0 * n) / (spmv_ms * 1e-3) / 1e9
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -420,6 +426,8 @@ def run_ours(a):
                        "operator_complexity": round(oc, 4), "iterations": it,
                        "precision": a.precision, "autotune": bool(a.autotune),
                        "tail_rows": int(H.opts.tail_rows),
+                       "level0_layout": lay,
+                       "level0_ap_layout": H.level_layout(0, ap=True) if nl > 1 else None,
                        "rhs": "uniform[0,1) seed %d" % RHS_SEED,
                        "l2": "inputs larger than L2 (matrix %.2f GB)" % (12.0 * nnz / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},

@@ -93,7 +93,12 @@ typedef struct amg_options {
                             the largest of them has at most 16384 rows (and the
                             coarsest level is one block), else a cooperative
                             grid with bounded grid barriers.  Same results bit
-                            for bit.  0 = off; default 4096 */
+                            for bit.  0 = off; default 1024 */
+  int compress_columns;  /* 1: store 2-byte column offsets where every slice
+                            allows (see amg_level_layout); 0 (default): plain
+                            4-byte indices.  Same results bit for bit; fewer
+                            bytes, but slower on GB300 (more load instructions
+                            for fewer bytes each) */
 } amg_options;
 
 /* PCG controls (Sec. 3, psb_krylov arguments). */
@@ -320,6 +325,25 @@ int amg_num_levels(const amg_handle* H, int* levels);
 
 /* Rows and stored entries of level l. */
 int amg_level_info(const amg_handle* H, int level, int64_t* n, int64_t* nnz);
+
+/*
+ * Storage of level l's matrix A in the kernels (sliced ELL, Sec. 2.2):
+ * slice height C, threads per row, stored slots (entries plus padding), and
+ * whether column indices are compressed: slot e of ELL column k of a slice
+ * then holds a 2-byte offset from a 4-byte base shared by the C slots of that
+ * column (else a plain 4-byte index).  Compression is used whenever every
+ * slice's offsets fit 16 bits; results are identical either way.  The
+ * layout of A P (the post-smoother's operator) is reported when `ap` is 1.
+ * No counterpart in the paper.  Errors: AMG_ERR_ARG (bad level, NULL out,
+ * ap = 1 on the coarsest level).
+ */
+typedef struct amg_layout {
+  int slice_height;
+  int threads_per_row;
+  int64_t slots;
+  int compressed;
+} amg_layout;
+int amg_level_layout(const amg_handle* H, int level, int ap, amg_layout* out);
 
 /*
  * Copies level-l data into caller device buffers (each may be NULL):

@@ -108,6 +108,14 @@ class Hierarchy:
         _check(self._lib.amg_level_info(self.h, l, C.byref(n), C.byref(nnz)))
         return n.value, nnz.value
 
+    def level_layout(self, l, ap=False):
+        """Kernel storage of level l's matrix (or of A P): dict with
+        slice_height, threads_per_row, slots, compressed."""
+        o = _lib.AmgLayout()
+        _check(self._lib.amg_level_layout(self.h, l, 1 if ap else 0, C.byref(o)))
+        return dict(slice_height=o.slice_height, threads_per_row=o.threads_per_row,
+                    slots=o.slots, compressed=bool(o.compressed))
+
     def level_export(self, l, stream=None):
         n, nnz = self.level_info(l)
         dev = torch.device("cuda")

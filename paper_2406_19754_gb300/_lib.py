@@ -36,7 +36,7 @@ class AmgOptions(C.Structure):
                 ("stall_ratio", C.c_double), ("max_dense", C.c_int64), ("precision", C.c_int),
                 ("bf16_from_level", C.c_int), ("slice_height", C.c_int),
                 ("threads_per_row", C.c_int), ("autotune", C.c_int),
-                ("tail_rows", C.c_int64)]
+                ("tail_rows", C.c_int64), ("compress_columns", C.c_int)]
 
 
 class PcgOptions(C.Structure):
@@ -48,6 +48,11 @@ class PcgOptions(C.Structure):
 class PcgStats(C.Structure):
     _fields_ = [("iterations", C.c_int), ("status", C.c_int), ("rel_residual", C.c_double),
                 ("true_rel_residual", C.c_double), ("solve_ms", C.c_double)]
+
+
+class AmgLayout(C.Structure):
+    _fields_ = [("slice_height", C.c_int), ("threads_per_row", C.c_int), ("slots", C.c_int64),
+                ("compressed", C.c_int)]
 
 
 class AmgKernelTime(C.Structure):
@@ -88,6 +93,7 @@ SIGNATURES = {
     "amg_twogrid_loss": (C.c_int, [_P, C.c_int, C.c_int, _P, C.POINTER(C.c_double), _P, _P]),
     "amg_num_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "amg_level_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "amg_level_layout": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(AmgLayout)]),
     "amg_level_export": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "amg_pairwise_match": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_pairwise_match_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),

@@ -21,7 +21,8 @@ int amg_default_options(amg_options* o) {
   o->slice_height = 0;
   o->threads_per_row = 0;
   o->autotune = 0;
-  o->tail_rows = 4096;
+  o->tail_rows = 1024;
+  o->compress_columns = 0;
   return AMG_OK;
 }
 
@@ -58,6 +59,7 @@ static int check_options(const amg_options& o) {
   if (!(o.stall_ratio > 0.0 && o.stall_ratio <= 1.0)) return AMG_ERR_ARG;
   if (o.precision != AMG_PREC_F64 && o.precision != AMG_PREC_F32) return AMG_ERR_ARG;
   if (o.bf16_from_level < 0 || o.tail_rows < 0) return AMG_ERR_ARG;
+  if (o.compress_columns != 0 && o.compress_columns != 1) return AMG_ERR_ARG;
   const int C = o.slice_height, t = o.threads_per_row;
   if (C != 0 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
   if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8) return AMG_ERR_ARG;
@@ -282,6 +284,17 @@ int amg_level_info(const amg_handle* H, int level, int64_t* n, int64_t* nnz) {
   if (!H || level < 0 || level >= (int)H->L.size()) return AMG_ERR_ARG;
   if (n) *n = H->L[level].n;
   if (nnz) *nnz = H->L[level].nnz;
+  return AMG_OK;
+}
+
+int amg_level_layout(const amg_handle* H, int level, int ap, amg_layout* out) {
+  if (!H || !out || level < 0 || level >= (int)H->L.size()) return AMG_ERR_ARG;
+  if (ap && level == (int)H->L.size() - 1) return AMG_ERR_ARG;
+  const Sell& M = ap ? H->L[level].AP : H->L[level].A;
+  out->slice_height = M.C;
+  out->threads_per_row = M.tpr;
+  out->slots = M.nnz_pad;
+  out->compressed = M.d16 ? 1 : 0;
   return AMG_OK;
 }
 

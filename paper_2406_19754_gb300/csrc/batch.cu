@@ -201,7 +201,7 @@ static int b_residual(const BatchRun& R, const double* b, const double* x, doubl
                       cudaStream_t s) {
   const Level& L = R.H->L[0];
   const int grid = sell_grid(L.A.nslices, R.H->num_sms);
-  AMG_DISPATCH_TPR(L.A.tpr, (k_b_residual<TPR><<<grid, SELL_BLOCK, 0, s>>>(
+  AMG_DISPATCH_TPR(sell_code(L.A), (k_b_residual<TPR><<<grid, SELL_BLOCK, 0, s>>>(
                                 a0(R.H), b, x, r, R.H->batch.part)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -216,7 +216,7 @@ static int b_body(const BatchRun& R, double* x, cudaStream_t s) {
   AMG_TRY(seg<SEG_RZ>(R, s));
   k_b_p_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), H->p, H->z, H->batch.sc);
   AMG_LAUNCH_CHECK();
-  AMG_DISPATCH_TPR(L.A.tpr, (k_b_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(
+  AMG_DISPATCH_TPR(sell_code(L.A), (k_b_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(
                                 a0(H), H->p, H->q, H->batch.part, H->batch.sc)));
   AMG_LAUNCH_CHECK();
   AMG_TRY(seg<SEG_PQ>(R, s));
@@ -275,7 +275,7 @@ int pcg_batch_run(amg_handle* H, const double* b, double* x, const pcg_options* 
     AMG_TRY(vcycle_run(H, H->r, H->z, R.dots, H->q, s, B.part));
     AMG_TRY(seg<SEG_RZ_FIRST>(R, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(H->p, H->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    AMG_DISPATCH_TPR(H->L[0].A.tpr, (k_b_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(
+    AMG_DISPATCH_TPR(sell_code(H->L[0].A), (k_b_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(
                                         a0(H), H->p, H->q, B.part, B.sc)));
     AMG_LAUNCH_CHECK();
     AMG_TRY(seg<SEG_PQ>(R, s));

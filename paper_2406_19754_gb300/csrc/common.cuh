@@ -70,6 +70,12 @@ struct Sell {
   __nv_bfloat16* v16 = nullptr;
   int64_t* row0 = nullptr;  // nslices + 1, or null
   int32_t* sys = nullptr;   // nslices, or null
+  // Compressed columns (null when some slice does not fit): ELL column k of
+  // slice s (the C slots sliceptr[s] + k*C + [0, C)) has base
+  // kbase[sliceptr[s]/C + k], and slot e holds column kbase[..] + d16[e].
+  // The kernels stream d16 (2 bytes a slot) instead of col (4 bytes).
+  uint16_t* d16 = nullptr;
+  int32_t* kbase = nullptr;
 };
 
 template <typename V>
@@ -80,6 +86,8 @@ struct SellView {
   const V* val;
   const int64_t* row0;
   const int32_t* sys;
+  const uint16_t* d16;   // compressed columns, or null
+  const int32_t* kbase;
   // first row of slice s and one past its last row
   __device__ __forceinline__ int64_t rbeg(int64_t s, int C) const {
     return row0 ? __ldg(row0 + s) : s * C;
@@ -343,8 +351,11 @@ int scan_exclusive_i64(Arena& ar, const int64_t* in, int64_t* out, int64_t n, in
 // SELL conversion (sell.cu)
 int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* col,
                   const double* val, int C, int tpr, Sell& out, cudaStream_t s,
-                  const std::vector<int64_t>* sys_off = nullptr);
+                  const std::vector<int64_t>* sys_off = nullptr, bool compress = true);
 int sell_make_copies(Arena& ar, Sell& A, int vstore, cudaStream_t s);
+// Builds A.d16 / A.kbase from A.col (left null when a slice's column offsets
+// exceed 16 bits).  Synchronous.
+int sell_compress(Arena& ar, Sell& A, cudaStream_t s);
 int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, double* y,
                 int num_sms, cudaStream_t s);
 

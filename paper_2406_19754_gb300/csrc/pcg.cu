@@ -138,10 +138,10 @@ static int launch_residual(const amg_handle* H, int mode, const double* b, const
   const int grid = sell_grid(L.A.nslices, H->num_sms);
   const SellView<double> v = view<double>(L.A, L.A.v64);
   if (mode == 0) {
-    AMG_DISPATCH_TPR(L.A.tpr, (k_residual<TPR, 0><<<grid, SELL_BLOCK, 0, s>>>(
+    AMG_DISPATCH_TPR(sell_code(L.A), (k_residual<TPR, 0><<<grid, SELL_BLOCK, 0, s>>>(
                                   v, b, x, r, H->red, H->sc, H->r32)));
   } else {
-    AMG_DISPATCH_TPR(L.A.tpr, (k_residual<TPR, 1><<<grid, SELL_BLOCK, 0, s>>>(
+    AMG_DISPATCH_TPR(sell_code(L.A), (k_residual<TPR, 1><<<grid, SELL_BLOCK, 0, s>>>(
                                   v, b, x, r, H->red, H->sc, nullptr)));
   }
   AMG_LAUNCH_CHECK();
@@ -152,7 +152,7 @@ static int launch_spmv_dot(const amg_handle* H, cudaStream_t s) {
   const Level& L = H->L[0];
   const int grid = sell_grid(L.A.nslices, H->num_sms);
   const SellView<double> v = view<double>(L.A, L.A.v64);
-  AMG_DISPATCH_TPR(L.A.tpr,
+  AMG_DISPATCH_TPR(sell_code(L.A),
                    (k_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(v, H->p, H->q, H->red, H->sc)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;

@@ -16,9 +16,48 @@ __device__ __forceinline__ void slice_rows(int64_t s, int C, int64_t n, const in
   }
 }
 
-// Slice lengths (width * C) from the CSR row lengths.
+// Slot layout of a slice.  Sorted: slot k of a row holds its k-th entry
+// (ascending columns), padding after the last one.  Aligned: the slice's ELL
+// columns are the distinct column offsets o = col - row of its rows, in
+// ascending order, and a row places each entry in the column of its offset
+// (padding where it has none), so a stencil's ELL column k holds one offset
+// and its columns differ only by the row.  Aligned is used when the distinct
+// offsets are no more than the longest row (no extra padding).  Either way a
+// row's entries are visited in ascending column order with zero-valued
+// padding in between, so every sum comes out the same.
+
+// Distinct column offsets of rows [rb, re), ascending; writes them to `u`
+// (if non-null) and returns their count, or -1 once it exceeds `cap`.
+__device__ int slice_offsets(int64_t rb, int64_t re, const int64_t* rowptr, const int32_t* col,
+                             int cap, int32_t* u) {
+  int pos[32];
+  const int m = (int)(re - rb);
+  for (int r = 0; r < m; ++r) pos[r] = 0;
+  int cnt = 0;
+  for (;;) {
+    int64_t next = INT64_MAX;
+    for (int r = 0; r < m; ++r) {
+      const int64_t i = rb + r, len = rowptr[i + 1] - rowptr[i];
+      if (pos[r] < len) {
+        const int64_t o = (int64_t)col[rowptr[i] + pos[r]] - i;
+        next = o < next ? o : next;
+      }
+    }
+    if (next == INT64_MAX) return cnt;
+    if (cnt == cap) return -1;
+    if (u) u[cnt] = (int32_t)next;
+    ++cnt;
+    for (int r = 0; r < m; ++r) {
+      const int64_t i = rb + r, len = rowptr[i + 1] - rowptr[i];
+      if (pos[r] < len && (int64_t)col[rowptr[i] + pos[r]] - i == next) ++pos[r];
+    }
+  }
+}
+
+// Slice lengths (width * C) and the aligned flag of every slice.
 __global__ void k_sell_widths(int64_t n, int64_t nslices, int C, const int64_t* row0,
-                              const int64_t* rowptr, int64_t* slen) {
+                              const int64_t* rowptr, const int32_t* col, int64_t* slen,
+                              uint8_t* aligned) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nslices) return;
   int64_t rb, re, w = 0;
@@ -27,14 +66,27 @@ __global__ void k_sell_widths(int64_t n, int64_t nslices, int C, const int64_t* 
     int64_t len = rowptr[i + 1] - rowptr[i];
     w = len > w ? len : w;
   }
+  aligned[s] = w > 0 && slice_offsets(rb, re, rowptr, col, (int)w, nullptr) >= 0;
   slen[s] = w * C;
 }
 
-// One thread per slot row of a slice: copy its entries, pad the rest.
+// Offsets of the aligned slices, stored per ELL column at sliceptr[s]/C + k.
+__global__ void k_sell_offsets(int64_t n, int64_t nslices, int C, const int64_t* row0,
+                               const int64_t* rowptr, const int32_t* col,
+                               const int64_t* sliceptr, const uint8_t* aligned, int32_t* uoff) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nslices || !aligned[s]) return;
+  int64_t rb, re;
+  slice_rows(s, C, n, row0, &rb, &re);
+  const int w = (int)((sliceptr[s + 1] - sliceptr[s]) / C);
+  slice_offsets(rb, re, rowptr, col, w, uoff + sliceptr[s] / C);
+}
+
+// One thread per slot row of a slice: place its entries, pad the rest.
 __global__ void k_sell_fill(int64_t n, int64_t ncols, int64_t nslices, int C,
                             const int64_t* row0, const int64_t* rowptr, const int32_t* col,
-                            const double* val, const int64_t* sliceptr, int32_t* ocol,
-                            double* oval) {
+                            const double* val, const int64_t* sliceptr, const uint8_t* aligned,
+                            const int32_t* uoff, int32_t* ocol, double* oval) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nslices * C) return;
   const int64_t s = t / C;
@@ -49,8 +101,31 @@ __global__ void k_sell_fill(int64_t n, int64_t ncols, int64_t nslices, int C,
     rb = rowptr[i];
     len = rowptr[i + 1] - rowptr[i];
   }
-  // padding reads a valid column: the row itself when it exists in x
-  const int32_t pad_col = (int32_t)(i < ncols ? i : ncols - 1);
+  if (aligned[s]) {
+    // ELL column k holds offset u[k]; padding reads column i + u[k] clamped
+    // into range (value 0), which keeps the ELL column's columns together
+    const int32_t* u = uoff + beg / C;
+    const int64_t ir = i < se ? i : se - 1;
+    int64_t e = 0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t dst = beg + (int64_t)k * C + r;
+      if (e < len && (int64_t)col[rb + e] - i == u[k]) {
+        ocol[dst] = col[rb + e];
+        oval[dst] = val[rb + e];
+        ++e;
+      } else {
+        int64_t c = ir + u[k];
+        c = c < 0 ? 0 : c >= ncols ? ncols - 1 : c;
+        ocol[dst] = (int32_t)c;
+        oval[dst] = 0.0;
+      }
+    }
+    return;
+  }
+  // padding (value 0) reads a valid column: the row's last one (it is in
+  // cache, and it keeps the slice's column deltas small), else the row itself
+  const int32_t pad_col =
+      len > 0 ? col[rb + len - 1] : (int32_t)(i < ncols ? i : ncols - 1);
   for (int k = 0; k < w; ++k) {
     int64_t dst = beg + (int64_t)k * C + r;
     if (k < len) {
@@ -60,6 +135,29 @@ __global__ void k_sell_fill(int64_t n, int64_t ncols, int64_t nslices, int C,
       ocol[dst] = pad_col;
       oval[dst] = 0.0;
     }
+  }
+}
+
+// Column compression, one thread per slice: for each ELL column k the base is
+// the smallest column of its C slots and every slot stores its offset from it.
+// A slice whose offsets do not fit 16 bits raises *wide (the caller then
+// keeps plain columns for the whole matrix).
+__global__ void k_sell_compress(int64_t nslices, int C, const int64_t* sliceptr,
+                                const int32_t* col, uint16_t* d16, int32_t* kbase, int* wide) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nslices) return;
+  const int64_t beg = sliceptr[s];
+  const int w = (int)((sliceptr[s + 1] - beg) / C);
+  for (int k = 0; k < w; ++k) {
+    const int32_t* c = col + beg + (int64_t)k * C;
+    int32_t lo = c[0], hi = c[0];
+    for (int r = 1; r < C; ++r) {
+      lo = c[r] < lo ? c[r] : lo;
+      hi = c[r] > hi ? c[r] : hi;
+    }
+    if ((int64_t)hi - (int64_t)lo > 65535) *wide = 1;
+    kbase[beg / C + k] = lo;
+    for (int r = 0; r < C; ++r) d16[beg + (int64_t)k * C + r] = (uint16_t)(c[r] - lo);
   }
 }
 
@@ -77,7 +175,7 @@ __global__ void k_to_bf16(int64_t n, const double* in, __nv_bfloat16* out) {
 
 int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, const int32_t* col,
                   const double* val, int C, int tpr, Sell& out, cudaStream_t s,
-                  const std::vector<int64_t>* sys_off) {
+                  const std::vector<int64_t>* sys_off, bool compress) {
   if (n <= 0 || ncols <= 0) return AMG_ERR_ARG;
   if (C * tpr != 32) return AMG_ERR_ARG;
   out.n = n;
@@ -104,10 +202,12 @@ int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, co
     AMG_CUDA_TRY(cudaStreamSynchronize(s));  // host vectors go out of scope
   }
   int64_t* slen = nullptr;
+  uint8_t* aligned = nullptr;
   AMG_TRY(ar.alloc_n(&slen, out.nslices));
+  AMG_TRY(ar.alloc_n(&aligned, out.nslices));
   AMG_TRY(ar.alloc_n(&out.sliceptr, out.nslices + 1));
-  k_sell_widths<<<(unsigned)((out.nslices + 255) / 256), 256, 0, s>>>(n, out.nslices, C,
-                                                                       out.row0, rowptr, slen);
+  const unsigned gs = (unsigned)((out.nslices + 127) / 128);
+  k_sell_widths<<<gs, 128, 0, s>>>(n, out.nslices, C, out.row0, rowptr, col, slen, aligned);
   AMG_LAUNCH_CHECK();
   int64_t total = 0;
   AMG_TRY(scan_exclusive_i64(ar, slen, out.sliceptr, out.nslices, &total, s));
@@ -117,12 +217,43 @@ int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, co
   out.nnz_pad = total;
   AMG_TRY(ar.alloc_n(&out.col, total));
   AMG_TRY(ar.alloc_n(&out.v64, total));
+  int32_t* uoff = nullptr;
+  AMG_TRY(ar.alloc_n(&uoff, total / C));
+  k_sell_offsets<<<gs, 128, 0, s>>>(n, out.nslices, C, out.row0, rowptr, col, out.sliceptr,
+                                    aligned, uoff);
+  AMG_LAUNCH_CHECK();
   int64_t rows = out.nslices * C;
   k_sell_fill<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(n, ncols, out.nslices, C, out.row0,
                                                              rowptr, col, val, out.sliceptr,
-                                                             out.col, out.v64);
+                                                             aligned, uoff, out.col, out.v64);
   AMG_LAUNCH_CHECK();
+  if (compress) AMG_TRY(sell_compress(ar, out, s));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  ar.release(aligned);
+  ar.release(uoff);
   AMG_CUDA_TRY(cudaStreamSynchronize(s));  // `total` lives on this stack frame
+  return AMG_OK;
+}
+
+int sell_compress(Arena& ar, Sell& A, cudaStream_t s) {
+  int* wide = nullptr;
+  AMG_TRY(ar.alloc_n(&A.d16, A.nnz_pad));
+  AMG_TRY(ar.alloc_n(&A.kbase, A.nnz_pad / A.C));
+  AMG_TRY(ar.alloc_n(&wide, 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(wide, 0, sizeof(int), s));
+  k_sell_compress<<<(unsigned)((A.nslices + 127) / 128), 128, 0, s>>>(
+      A.nslices, A.C, A.sliceptr, A.col, A.d16, A.kbase, wide);
+  AMG_LAUNCH_CHECK();
+  int h = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&h, wide, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  ar.release(wide);
+  if (h) {
+    ar.release(A.d16);
+    ar.release(A.kbase);
+    A.d16 = nullptr;
+    A.kbase = nullptr;
+  }
   return AMG_OK;
 }
 
@@ -158,7 +289,8 @@ int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, doubl
                 int num_sms, cudaStream_t s) {
   const int grid = sell_grid(A.nslices, num_sms);
   SellView<double> v = view(A, (const double*)A.v64);
-  AMG_DISPATCH_TPR(A.tpr, (k_spmv64<TPR><<<grid, SELL_BLOCK, 0, s>>>(v, alpha, x, beta, y)));
+  AMG_DISPATCH_TPR(sell_code(A),
+                   (k_spmv64<TPR><<<grid, SELL_BLOCK, 0, s>>>(v, alpha, x, beta, y)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }

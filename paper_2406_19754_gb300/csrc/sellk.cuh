@@ -17,9 +17,15 @@ constexpr int SELL_BLOCK = 256;  // threads per block (8 slices in flight)
 // which the streaming kernels need to keep enough loads in flight.
 #define SELL_MIN_BLOCKS 8
 
+// Layout code of a SELL kernel instantiation: threads per row (1, 2, 4 or 8)
+// plus SELL_D16 when the matrix stores compressed columns.
+constexpr int SELL_D16 = 16;
+
 template <int TPR>
 struct Lanes {
-  static constexpr int C = 32 / TPR;
+  static constexpr int W = TPR & 15;  // threads per row
+  static constexpr bool D16 = (TPR & SELL_D16) != 0;
+  static constexpr int C = 32 / W;
   int r, t;
   __device__ __forceinline__ Lanes() {
     int lane = threadIdx.x & 31;
@@ -29,47 +35,61 @@ struct Lanes {
 };
 
 // sum_k a_{row,k} * g(col_{row,k}) over the row's entries, accumulated in AccT.
+// Compressed columns (SELL_D16 in the layout code; A.d16 set) give the same j
+// for every slot, so the sum is the same bits either way.
 template <int TPR, typename AccT, typename V, typename G>
 __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const Lanes<TPR>& ln,
                                          G g) {
-  constexpr int C = Lanes<TPR>::C;
+  constexpr int C = Lanes<TPR>::C, W = Lanes<TPR>::W;
   const int64_t beg = __ldg(A.sliceptr + s);
   const int w = (int)((__ldg(A.sliceptr + s + 1) - beg) / C);
-  const int32_t* cp = A.col + beg + ln.r;
   const V* vp = A.val + beg + ln.r;
   AccT acc = AccT(0);
+  if constexpr (Lanes<TPR>::D16) {
+    const uint16_t* dp = A.d16 + beg + ln.r;
+    const int32_t* bp = A.kbase + beg / C;
 #pragma unroll 4
-  for (int k = ln.t; k < w; k += TPR) {
-    const int j = ld_stream(cp + (int64_t)k * C);
-    const AccT a = to_f(ld_stream(vp + (int64_t)k * C), AccT(0));
-    acc = fma(a, g(j), acc);
+    for (int k = ln.t; k < w; k += W) {
+      const int j = __ldg(bp + k) + (int)ld_stream(dp + (int64_t)k * C);
+      const AccT a = to_f(ld_stream(vp + (int64_t)k * C), AccT(0));
+      acc = fma(a, g(j), acc);
+    }
+  } else {
+    const int32_t* cp = A.col + beg + ln.r;
+#pragma unroll 4
+    for (int k = ln.t; k < w; k += W) {
+      const int j = ld_stream(cp + (int64_t)k * C);
+      const AccT a = to_f(ld_stream(vp + (int64_t)k * C), AccT(0));
+      acc = fma(a, g(j), acc);
+    }
   }
 #pragma unroll
   for (int o = C; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   return acc;
 }
 
-#define AMG_DISPATCH_TPR(tpr, ...)        \
-  switch (tpr) {                          \
-    case 1: {                             \
-      constexpr int TPR = 1;              \
-      __VA_ARGS__;                        \
-    } break;                              \
-    case 2: {                             \
-      constexpr int TPR = 2;              \
-      __VA_ARGS__;                        \
-    } break;                              \
-    case 4: {                             \
-      constexpr int TPR = 4;              \
-      __VA_ARGS__;                        \
-    } break;                              \
-    case 8: {                             \
-      constexpr int TPR = 8;              \
-      __VA_ARGS__;                        \
-    } break;                              \
-    default:                              \
-      return AMG_ERR_ARG;                 \
+#define AMG_SELL_CASE(code, ...) \
+  case code: {                    \
+    constexpr int TPR = code;     \
+    __VA_ARGS__;                  \
+  } break;
+
+// Runs the statement with TPR = the layout code (see Lanes) as a constant.
+#define AMG_DISPATCH_TPR(code, ...)        \
+  switch (code) {                          \
+    AMG_SELL_CASE(1, __VA_ARGS__)          \
+    AMG_SELL_CASE(2, __VA_ARGS__)          \
+    AMG_SELL_CASE(4, __VA_ARGS__)          \
+    AMG_SELL_CASE(8, __VA_ARGS__)          \
+    AMG_SELL_CASE(17, __VA_ARGS__)         \
+    AMG_SELL_CASE(18, __VA_ARGS__)         \
+    AMG_SELL_CASE(20, __VA_ARGS__)         \
+    AMG_SELL_CASE(24, __VA_ARGS__)         \
+    default:                               \
+      return AMG_ERR_ARG;                  \
   }
+
+inline int sell_code(const Sell& A) { return A.tpr | (A.d16 ? SELL_D16 : 0); }
 
 template <typename V>
 inline SellView<V> view(const Sell& A, const V* val) {
@@ -81,6 +101,8 @@ inline SellView<V> view(const Sell& A, const V* val) {
   v.val = val;
   v.row0 = A.row0;
   v.sys = A.sys;
+  v.d16 = A.d16;
+  v.kbase = A.kbase;
   return v;
 }
 

@@ -806,7 +806,7 @@ static int build_ah(Arena& ar, Level& L, int num_sms, cudaStream_t s) {
 }
 
 static int build_ap(Arena& ar, Level& L, const int64_t* rp, const int32_t* ci, const double* va,
-                    int num_sms, cudaStream_t s) {
+                    bool compress, int num_sms, cudaStream_t s) {
   const int64_t n = L.n;
   int64_t* cnt = nullptr;
   int64_t* rp_ap = nullptr;
@@ -826,7 +826,7 @@ static int build_ap(Arena& ar, Level& L, const int64_t* rp, const int32_t* ci, c
   AMG_LAUNCH_CHECK();
   L.ap_nnz = total;
   AMG_TRY(sell_from_csr(ar, n, L.nc, rp_ap, ci_ap, va_ap, L.A.C, L.A.tpr, L.AP, s,
-                        L.sys_off.empty() ? nullptr : &L.sys_off));
+                        L.sys_off.empty() ? nullptr : &L.sys_off, compress));
   if (L.vstore != VAL_F64) AMG_TRY(sell_make_copies(ar, L.AP, L.vstore, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   ar.release(cnt);
@@ -846,11 +846,13 @@ struct TuneKey {
   int nnz10;
   int vstore;
   bool batched;
+  bool compress;
   bool operator<(const TuneKey& o) const {
     if (n != o.n) return n < o.n;
     if (nnz10 != o.nnz10) return nnz10 < o.nnz10;
     if (vstore != o.vstore) return vstore < o.vstore;
-    return batched < o.batched;
+    if (batched != o.batched) return batched < o.batched;
+    return compress < o.compress;
   }
 };
 
@@ -872,7 +874,7 @@ static void tune_store(const TuneKey& k, int tpr) {
 
 static void release_sell(Arena& ar, Sell& A) {
   for (void* p : {(void*)A.sliceptr, (void*)A.col, (void*)A.v64, (void*)A.v32, (void*)A.v16,
-                  (void*)A.row0, (void*)A.sys})
+                  (void*)A.row0, (void*)A.sys, (void*)A.d16, (void*)A.kbase})
     ar.release(p);
   A = Sell();
 }
@@ -1110,18 +1112,20 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     const double* va = l == 0 ? A->val : L.val;
     const bool smooth = l + 1 < H->L.size();  // a level with a coarser one
     auto build = [&](int tpr) -> int {
+      const bool cmp = o.compress_columns != 0;
       AMG_TRY(sell_from_csr(ar, L.n, L.n, rp, ci, va, 32 / tpr, tpr, L.A, s,
-                            H->batched ? &L.sys_off : nullptr));
+                            H->batched ? &L.sys_off : nullptr, cmp));
       if (smooth) {
         AMG_TRY(build_ah(ar, L, sms, s));
-        AMG_TRY(build_ap(ar, L, rp, ci, va, sms, s));
+        AMG_TRY(build_ap(ar, L, rp, ci, va, cmp, sms, s));
       }
       return AMG_OK;
     };
     int tpr = o.threads_per_row > 0 ? o.threads_per_row : 1;
     if (o.slice_height > 0) tpr = 32 / o.slice_height;
     if (o.autotune && smooth) {
-      const TuneKey key{L.n, (int)(10 * L.nnz / L.n), L.vstore, H->batched};
+      const TuneKey key{L.n, (int)(10 * L.nnz / L.n), L.vstore, H->batched,
+                        o.compress_columns != 0};
       if (!tune_lookup(key, &tpr)) {
         float best = 1e30f;
         for (int cand : {1, 2, 4, 8}) {

@@ -47,6 +47,8 @@ struct SellDesc {
   const void* val;
   const int64_t* row0;
   const int32_t* sys;
+  const uint16_t* d16;
+  const int32_t* kbase;
   int tpr;
 };
 
@@ -98,6 +100,8 @@ __device__ __forceinline__ SellView<V> dview(const SellDesc& d) {
   v.val = (const V*)d.val;
   v.row0 = d.row0;
   v.sys = d.sys;
+  v.d16 = d.d16;
+  v.kbase = d.kbase;
   return v;
 }
 
@@ -145,26 +149,25 @@ __device__ void tail_report(const TailParams& P) {
 
 // ------------------------------------------------------------------ phases
 
-// Threads per row of a level's slices: 1, 2, 4 or 8 (the host builds no other).
-#define TAIL_TPR(tpr, ...)          \
-  switch (tpr) {                    \
-    case 1: {                       \
-      constexpr int TPR = 1;        \
-      __VA_ARGS__;                  \
-    } break;                        \
-    case 2: {                       \
-      constexpr int TPR = 2;        \
-      __VA_ARGS__;                  \
-    } break;                        \
-    case 4: {                       \
-      constexpr int TPR = 4;        \
-      __VA_ARGS__;                  \
-    } break;                        \
-    default: {                      \
-      constexpr int TPR = 8;        \
-      __VA_ARGS__;                  \
-    } break;                        \
+// Layout code of a level's matrix (threads per row, plus SELL_D16 for
+// compressed columns); the host builds no other codes.
+#define TAIL_TPR(code, ...)         \
+  switch (code) {                   \
+    AMG_SELL_CASE(1, __VA_ARGS__)   \
+    AMG_SELL_CASE(2, __VA_ARGS__)   \
+    AMG_SELL_CASE(4, __VA_ARGS__)   \
+    AMG_SELL_CASE(8, __VA_ARGS__)   \
+    AMG_SELL_CASE(17, __VA_ARGS__)  \
+    AMG_SELL_CASE(18, __VA_ARGS__)  \
+    AMG_SELL_CASE(20, __VA_ARGS__)  \
+    AMG_SELL_CASE(24, __VA_ARGS__)  \
+    default:                        \
+      break;                        \
   }
+
+__device__ __forceinline__ int dcode(const SellDesc& d) {
+  return d.tpr | (d.d16 ? SELL_D16 : 0);
+}
 
 template <int TPR, typename Ld, typename T, typename V>
 __device__ __forceinline__ void pre_rows(const TailLevel& L, int64_t gw, int64_t nw) {
@@ -188,22 +191,22 @@ __device__ __forceinline__ void post_rows(const TailLevel& L, int64_t gw, int64_
 template <typename Ld, typename T>
 __device__ void tail_pre(const TailLevel& L, int64_t gw, int64_t nw) {
   if constexpr (sizeof(T) == 8) {
-    TAIL_TPR(L.A.tpr, (pre_rows<TPR, Ld, T, double>(L, gw, nw)));
+    TAIL_TPR(dcode(L.A), (pre_rows<TPR, Ld, T, double>(L, gw, nw)));
   } else if (L.vstore == VAL_BF16) {
-    TAIL_TPR(L.A.tpr, (pre_rows<TPR, Ld, T, __nv_bfloat16>(L, gw, nw)));
+    TAIL_TPR(dcode(L.A), (pre_rows<TPR, Ld, T, __nv_bfloat16>(L, gw, nw)));
   } else {
-    TAIL_TPR(L.A.tpr, (pre_rows<TPR, Ld, T, float>(L, gw, nw)));
+    TAIL_TPR(dcode(L.A), (pre_rows<TPR, Ld, T, float>(L, gw, nw)));
   }
 }
 
 template <typename Ld, typename T>
 __device__ void tail_post(const TailLevel& L, int64_t gw, int64_t nw) {
   if constexpr (sizeof(T) == 8) {
-    TAIL_TPR(L.AP.tpr, (post_rows<TPR, Ld, T, double>(L, gw, nw)));
+    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, double>(L, gw, nw)));
   } else if (L.vstore == VAL_BF16) {
-    TAIL_TPR(L.AP.tpr, (post_rows<TPR, Ld, T, __nv_bfloat16>(L, gw, nw)));
+    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, __nv_bfloat16>(L, gw, nw)));
   } else {
-    TAIL_TPR(L.AP.tpr, (post_rows<TPR, Ld, T, float>(L, gw, nw)));
+    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, float>(L, gw, nw)));
   }
 }
 
@@ -293,6 +296,8 @@ static SellDesc desc(const Sell& A, const void* val) {
   d.val = val;
   d.row0 = A.row0;
   d.sys = A.sys;
+  d.d16 = A.d16;
+  d.kbase = A.kbase;
   d.tpr = A.tpr;
   return d;
 }
@@ -416,11 +421,16 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s) {
   for (int k = 0; k < P.nlev; ++k) {
     const Level& L = H->L[lt + k];
     const double mb = L.vstore == VAL_F64 ? 8.0 : L.vstore == VAL_F32 ? 4.0 : 2.0;
-    pf(L.A.sliceptr, 8.0 * (double)(L.A.nslices + 1));
-    pf(L.A.col, 4.0 * (double)L.A.nnz_pad);
+    for (const Sell* M : {&L.A, &L.AP}) {
+      pf(M->sliceptr, 8.0 * (double)(M->nslices + 1));
+      if (M->d16) {
+        pf(M->d16, 2.0 * (double)M->nnz_pad);
+        pf(M->kbase, 4.0 * (double)(M->nnz_pad / M->C));
+      } else {
+        pf(M->col, 4.0 * (double)M->nnz_pad);
+      }
+    }
     pf(P.lv[k].A.val, mb * (double)L.A.nnz_pad);
-    pf(L.AP.sliceptr, 8.0 * (double)(L.AP.nslices + 1));
-    pf(L.AP.col, 4.0 * (double)L.AP.nnz_pad);
     pf(P.lv[k].AP.val, mb * (double)L.AP.nnz_pad);
     pf(P.lv[k].s, vb * (double)L.n);
     pf(L.agg, 4.0 * (double)L.n);

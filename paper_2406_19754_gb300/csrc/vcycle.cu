@@ -217,7 +217,8 @@ static int launch_pre(const amg_handle* H, const Level& L, const V* ah, const BT
                       cudaStream_t s) {
   const int grid = sell_grid(L.A.nslices, H->num_sms);
   const SellView<V> v = view<V>(L.A, ah);
-  AMG_DISPATCH_TPR(L.A.tpr, (k_pre<TPR, V, T, BT><<<grid, SELL_BLOCK, 0, s>>>(v, b, r)));
+  AMG_DISPATCH_TPR(sell_code(L.A),
+                   (k_pre<TPR, V, T, BT><<<grid, SELL_BLOCK, 0, s>>>(v, b, r)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -229,8 +230,9 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
   const int grid = sell_grid(L.AP.nslices, H->num_sms);
   const SellView<V> v = view<V>(L.AP, ap);
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
-  AMG_DISPATCH_TPR(L.AP.tpr, (k_post<TPR, V, T, BT, XT, NDOT><<<grid, SELL_BLOCK, 0, s>>>(
-                                 v, b, sc, (const T*)L.r, L.agg, xc, x, q, H->red, H->sc, slice_part)));
+  AMG_DISPATCH_TPR(sell_code(L.AP),
+                   (k_post<TPR, V, T, BT, XT, NDOT><<<grid, SELL_BLOCK, 0, s>>>(
+                       v, b, sc, (const T*)L.r, L.agg, xc, x, q, H->red, H->sc, slice_part)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -302,9 +304,11 @@ struct Prof {
 };
 
 // Algorithmic bytes of each V-cycle kernel on one level: operator entries
-// (value + int32 column) once, every vector once.  mb = bytes of an operator
-// entry, vb = bytes of a V-cycle vector element, ib/ob = bytes of the level's
-// input b / output z elements (FP64 on level 0).
+// (value + column index) once, every vector once.  mb = bytes of an operator
+// entry (value + 4-byte column, or + 2-byte offset and a share of the 4-byte
+// base per C slots when the columns are compressed), vb = bytes of a V-cycle
+// vector element, ib/ob = bytes of the level's input b / output z elements
+// (FP64 on level 0).
 static double bytes_pre(const Level& L, double mb, double vb, double ib) {
   return (double)L.nnz * mb + (double)L.n * (ib + vb);  // Ah, b, r
 }
@@ -338,9 +342,12 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
                          const float* r32 = nullptr) {
   const int nl = (int)H->L.size();
   const double vb = sizeof(T);
-  auto mbytes = [&](const Level& L) {
-    return 4.0 + (L.vstore == VAL_F64 ? 8.0 : L.vstore == VAL_F32 ? 4.0 : 2.0);
+  auto entry = [&](const Level& L, const Sell& M) {
+    const double idx = M.d16 ? 2.0 + 4.0 / M.C : 4.0;
+    return idx + (L.vstore == VAL_F64 ? 8.0 : L.vstore == VAL_F32 ? 4.0 : 2.0);
   };
+  auto mbytes = [&](const Level& L) { return entry(L, L.A); };
+  auto pbytes = [&](const Level& L) { return entry(L, L.AP); };
   if (nl == 1) {
     const double m = (double)H->nco;
     PROF_BEGIN(0, 3, coarse_factor_bytes(H) + m * 16.0);
@@ -387,7 +394,7 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
     for (int l = lt; l < nl - 1; ++l) {
       const Level& L = H->L[l];
       bytes += bytes_pre(L, mbytes(L), vb, vb) + bytes_restrict(L, vb) +
-               bytes_post(L, mbytes(L), vb, vb, vb);
+               bytes_post(L, pbytes(L), vb, vb, vb);
     }
     PROF_BEGIN(lt, 4, bytes);
     AMG_TRY(tail_launch<T>(H, lt, s));
@@ -400,13 +407,13 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
   // upward: prolongation + post-smooth
   for (int l = ldown - 1; l >= 1; --l) {
     const Level& L = H->L[l];
-    PROF_BEGIN(l, 2, bytes_post(L, mbytes(L), vb, vb, vb));
+    PROF_BEGIN(l, 2, bytes_post(L, pbytes(L), vb, vb, vb));
     AMG_TRY((post_any<T, T, T, 0>(H, L, (const T*)L.b, (const T*)H->L[l + 1].x, (T*)L.x, q, s)));
     PROF_END();
   }
   const Level& L0 = H->L[0];
   const T* xc = (const T*)H->L[1].x;
-  PROF_BEGIN(0, 2, bytes_post(L0, mbytes(L0), vb, 8.0, 8.0));
+  PROF_BEGIN(0, 2, bytes_post(L0, pbytes(L0), vb, 8.0, 8.0));
   int rc;
   if (dots == 0)
     rc = post_any<T, double, double, 0>(H, L0, r0, xc, z0, q, s, slice_part);
