@@ -53,6 +53,7 @@ def _declare(L):
     L.orc_setup_systems.argtypes = [_I64, _P, _P, _P, C.c_int, _P, C.c_int, _I64, C.c_int,
                                     C.c_double, _I64, C.POINTER(C.c_int)]
     L.orc_free.argtypes = [_P]
+    L.orc_set_cycle.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
     L.orc_levels.restype = C.c_int
     L.orc_levels.argtypes = [_P]
     L.orc_level_n.restype = _I64
@@ -235,9 +236,14 @@ class Hierarchy:
     """The oracle's AMG hierarchy (levels, aggregates, smoother scales, coarse factor)."""
 
     def __init__(self, A, sweeps=2, max_coarse=200, max_levels=30, stall=0.9,
-                 max_dense=8192, omega=None, systems=None):
+                 max_dense=8192, omega=None, systems=None, smooth_sweeps=1, variable=False,
+                 coarse="cholesky", coarse_maxit=40, coarse_tol=1e-4):
         """systems: row offsets (nsys + 1) of independent systems stacked block
-        diagonally in A; coarsening then stops when each has <= max_coarse rows."""
+        diagonally in A; coarsening then stops when each has <= max_coarse rows.
+        smooth_sweeps: l1-Jacobi sweeps nu_0 before and after the coarse
+        correction; variable: nu_l = nu_0 * 2^l (variable V-cycle, Sec. 3);
+        coarse: "cholesky" (dense) or "pcg" (PCG with l1-Jacobi, at most
+        coarse_maxit iterations, stop at ||r|| <= coarse_tol ||b||)."""
         n, rp, ci, v = csr_args(A)
         self._keep = (rp, ci, v)
         st = C.c_int(0)
@@ -253,6 +259,8 @@ class Hierarchy:
         self.status = st.value
         self.n = n
         self.sweeps = sweeps
+        lib().orc_set_cycle(self.h, smooth_sweeps, 1 if variable else 0,
+                            {"cholesky": 0, "pcg": 1}[coarse], coarse_maxit, coarse_tol)
 
     def __del__(self):
         if getattr(self, "h", None):

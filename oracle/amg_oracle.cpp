@@ -38,6 +38,14 @@
 //    with w_i the damping weight (1 for plain l1-Jacobi).
 //  * Coarsening stops when n_l <= max_coarse, when n_{l+1} > 0.9 n_l, or at
 //    max_levels levels; the coarsest level is solved by dense Cholesky.
+//  * Smoother sweeps (Sec. 3, the VBM/SMATCH/VMATCH configurations): nu
+//    l1-Jacobi sweeps before and nu after the coarse correction, the first
+//    pre-sweep from a zero guess.  The variable V-cycle (VMATCH) uses nu_0
+//    sweeps on level 0, doubled on each coarser level: nu_l = nu_0 * 2^l.
+//  * Iterative coarsest solve (VBM, Sec. 3): PCG with the coarsest level's
+//    l1-Jacobi scaling as preconditioner, zero initial guess, at most maxit
+//    iterations; it stops once ||r|| <= tol * ||b|| (the paper gives only the
+//    iteration cap; the tolerance is a parameter), and on p^T A p <= 0.
 //  * Dot products: partial sums over fixed blocks of 4096 entries, then the
 //    partials in order.
 
@@ -71,6 +79,13 @@ struct Hierarchy {
   std::vector<Level> lev;
   std::vector<double> chol;  // dense lower factor of the coarsest matrix, row-major
   int64_t nco = 0;
+  // cycle: smoother sweeps nu_0, variable V-cycle (nu_l = nu_0 * 2^l), and the
+  // coarsest solver (0 dense Cholesky, 1 PCG with l1-Jacobi)
+  int nu0 = 1;
+  int variable = 0;
+  int coarse = 0;
+  int coarse_maxit = 40;
+  double coarse_tol = 1e-4;
 };
 
 // ---------------------------------------------------------------- basics
@@ -366,16 +381,63 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
   return cholesky(C.n, dense_of(C), H.chol) == 0 ? 0 : -4;
 }
 
-// V(1,1) with zero initial guess at every level (Eq. amg).
+// Coarsest solve by PCG with the l1-Jacobi preconditioner (see the header).
+void coarse_pcg(const Hierarchy& H, const double* b, double* x) {
+  const Level& L = H.lev.back();
+  const int64_t n = L.A.n;
+  std::vector<double> r(b, b + n), z(n), p(n), q(n);
+  for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+  const double bnorm = std::sqrt(dot_blocked(n, b, b));
+  if (bnorm == 0.0) return;
+  for (int64_t i = 0; i < n; ++i) z[i] = L.dinv[i] * r[i];
+  p = z;
+  double rz = dot_blocked(n, r.data(), z.data());
+  for (int k = 0; k < H.coarse_maxit; ++k) {
+    spmv(L.A, p.data(), q.data());
+    const double pq = dot_blocked(n, p.data(), q.data());
+    if (!(pq > 0.0)) break;
+    const double alpha = rz / pq;
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] = x[i] + alpha * p[i];
+      r[i] = r[i] - alpha * q[i];
+    }
+    if (std::sqrt(dot_blocked(n, r.data(), r.data())) <= H.coarse_tol * bnorm) break;
+    for (int64_t i = 0; i < n; ++i) z[i] = L.dinv[i] * r[i];
+    const double rz_new = dot_blocked(n, r.data(), z.data());
+    const double beta = rz_new / rz;
+    for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    rz = rz_new;
+  }
+}
+
+// Smoother sweeps on level l.
+int64_t sweeps_at(const Hierarchy& H, int l) {
+  return H.variable ? (int64_t)H.nu0 << l : (int64_t)H.nu0;
+}
+
+// One l1-Jacobi sweep x <- x + S (b - A x); r is scratch.
+void jacobi_sweep(const Level& L, const double* b, double* x, double* r) {
+  const int64_t n = L.A.n;
+  spmv(L.A, x, r);
+  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + L.dinv[i] * (b[i] - r[i]);
+}
+
+// V(nu, nu) cycle with zero initial guess at every level (Eq. amg); nu = 1 is
+// the V(1,1) cycle.
 void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
   const Level& L = H.lev[l];
   const int64_t n = L.A.n;
   if (l + 1 == (int)H.lev.size()) {
-    chol_solve(n, H.chol, b, x);
+    if (H.coarse == 1)
+      coarse_pcg(H, b, x);
+    else
+      chol_solve(n, H.chol, b, x);
     return;
   }
+  const int64_t nu = sweeps_at(H, l);
   std::vector<double> r(n), bc(L.nc), xc(L.nc);
-  for (int64_t i = 0; i < n; ++i) x[i] = L.dinv[i] * b[i];  // pre-smooth
+  for (int64_t i = 0; i < n; ++i) x[i] = L.dinv[i] * b[i];  // pre-smooth, zero guess
+  for (int64_t k = 1; k < nu; ++k) jacobi_sweep(L, b, x, r.data());
   spmv(L.A, x, r.data());
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];  // residual
   const int stride = 1 << H.sweeps;
@@ -390,8 +452,7 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
   }
   vcycle(H, l + 1, bc.data(), xc.data());
   for (int64_t i = 0; i < n; ++i) x[i] = x[i] + xc[L.agg[i]];  // prolongation
-  spmv(L.A, x, r.data());
-  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + L.dinv[i] * (b[i] - r[i]);  // post-smooth
+  for (int64_t k = 0; k < nu; ++k) jacobi_sweep(L, b, x, r.data());  // post-smooth
 }
 
 // ---------------------------------------------------------------- PCG
@@ -578,6 +639,17 @@ void* orc_setup_systems(int64_t n, const int64_t* rp, const int32_t* ci, const d
   *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
                   nullptr, sys);
   return H;
+}
+
+// Cycle parameters of a hierarchy (defaults: V(1,1), dense Cholesky coarsest).
+void orc_set_cycle(void* h, int nu0, int variable, int coarse, int coarse_maxit,
+                   double coarse_tol) {
+  Hierarchy* H = (Hierarchy*)h;
+  H->nu0 = nu0;
+  H->variable = variable;
+  H->coarse = coarse;
+  H->coarse_maxit = coarse_maxit;
+  H->coarse_tol = coarse_tol;
 }
 
 void orc_free(void* h) { delete (Hierarchy*)h; }
