@@ -54,6 +54,9 @@ def _args():
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
     ap.add_argument("--workload", choices=["poisson", "diffusion", "batch"], default="poisson")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--graph", choices=["loop", "iteration", "none"], default="loop",
+                    help="PCG replay: the whole loop as one graph (default), one graph per "
+                         "iteration (the host tests after each), or plain launches")
     ap.add_argument("--compress", action="store_true",
                     help="2-byte column offsets in the kernels (compress_columns=1)")
     ap.add_argument("--tail-rows", type=int, default=None,
@@ -281,12 +284,12 @@ def run_ours(a):
 
     def solve(bv, xv):
         if batch:
-            _, stats = H.pcg(bv, xv, tol=a.tol)
+            _, stats = H.pcg(bv, xv, tol=a.tol, use_graph=GRAPH_MODE[a.graph])
             worst = min(s["status"] for s in stats) if any(s["status"] < 0 for s in stats) \
                 else max(s["status"] for s in stats)
             return dict(iterations=max(s["iterations"] for s in stats), status=worst,
                         per_system=[s["iterations"] for s in stats])
-        return H.pcg(bv, xv, tol=a.tol)[1]
+        return H.pcg(bv, xv, tol=a.tol, use_graph=GRAPH_MODE[a.graph])[1]
 
     # warm the module on a small problem, then time the setup of the real one
     amg.Hierarchy(*amg.csr_to_device(poisson3d(16), dev), precision=a.precision).close()
@@ -427,6 +430,7 @@ def run_ours(a):
                        "precision": a.precision, "autotune": bool(a.autotune),
                        "tail_rows": int(H.opts.tail_rows),
                        "level0_layout": lay,
+                       "pcg_graph": a.graph,
                        "level0_ap_layout": H.level_layout(0, ap=True) if nl > 1 else None,
                        "rhs": "uniform[0,1) seed %d" % RHS_SEED,
                        "l2": "inputs larger than L2 (matrix %.2f GB)" % (12.0 * nnz / 1e9),
@@ -452,6 +456,9 @@ def run_ours(a):
     H.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+GRAPH_MODE = {"loop": 1, "iteration": 2, "none": 0}
 
 
 def main():

@@ -94,6 +94,18 @@ typedef struct amg_options {
                             coarsest level is one block), else a cooperative
                             grid with bounded grid barriers.  Same results bit
                             for bit.  0 = off; default 1024 */
+  int smooth_sweeps;     /* l1-Jacobi sweeps nu_0 before and after the coarse
+                            correction on level 0, 1..8; default 1 (V(1,1)) */
+  int variable_cycle;    /* 1: nu_l = nu_0 * 2^l sweeps on level l, the variable
+                            V-cycle of Sec. 3 (VMATCH); 0 (default): nu_0 on
+                            every level */
+  int coarse_solver;     /* 0 (default): dense Cholesky of the coarsest level;
+                            1: PCG preconditioned by its l1-Jacobi scaling
+                            (Sec. 3, VBM/VMATCH coarsest solver), one CUDA block,
+                            FP64; not for batched systems */
+  int coarse_maxit;      /* PCG coarsest solve: iteration cap, default 40 */
+  double coarse_tol;     /* PCG coarsest solve: stop at ||r|| <= tol ||b||,
+                            default 1e-4 (0: run coarse_maxit iterations) */
   int compress_columns;  /* 1: store 2-byte column offsets where every slice
                             allows (see amg_level_layout); 0 (default): plain
                             4-byte indices.  Same results bit for bit; fewer
@@ -108,8 +120,13 @@ typedef struct pcg_options {
   int beta_form;         /* PCG_BETA_* */
   double* res_history;   /* host, maxit + 1 entries or NULL: relative residuals */
   double* x_history;     /* device, (maxit + 1) * n entries or NULL: iterates */
-  int use_graph;         /* 1 (default via pcg_default_options): replay each
-                            iteration as one captured CUDA graph */
+  int use_graph;         /* 1 (default via pcg_default_options): all iterations
+                            as one captured CUDA graph whose conditional while
+                            node runs the stopping test on the device (one host
+                            wait per solve; without histories), else one graph
+                            per iteration; 2: one graph per iteration, the host
+                            testing after each; 0: plain launches.  Same
+                            results in every mode */
 } pcg_options;
 
 /* Result of a solve. */
@@ -304,16 +321,22 @@ int amg_twogrid_loss(amg_handle* H, int nsamples, int ncycles, const double* e0,
 typedef struct amg_kernel_time {
   int level;     /* hierarchy level */
   int kind;      /* 0 pre-smooth+residual, 1 restriction, 2 prolongation+post-smooth,
-                    3 coarsest-level Cholesky solve, 4 the persistent launch of
-                    levels >= `level` (all their steps and the coarsest solve) */
-  double bytes;  /* algorithmic bytes: each matrix entry (value + int32 column) and
-                    each vector entry read or written once */
+                    3 coarsest-level solve, 4 the persistent launch of levels
+                    >= `level` (all their steps and the coarsest solve), 5 a
+                    further smoothing sweep (smooth_sweeps > 1) */
+  double bytes;  /* algorithmic bytes: each matrix entry (value + column index:
+                    4 bytes, or 2 plus a share of the slice column's base when
+                    compressed) and each vector entry read or written once */
   double ms;     /* device time between CUDA events around the launch */
 } amg_kernel_time;
 
 /*
  * z = B r like amg_vcycle_apply, with a CUDA event pair around every kernel
- * (the paper reports time per iteration; this splits it per kernel).
+ * (the paper reports time per iteration; this splits it per kernel).  The
+ * kernels are the ones a PCG iteration runs: the level-0 post-smoother also
+ * forms the dot products PCG fuses into it ((r, z), and (z, q) with an FP32
+ * hierarchy, q being internal scratch), and an FP32 hierarchy first copies r
+ * to FP32 (untimed) as the CG update does.
  * out: host array of max_out records; *count receives the number of kernels
  * launched (records beyond max_out are dropped).  Synchronous.
  */

@@ -162,7 +162,7 @@ class Hierarchy:
         cnt = C.c_int()
         _check(self._lib.amg_vcycle_profile(self.h, _ptr(r), _ptr(z), recs, 256, C.byref(cnt),
                                             _stream(stream)), "amg_vcycle_profile")
-        kinds = ("pre", "restrict", "post", "coarse", "tail")
+        kinds = ("pre", "restrict", "post", "coarse", "tail", "sweep")
         out = [dict(level=k.level, kind=kinds[k.kind], bytes=k.bytes, ms=k.ms)
                for k in recs[:min(cnt.value, 256)]]
         return z, out
@@ -235,7 +235,8 @@ def _pcg_options(lib, tol, maxit, beta_form, use_graph):
     o.maxit = maxit
     o.beta_form = {"auto": PCG_BETA_AUTO, "fr": PCG_BETA_FR,
                    "flexible": PCG_BETA_FLEXIBLE}.get(beta_form, beta_form)
-    o.use_graph = 1 if use_graph else 0
+    # True / 1: whole loop as one graph; 2: one graph per iteration; False / 0: none
+    o.use_graph = int(use_graph) if not isinstance(use_graph, bool) else (1 if use_graph else 0)
     return o
 
 

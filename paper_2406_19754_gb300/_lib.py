@@ -36,7 +36,10 @@ class AmgOptions(C.Structure):
                 ("stall_ratio", C.c_double), ("max_dense", C.c_int64), ("precision", C.c_int),
                 ("bf16_from_level", C.c_int), ("slice_height", C.c_int),
                 ("threads_per_row", C.c_int), ("autotune", C.c_int),
-                ("tail_rows", C.c_int64), ("compress_columns", C.c_int)]
+                ("tail_rows", C.c_int64), ("smooth_sweeps", C.c_int),
+                ("variable_cycle", C.c_int), ("coarse_solver", C.c_int),
+                ("coarse_maxit", C.c_int), ("coarse_tol", C.c_double),
+                ("compress_columns", C.c_int)]
 
 
 class PcgOptions(C.Structure):

@@ -22,6 +22,11 @@ int amg_default_options(amg_options* o) {
   o->threads_per_row = 0;
   o->autotune = 0;
   o->tail_rows = 1024;
+  o->smooth_sweeps = 1;
+  o->variable_cycle = 0;
+  o->coarse_solver = 0;
+  o->coarse_maxit = 40;
+  o->coarse_tol = 1e-4;
   o->compress_columns = 0;
   return AMG_OK;
 }
@@ -60,6 +65,11 @@ static int check_options(const amg_options& o) {
   if (o.precision != AMG_PREC_F64 && o.precision != AMG_PREC_F32) return AMG_ERR_ARG;
   if (o.bf16_from_level < 0 || o.tail_rows < 0) return AMG_ERR_ARG;
   if (o.compress_columns != 0 && o.compress_columns != 1) return AMG_ERR_ARG;
+  if (o.smooth_sweeps < 1 || o.smooth_sweeps > 8) return AMG_ERR_ARG;
+  if (o.variable_cycle != 0 && o.variable_cycle != 1) return AMG_ERR_ARG;
+  if (o.coarse_solver != 0 && o.coarse_solver != 1) return AMG_ERR_ARG;
+  if (o.coarse_maxit < 0 || o.coarse_maxit > 100000 || !(o.coarse_tol >= 0.0))
+    return AMG_ERR_ARG;
   const int C = o.slice_height, t = o.threads_per_row;
   if (C != 0 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
   if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8) return AMG_ERR_ARG;
@@ -81,6 +91,7 @@ static void destroy(amg_handle* H) {
   if (H->bgraph) cudaGraphExecDestroy(H->bgraph);
   if (H->graph) cudaGraphExecDestroy(H->graph);
   if (H->loop) cudaGraphExecDestroy(H->loop);
+  if (H->bloop) cudaGraphExecDestroy(H->bloop);
   if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
   if (H->ev0) cudaEventDestroy(H->ev0);
   if (H->ev1) cudaEventDestroy(H->ev1);
@@ -102,6 +113,7 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   int64_t* cat_rp = nullptr;
   int32_t* cat_ci = nullptr;
   double* cat_va = nullptr;
+  if (systems && H->opt.coarse_solver != 0) return AMG_ERR_UNSUPPORTED;
   if (systems) {  // batched: one block-diagonal matrix with system-aligned slices
     int dev = 0, sms = 0;
     AMG_CUDA_TRY(cudaGetDevice(&dev));
@@ -133,7 +145,7 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   AMG_TRY(ar.alloc_n(&H->z, n));
   AMG_TRY(ar.alloc_n(&H->p, n));
   AMG_TRY(ar.alloc_n(&H->q, n));
-  if (H->opt.precision == AMG_PREC_F32 && H->L.size() > 1 && !H->batched)
+  if (H->opt.precision == AMG_PREC_F32 && H->L.size() > 1)
     AMG_TRY(ar.alloc_n(&H->r32, n));
   if (H->batched) {
     AMG_TRY(batch_init(H, s));
@@ -210,6 +222,7 @@ int pcg_solve_batch(amg_handle* H, const double* b, double* x, const pcg_options
   if (op->maxit < 0 || !(op->tol >= 0.0)) return AMG_ERR_ARG;
   if (op->beta_form < PCG_BETA_AUTO || op->beta_form > PCG_BETA_FLEXIBLE) return AMG_ERR_ARG;
   if (op->res_history || op->x_history) return AMG_ERR_ARG;  // per-system histories: not kept
+  if (op->use_graph < 0 || op->use_graph > 2) return AMG_ERR_ARG;
   return pcg_batch_run(H, b, x, op, st, (cudaStream_t)stream);
 }
 
@@ -245,6 +258,7 @@ int pcg_solve(amg_handle* H, const double* b, double* x, const pcg_options* o, p
   const pcg_options* op = o ? o : &def;
   if (op->maxit < 0 || !(op->tol >= 0.0)) return AMG_ERR_ARG;
   if (op->beta_form < PCG_BETA_AUTO || op->beta_form > PCG_BETA_FLEXIBLE) return AMG_ERR_ARG;
+  if (op->use_graph < 0 || op->use_graph > 2) return AMG_ERR_ARG;
   return pcg_run(H, b, x, op, st, (cudaStream_t)stream);
 }
 

@@ -25,7 +25,7 @@ enum { SEG_INIT = 0, SEG_RZ_FIRST = 1, SEG_PQ = 2, SEG_RR = 3, SEG_RZ = 4, SEG_T
 template <int TPR>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_b_residual(SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
-                 double* __restrict__ r, double* __restrict__ part) {
+                 double* __restrict__ r, double* __restrict__ part, float* __restrict__ r32) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
@@ -36,6 +36,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     if (i >= 0) {
       const double ri = b[i] - acc;
       r[i] = ri;
+      if (r32) r32[i] = (float)ri;
       d0 = ri * ri;
       d1 = b[i] * b[i];
     }
@@ -70,10 +71,11 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   }
 }
 
-// x += alpha_k p; r -= alpha_k q; per-tile (r, r).
+// x += alpha_k p; r -= alpha_k q; per-tile (r, r); r32 (if set) = (float) r.
 __global__ void k_b_update(SellView<double> A, double* __restrict__ x, double* __restrict__ r,
                            const double* __restrict__ p, const double* __restrict__ q,
-                           double* __restrict__ part, const Scal* __restrict__ sc) {
+                           double* __restrict__ part, const Scal* __restrict__ sc,
+                           float* __restrict__ r32) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
@@ -86,6 +88,7 @@ __global__ void k_b_update(SellView<double> A, double* __restrict__ x, double* _
       x[i] = x[i] + alpha * p[i];
       const double ri = r[i] - alpha * q[i];
       r[i] = ri;
+      if (r32) r32[i] = (float)ri;
       d += ri * ri;
     }
     d = warp_sum(d);
@@ -107,23 +110,23 @@ __global__ void k_b_p_update(SellView<double> A, double* __restrict__ p,
   }
 }
 
-// One warp per system: sums its tiles' partials in tile order (fixed tree),
-// then updates that system's scalars.
+// One CUDA block per system: each thread sums a fixed stride of its tiles'
+// partials, the block adds them by a fixed tree, and thread 0 updates that
+// system's scalars (deterministic run to run).
 template <int MODE>
 __global__ void k_b_seg(int nsys, const int64_t* __restrict__ slice_off,
                         const double* __restrict__ part, Scal* sc, double tol, int maxit,
-                        int beta_form, int* nactive) {
-  const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nsys; k += nw) {
-    double t0 = 0.0, t1 = 0.0;
-    for (int64_t sl = slice_off[k] + lane; sl < slice_off[k + 1]; sl += 32) {
-      t0 += part[2 * sl];
-      t1 += part[2 * sl + 1];
+                        int beta_form, int* nactive, int* active) {
+  for (int k = blockIdx.x; k < nsys; k += gridDim.x) {
+    double t[2] = {0.0, 0.0};
+    for (int64_t sl = slice_off[k] + threadIdx.x; sl < slice_off[k + 1]; sl += blockDim.x) {
+      t[0] += part[2 * sl];
+      t[1] += part[2 * sl + 1];
     }
-    t0 = warp_sum(t0);
-    t1 = warp_sum(t1);
-    if (lane != 0) continue;
+    block_sum<2>(t);
+    const double t0 = t[0], t1 = t[1];
+    __syncthreads();  // the block's shared scratch is reused by the next system
+    if (threadIdx.x != 0) continue;
     Scal& S = sc[k];
     if (MODE == SEG_INIT) {
       S.rr = t0;
@@ -174,6 +177,7 @@ __global__ void k_b_seg(int nsys, const int64_t* __restrict__ slice_off,
         }
       }
     }
+    active[k] = S.active;
   }
 }
 
@@ -188,9 +192,9 @@ struct BatchRun {
 template <int MODE>
 static int seg(const BatchRun& R, cudaStream_t s) {
   const Batch& B = R.H->batch;
-  const int grid = std::max(1, std::min((B.nsys * 32 + 255) / 256, R.H->num_sms * 4));
+  const int grid = std::max(1, std::min(B.nsys, R.H->num_sms * 8));
   k_b_seg<MODE><<<grid, 256, 0, s>>>(B.nsys, B.slice_off, B.part, B.sc, R.tol, R.maxit,
-                                     R.beta_form, B.nactive);
+                                     R.beta_form, B.nactive, B.active);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -198,11 +202,11 @@ static int seg(const BatchRun& R, cudaStream_t s) {
 static SellView<double> a0(const amg_handle* H) { return view<double>(H->L[0].A, H->L[0].A.v64); }
 
 static int b_residual(const BatchRun& R, const double* b, const double* x, double* r,
-                      cudaStream_t s) {
+                      float* r32, cudaStream_t s) {
   const Level& L = R.H->L[0];
   const int grid = sell_grid(L.A.nslices, R.H->num_sms);
   AMG_DISPATCH_TPR(sell_code(L.A), (k_b_residual<TPR><<<grid, SELL_BLOCK, 0, s>>>(
-                                a0(R.H), b, x, r, R.H->batch.part)));
+                                a0(R.H), b, x, r, R.H->batch.part, r32)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -212,7 +216,7 @@ static int b_body(const BatchRun& R, double* x, cudaStream_t s) {
   const amg_handle* H = R.H;
   const Level& L = H->L[0];
   const int grid = sell_grid(L.A.nslices, H->num_sms);
-  AMG_TRY(vcycle_run(H, H->r, H->z, R.dots, H->q, s, H->batch.part));
+  AMG_TRY(vcycle_run(H, H->r, H->z, R.dots, H->q, s, H->batch.part, H->r32));
   AMG_TRY(seg<SEG_RZ>(R, s));
   k_b_p_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), H->p, H->z, H->batch.sc);
   AMG_LAUNCH_CHECK();
@@ -221,10 +225,76 @@ static int b_body(const BatchRun& R, double* x, cudaStream_t s) {
   AMG_LAUNCH_CHECK();
   AMG_TRY(seg<SEG_PQ>(R, s));
   k_b_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), x, H->r, H->p, H->q, H->batch.part,
-                                         H->batch.sc);
+                                         H->batch.sc, H->r32);
   AMG_LAUNCH_CHECK();
   AMG_CUDA_TRY(cudaMemsetAsync(H->batch.nactive, 0, sizeof(int), s));
   AMG_TRY(seg<SEG_RR>(R, s));
+  return AMG_OK;
+}
+
+// Stopping test of the batched loop graph, the host loop's test on the
+// device: another iteration while a system is active and fewer than maxit
+// iterations were taken (ctl[0] counts them, ctl[1] is maxit).
+__global__ void k_b_control(const int* nactive, int* ctl, cudaGraphConditionalHandle h) {
+  const int k = ctl[0];
+  const unsigned go = (*nactive > 0 && k < ctl[1]) ? 1u : 0u;
+  if (go) ctl[0] = k + 1;
+  cudaGraphSetConditional(h, go);
+}
+
+// Per-iteration graph (host-driven loop), keyed on everything it bakes in.
+static int ensure_bgraph(amg_handle* H, const BatchRun& R, double* x) {
+  if (H->bgraph && H->bgraph_x == x && H->bgraph_beta == R.beta_form &&
+      H->bgraph_tol == R.tol && H->bgraph_maxit == R.maxit)
+    return AMG_OK;
+  if (H->bgraph) {
+    cudaGraphExecDestroy(H->bgraph);
+    H->bgraph = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  AMG_CUDA_TRY(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = b_body(R, x, H->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(H->cap_stream, &g);
+  if (rc < 0) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  AMG_CUDA_TRY(e);
+  e = cudaGraphInstantiate(&H->bgraph, g, 0);
+  cudaGraphDestroy(g);
+  AMG_CUDA_TRY(e);
+  H->bgraph_x = x;
+  H->bgraph_beta = R.beta_form;
+  H->bgraph_tol = R.tol;
+  H->bgraph_maxit = R.maxit;
+  return AMG_OK;
+}
+
+// All remaining iterations as one graph; AMG_ERR_UNSUPPORTED (remembered)
+// when the runtime cannot build it.
+static int ensure_bloop(amg_handle* H, const BatchRun& R, double* x) {
+  if (H->bloop_state < 0) return AMG_ERR_UNSUPPORTED;
+  if (H->bloop && H->bloop_x == x && H->bloop_beta == R.beta_form && H->bloop_tol == R.tol &&
+      H->bloop_maxit == R.maxit)
+    return AMG_OK;
+  if (H->bloop) {
+    cudaGraphExecDestroy(H->bloop);
+    H->bloop = nullptr;
+  }
+  const Batch& B = H->batch;
+  const int rc = build_while_graph(
+      H->cap_stream, [&](cudaStream_t cs) { return b_body(R, x, cs); },
+      [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        k_b_control<<<1, 1, 0, cs>>>(B.nactive, B.loop_ctl, h);
+      },
+      &H->bloop);
+  if (rc == AMG_ERR_UNSUPPORTED) H->bloop_state = -1;
+  if (rc < 0) return rc;
+  H->bloop_state = 1;
+  H->bloop_x = x;
+  H->bloop_beta = R.beta_form;
+  H->bloop_tol = R.tol;
+  H->bloop_maxit = R.maxit;
   return AMG_OK;
 }
 
@@ -243,48 +313,39 @@ int pcg_batch_run(amg_handle* H, const double* b, double* x, const pcg_options* 
   BatchRun R{H, o->tol, o->maxit, beta_form, beta_form == PCG_BETA_FLEXIBLE ? 2 : 1};
   const Batch& B = H->batch;
   const int grid = sell_grid(H->L[0].A.nslices, H->num_sms);
-  if (o->use_graph &&
-      !(H->bgraph && H->bgraph_x == x && H->bgraph_beta == beta_form)) {
-    if (H->bgraph) {
-      cudaGraphExecDestroy(H->bgraph);
-      H->bgraph = nullptr;
-    }
-    cudaGraph_t g = nullptr;
-    AMG_CUDA_TRY(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
-    int rc = b_body(R, x, H->cap_stream);
-    cudaError_t e = cudaStreamEndCapture(H->cap_stream, &g);
-    if (rc < 0) {
-      if (g) cudaGraphDestroy(g);
-      return rc;
-    }
-    AMG_CUDA_TRY(e);
-    e = cudaGraphInstantiate(&H->bgraph, g, 0);
-    cudaGraphDestroy(g);
-    AMG_CUDA_TRY(e);
-    H->bgraph_x = x;
-    H->bgraph_beta = beta_form;
+  bool use_loop = false;
+  if (o->use_graph == 1) {
+    const int rc = ensure_bloop(H, R, x);
+    if (rc < 0 && rc != AMG_ERR_UNSUPPORTED) return rc;
+    use_loop = rc == AMG_OK;
   }
+  if (o->use_graph && !use_loop) AMG_TRY(ensure_bgraph(H, R, x));
   AMG_CUDA_TRY(cudaEventRecord(H->ev0, s));
-  AMG_TRY(b_residual(R, b, x, H->r, s));
+  AMG_TRY(b_residual(R, b, x, H->r, H->r32, s));
   AMG_CUDA_TRY(cudaMemsetAsync(B.nactive, 0, sizeof(int), s));
   AMG_TRY(seg<SEG_INIT>(R, s));
   int act = 0;
   AMG_TRY(read_nactive(H, &act, s));
   int k = 0;
   if (act > 0) {
-    AMG_TRY(vcycle_run(H, H->r, H->z, R.dots, H->q, s, B.part));
+    AMG_TRY(vcycle_run(H, H->r, H->z, R.dots, H->q, s, B.part, H->r32));
     AMG_TRY(seg<SEG_RZ_FIRST>(R, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(H->p, H->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     AMG_DISPATCH_TPR(sell_code(H->L[0].A), (k_b_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(
                                         a0(H), H->p, H->q, B.part, B.sc)));
     AMG_LAUNCH_CHECK();
     AMG_TRY(seg<SEG_PQ>(R, s));
-    k_b_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), x, H->r, H->p, H->q, B.part, B.sc);
+    k_b_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), x, H->r, H->p, H->q, B.part, B.sc, H->r32);
     AMG_LAUNCH_CHECK();
     AMG_CUDA_TRY(cudaMemsetAsync(B.nactive, 0, sizeof(int), s));
     AMG_TRY(seg<SEG_RR>(R, s));
     k = 1;
-    for (;;) {
+    if (use_loop) {
+      const int ctl[2] = {1, o->maxit};
+      AMG_CUDA_TRY(cudaMemcpyAsync(B.loop_ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, s));
+      AMG_CUDA_TRY(cudaGraphLaunch(H->bloop, s));
+    }
+    for (; !use_loop;) {
       AMG_TRY(read_nactive(H, &act, s));
       if (act == 0 || k >= o->maxit) break;
       if (o->use_graph)
@@ -295,7 +356,7 @@ int pcg_batch_run(amg_handle* H, const double* b, double* x, const pcg_options* 
     }
   }
   AMG_CUDA_TRY(cudaEventRecord(H->ev1, s));
-  AMG_TRY(b_residual(R, b, x, H->z, s));
+  AMG_TRY(b_residual(R, b, x, H->z, nullptr, s));
   AMG_TRY(seg<SEG_TRUE>(R, s));
   AMG_CUDA_TRY(cudaMemcpyAsync(B.sc_host, B.sc, sizeof(Scal) * B.nsys, cudaMemcpyDeviceToHost, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -336,6 +397,8 @@ int batch_init(amg_handle* H, cudaStream_t s) {
   AMG_TRY(ar.alloc_n(&B.part, 2 * B.nslices));
   AMG_TRY(ar.alloc_n(&B.sc, B.nsys));
   AMG_TRY(ar.alloc_n(&B.nactive, 1));
+  AMG_TRY(ar.alloc_n(&B.loop_ctl, 2));
+  AMG_TRY(ar.alloc_n(&B.active, B.nsys));
   AMG_CUDA_TRY(cudaMallocHost((void**)&B.sc_host, sizeof(Scal) * B.nsys));
   AMG_CUDA_TRY(cudaMemcpyAsync(B.slice_off, off.data(), sizeof(int64_t) * off.size(),
                                cudaMemcpyHostToDevice, s));

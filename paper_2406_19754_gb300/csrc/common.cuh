@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <functional>
 #include <vector>
 
 #include "amg.h"
@@ -88,6 +89,10 @@ struct SellView {
   const int32_t* sys;
   const uint16_t* d16;   // compressed columns, or null
   const int32_t* kbase;
+  const int* act;        // batched PCG: per-system "still iterating" flags, or null
+  // false for a slice of a system whose solve has stopped (its results are
+  // not used), so the kernels skip it
+  __device__ __forceinline__ bool live(int64_t s) const { return !act || act[sys[s]]; }
   // first row of slice s and one past its last row
   __device__ __forceinline__ int64_t rbeg(int64_t s, int C) const {
     return row0 ? __ldg(row0 + s) : s * C;
@@ -129,6 +134,11 @@ struct Level {
   void* b = nullptr;
   void* x = nullptr;
   void* r = nullptr;
+  // smoother sweeps on this level (options smooth_sweeps / variable_cycle);
+  // with nu > 1: a second residual buffer and the pre-smoothed x
+  int64_t nu = 1;
+  void* r2 = nullptr;
+  void* xp = nullptr;
   // batched systems: first row of each system on this level (nsys + 1, host)
   std::vector<int64_t> sys_off;
 };
@@ -142,7 +152,9 @@ struct Batch {
   double* part = nullptr;        // device, 2 * nslices
   struct Scal* sc = nullptr;     // device, nsys
   struct Scal* sc_host = nullptr;  // pinned, nsys
+  int* active = nullptr;         // device, nsys: copy of each system's active flag
   int* nactive = nullptr;        // device counter
+  int* loop_ctl = nullptr;       // device: iteration count and cap of the loop graph
 };
 
 struct Scal {
@@ -205,6 +217,7 @@ struct amg_handle {
   double* Linv = nullptr;
   double* LinvT = nullptr;
   double* coarse_y = nullptr;  // nco: intermediate of the large-block coarse solve
+  double* cpcg = nullptr;      // 5 * nco: x, r, z, p, q of the PCG coarsest solve
   // PCG workspace
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   float* r32 = nullptr;  // FP32 copy of r for an FP32 V-cycle (else null)
@@ -232,6 +245,14 @@ struct amg_handle {
   cudaGraphExec_t bgraph = nullptr;
   double* bgraph_x = nullptr;
   int bgraph_beta = -2;
+  double bgraph_tol = -1.0;
+  int bgraph_maxit = -1;
+  cudaGraphExec_t bloop = nullptr;  // batched loop graph (device-side stop)
+  double* bloop_x = nullptr;
+  int bloop_beta = -2;
+  double bloop_tol = -1.0;
+  int bloop_maxit = -1;
+  int bloop_state = 0;
   void* multi = nullptr;  // multi-RHS workspace (multi.cu)
   void* tg = nullptr;     // two-grid loss workspace and inner solver (twogrid.cu)
   // persistent small-level launch (tail.cu): grid-barrier word, sticky
@@ -401,11 +422,18 @@ int time_level(const amg_handle* H, int l, int reps, const double* b64, double* 
 int tail_init(amg_handle* H, cudaStream_t s);
 int tail_start(const amg_handle* H);
 template <typename T>
-int tail_launch(const amg_handle* H, int lt, cudaStream_t s);
+int tail_launch(const amg_handle* H, int lt, cudaStream_t s, const int* act = nullptr);
 int tail_reset(amg_handle* H, cudaStream_t s);
 // Synchronous: AMG_ERR_DEVICE_CHECK (and a reset) if a persistent launch gave
 // up waiting at a barrier since the last check, else AMG_OK.
 int tail_check(amg_handle* H, cudaStream_t s);
+
+// exec = [ctl] -> while (condition) { body; ctl }, where ctl launches the
+// kernel that sets the condition through the handle (pcg.cu).
+// AMG_ERR_UNSUPPORTED if the runtime cannot build it.
+int build_while_graph(cudaStream_t cs, const std::function<int(cudaStream_t)>& body,
+                      const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& ctl,
+                      cudaGraphExec_t* out);
 
 // PCG (pcg.cu)
 int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg_stats* st,

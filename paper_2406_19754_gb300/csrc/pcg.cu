@@ -217,41 +217,38 @@ __global__ void k_pcg_control(PcgScalars* sc, cudaGraphConditionalHandle h) {
   cudaGraphSetConditional(h, go);
 }
 
-// The remaining iterations of a solve as one graph: the stopping test, then
-// a conditional while node whose body is one iteration plus the test.  The
-// host waits once per solve instead of once per iteration.
-static int build_loop(amg_handle* H, double* x, int dots, cudaGraphExec_t* out) {
-  cudaStream_t cs = H->cap_stream;
+int build_while_graph(cudaStream_t cs, const std::function<int(cudaStream_t)>& body,
+                      const std::function<void(cudaStream_t, cudaGraphConditionalHandle)>& ctl,
+                      cudaGraphExec_t* out) {
   const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
   cudaGraph_t g = nullptr;
   AMG_CUDA_TRY(cudaGraphCreate(&g, 0));
   int rc = AMG_OK;
   cudaGraphConditionalHandle h;
-  cudaGraphNode_t ctl = nullptr, wnode = nullptr;
+  cudaGraphNode_t first = nullptr, wnode = nullptr;
   size_t nn = 1;
   cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
-  cudaGraph_t body = nullptr, cap = nullptr;
+  cudaGraph_t cap = nullptr;
   cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
   if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, mode);
   if (e == cudaSuccess) {
-    k_pcg_control<<<1, 1, 0, cs>>>(H->sc, h);
+    ctl(cs, h);
     e = cudaStreamEndCapture(cs, &cap);
   }
-  if (e == cudaSuccess) e = cudaGraphGetNodes(g, &ctl, &nn);
+  if (e == cudaSuccess) e = cudaGraphGetNodes(g, &first, &nn);
   if (e == cudaSuccess && nn != 1) e = cudaErrorInvalidValue;
   if (e == cudaSuccess) {
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    e = cudaGraphAddNode(&wnode, g, &ctl, nullptr, 1, &cp);
+    e = cudaGraphAddNode(&wnode, g, &first, nullptr, 1, &cp);
   }
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      mode);
   if (e == cudaSuccess) {
-    body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, mode);
-  }
-  if (e == cudaSuccess) {
-    rc = iteration_body(H, x, dots, cs);
-    if (rc == AMG_OK) k_pcg_control<<<1, 1, 0, cs>>>(H->sc, h);
+    rc = body(cs);
+    if (rc == AMG_OK) ctl(cs, h);
     cudaGraph_t bcap = nullptr;
     e = cudaStreamEndCapture(cs, &bcap);
   }
@@ -264,6 +261,19 @@ static int build_loop(amg_handle* H, double* x, int dots, cudaGraphExec_t* out) 
     return AMG_ERR_UNSUPPORTED;
   }
   return AMG_OK;
+}
+
+// The remaining iterations of a solve as one graph: the stopping test, then
+// a conditional while node whose body is one iteration plus the test.  The
+// host waits once per solve instead of once per iteration.
+static int build_loop(amg_handle* H, double* x, int dots, cudaGraphExec_t* out) {
+  PcgScalars* sc = H->sc;
+  return build_while_graph(
+      H->cap_stream, [&](cudaStream_t cs) { return iteration_body(H, x, dots, cs); },
+      [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        k_pcg_control<<<1, 1, 0, cs>>>(sc, h);
+      },
+      out);
 }
 
 // Loop graph for (x, beta form); AMG_ERR_UNSUPPORTED (once, remembered) if
@@ -299,7 +309,7 @@ int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg
   const int dots = beta_form == PCG_BETA_FLEXIBLE ? 2 : 1;
   // one graph for the whole loop unless per-iteration histories are kept
   bool use_loop = false;
-  if (o->use_graph && !o->res_history && !o->x_history) {
+  if (o->use_graph == 1 && !o->res_history && !o->x_history) {
     const int rc = ensure_loop(H, x, dots, beta_form);
     if (rc < 0 && rc != AMG_ERR_UNSUPPORTED) return rc;
     use_loop = rc == AMG_OK;

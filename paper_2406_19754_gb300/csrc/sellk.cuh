@@ -103,6 +103,7 @@ inline SellView<V> view(const Sell& A, const V* val) {
   v.sys = A.sys;
   v.d16 = A.d16;
   v.kbase = A.kbase;
+  v.act = nullptr;
   return v;
 }
 

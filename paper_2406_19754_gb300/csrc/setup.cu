@@ -1043,11 +1043,16 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     H->L.push_back(next);
   }
   // coarsest level: dense Cholesky and its inverse factor
-  // (block diagonal for batched systems: one dense factor per system)
+  // (block diagonal for batched systems: one dense factor per system), or
+  // the work vectors of the PCG coarsest solve
   Level& Lc = H->L.back();
-  if (largest_block(Lc, Lc.n) > o.max_dense) return AMG_ERR_UNSUPPORTED;
   H->nco = Lc.n;
-  {
+  if (o.coarse_solver == 1) {
+    H->nblk = 1;
+    H->cblk_row = {0, Lc.n};
+    AMG_TRY(ar.alloc_n(&H->cpcg, 5 * Lc.n));
+  } else {
+    if (largest_block(Lc, Lc.n) > o.max_dense) return AMG_ERR_UNSUPPORTED;
     std::vector<int64_t> brow = Lc.sys_off.size() >= 2 ? Lc.sys_off
                                                         : std::vector<int64_t>{0, Lc.n};
     const int nb = (int)brow.size() - 1;
@@ -1091,10 +1096,18 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     L.vstore = VAL_F64;
     if (f32)
       L.vstore = (o.bf16_from_level > 0 && (int)l >= o.bf16_from_level) ? VAL_BF16 : VAL_F32;
+    // nu_l = nu_0, or nu_0 * 2^l for the variable V-cycle (capped at 2^30)
+    L.nu = o.variable_cycle ? (int64_t)o.smooth_sweeps << std::min<size_t>(l, 27)
+                            : o.smooth_sweeps;
     for (void** v : {&L.b, &L.x, &L.r}) {
       AMG_TRY(ar.alloc(v, vb * (size_t)L.n));
       AMG_CUDA_TRY(cudaMemsetAsync(*v, 0, vb * (size_t)L.n, s));
     }
+    if (L.nu > 1 && l + 1 < H->L.size())
+      for (void** v : {&L.r2, &L.xp}) {
+        AMG_TRY(ar.alloc(v, vb * (size_t)L.n));
+        AMG_CUDA_TRY(cudaMemsetAsync(*v, 0, vb * (size_t)L.n, s));
+      }
   }
   // sliced-ELL operators of every level, in the layout the options or the
   // autotuner choose

@@ -59,20 +59,43 @@ __device__ __forceinline__ T restrict_sum(const int32_t* m, int stride, const T*
 }
 
 // Writes x[i] = z_i for this lane's row and returns i (or -1, z untouched).
+// xp: the pre-smoothed x when more than one sweep made it (else it is S b);
+// e: if set, receives the residual b - A y of y = xp + P x_c, which further
+// post-smoothing sweeps start from.
 template <int TPR, typename Ld, typename V, typename T, typename BT, typename XT>
 __device__ __forceinline__ int64_t post_slice(const SellView<V>& AP, const BT* b, const T* s,
                                               const T* r, const int32_t* agg, const T* xc, XT* x,
-                                              int64_t sl, const Lanes<TPR>& ln, XT& z) {
+                                              int64_t sl, const Lanes<TPR>& ln, XT& z,
+                                              const T* xp = nullptr, T* e = nullptr) {
   const T acc = sell_row<TPR, T>(AP, sl, ln, [&](int J) { return Ld::ld(xc + J); });
   const int64_t i = lane_row(AP, sl, ln);
   if (i >= 0) {
-    const T bi = to_f(Ld::ld(b + i), T(0));
     const T si = s[i];
-    const T yi = si * bi + Ld::ld(xc + agg[i]);
-    z = to_f(yi + si * (Ld::ld(r + i) - acc), XT(0));
+    const T yi = (xp ? Ld::ld(xp + i) : si * to_f(Ld::ld(b + i), T(0))) + Ld::ld(xc + agg[i]);
+    const T ei = Ld::ld(r + i) - acc;
+    z = to_f(yi + si * ei, XT(0));
     x[i] = z;
+    if (e) e[i] = ei;
   }
   return i;
+}
+
+// One step of the residual recurrence of an l1-Jacobi sweep: for r = b - A x,
+// the sweep x' = x + S r leaves r' = r - (A S) r.  Gathers r through A S (one
+// element per entry), writes r' to r_out, and hands back this lane's row i
+// (-1 if none) with r_i and r'_i; the caller updates x (pre-smoother: x += S r,
+// post-smoother, which steps the residual first: y += S r').
+template <int TPR, typename Ld, typename V, typename T>
+__device__ __forceinline__ void sweep_slice(const SellView<V>& Ah, const T* s, const T* r,
+                                            T* r_out, int64_t sl, const Lanes<TPR>& ln,
+                                            T& ri, T& rn, int64_t& i) {
+  const T acc = sell_row<TPR, T>(Ah, sl, ln, [&](int j) { return Ld::ld(r + j); });
+  i = lane_row(Ah, sl, ln);
+  if (i >= 0) {
+    ri = Ld::ld(r + i);
+    rn = ri - acc;
+    r_out[i] = rn;
+  }
 }
 
 // One diagonal block of the coarsest level solved by the calling CTA:

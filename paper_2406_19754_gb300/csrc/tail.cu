@@ -49,6 +49,7 @@ struct SellDesc {
   const int32_t* sys;
   const uint16_t* d16;
   const int32_t* kbase;
+  const int* act;
   int tpr;
 };
 
@@ -76,6 +77,7 @@ struct TailParams {
   double* y;
   const void* cb;
   void* cx;
+  const int* act;  // batched PCG: per-system active flags (coarse block = system), or null
   unsigned* bar;
   unsigned unreachable;  // test hook: arrivals the barrier waits for that never come
   unsigned long long wait_ns;
@@ -102,6 +104,7 @@ __device__ __forceinline__ SellView<V> dview(const SellDesc& d) {
   v.sys = d.sys;
   v.d16 = d.d16;
   v.kbase = d.kbase;
+  v.act = d.act;
   return v;
 }
 
@@ -174,7 +177,7 @@ __device__ __forceinline__ void pre_rows(const TailLevel& L, int64_t gw, int64_t
   const Lanes<TPR> ln;
   const SellView<V> Ah = dview<V>(L.A);
   for (int64_t sl = gw; sl < Ah.nslices; sl += nw)
-    pre_slice<TPR, Ld>(Ah, (const T*)L.b, (T*)L.r, sl, ln);
+    if (Ah.live(sl)) pre_slice<TPR, Ld>(Ah, (const T*)L.b, (T*)L.r, sl, ln);
 }
 
 template <int TPR, typename Ld, typename T, typename V>
@@ -182,6 +185,7 @@ __device__ __forceinline__ void post_rows(const TailLevel& L, int64_t gw, int64_
   const Lanes<TPR> ln;
   const SellView<V> AP = dview<V>(L.AP);
   for (int64_t sl = gw; sl < AP.nslices; sl += nw) {
+    if (!AP.live(sl)) continue;
     T z;
     post_slice<TPR, Ld>(AP, (const T*)L.b, (const T*)L.s, (const T*)L.r, L.agg,
                           (const T*)L.xc, (T*)L.x, sl, ln, z);
@@ -237,7 +241,8 @@ __device__ bool tail_coarse(const TailParams& P, int64_t gw, int64_t nw, double*
   T* x = (T*)P.cx;
   if (P.small) {
     for (int blk = blockIdx.x; blk < P.nblk; blk += gridDim.x)
-      coarse_block_solve<Ld>(blk, P.brow, P.bmat, P.Linv, P.LinvT, b, x, csh);
+      if (!P.act || P.act[blk])
+        coarse_block_solve<Ld>(blk, P.brow, P.bmat, P.Linv, P.LinvT, b, x, csh);
     return true;
   }
   for (int64_t g = gw; g < P.nco; g += nw)
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(TAIL_BLOCK, 1) k_tail(const __grid_constant__ 
 
 // ------------------------------------------------------------------ host
 
-static SellDesc desc(const Sell& A, const void* val) {
+static SellDesc desc(const Sell& A, const void* val, const int* act) {
   SellDesc d;
   d.n = A.n;
   d.nslices = A.nslices;
@@ -298,6 +303,7 @@ static SellDesc desc(const Sell& A, const void* val) {
   d.sys = A.sys;
   d.d16 = A.d16;
   d.kbase = A.kbase;
+  d.act = act;
   d.tpr = A.tpr;
   return d;
 }
@@ -334,10 +340,14 @@ int tail_init(amg_handle* H, cudaStream_t s) {
 int tail_start(const amg_handle* H) {
   const int nl = (int)H->L.size();
   if (H->opt.tail_rows <= 0 || H->tail_grid <= 0 || nl < 3) return -1;
+  if (H->opt.coarse_solver != 0) return -1;  // the PCG coarsest solve has its own kernel
   int lt = 1;
   while (lt < nl - 1 && H->L[lt].n > H->opt.tail_rows) ++lt;
   lt = std::max(lt, nl - 1 - TAIL_MAX_LEVELS);
-  return lt <= nl - 2 ? lt : -1;
+  if (lt > nl - 2) return -1;
+  for (int l = lt; l < nl - 1; ++l)
+    if (H->L[l].nu > 1) return -1;  // one sweep per side only
+  return lt;
 }
 
 int tail_reset(amg_handle* H, cudaStream_t s) {
@@ -358,7 +368,7 @@ int tail_check(amg_handle* H, cudaStream_t s) {
 }
 
 template <typename T>
-int tail_launch(const amg_handle* H, int lt, cudaStream_t s) {
+int tail_launch(const amg_handle* H, int lt, cudaStream_t s, const int* act) {
   const int nl = (int)H->L.size();
   if (lt < 1 || lt > nl - 2 || nl - 1 - lt > TAIL_MAX_LEVELS || H->tail_grid <= 0)
     return AMG_ERR_ARG;
@@ -374,8 +384,8 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s) {
                          : L.vstore == VAL_BF16 ? (const void*)L.ah16 : (const void*)L.ah32;
     const void* ap = f64 ? (const void*)L.AP.v64
                          : L.vstore == VAL_BF16 ? (const void*)L.AP.v16 : (const void*)L.AP.v32;
-    d.A = desc(L.A, ah);
-    d.AP = desc(L.AP, ap);
+    d.A = desc(L.A, ah, act);
+    d.AP = desc(L.AP, ap, act);
     d.vstore = L.vstore;
     d.stride = L.stride;
     d.nc = L.nc;
@@ -401,6 +411,7 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s) {
   P.y = H->coarse_y;
   P.cb = Lc.b;
   P.cx = Lc.x;
+  P.act = act;
   P.bar = H->tail_bar;
   P.unreachable = H->tail_debug ? 1u : 0u;
   P.wait_ns = H->tail_debug ? TAIL_DEBUG_WAIT_NS : TAIL_WAIT_NS;
@@ -467,8 +478,8 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s) {
   return AMG_OK;
 }
 
-template int tail_launch<float>(const amg_handle*, int, cudaStream_t);
-template int tail_launch<double>(const amg_handle*, int, cudaStream_t);
+template int tail_launch<float>(const amg_handle*, int, cudaStream_t, const int*);
+template int tail_launch<double>(const amg_handle*, int, cudaStream_t, const int*);
 
 }  // namespace amg
 
@@ -479,8 +490,10 @@ extern "C" int amg_debug_tail_timeout(amg_handle* H, int on) {
   if (H->graph) cudaGraphExecDestroy(H->graph);
   if (H->bgraph) cudaGraphExecDestroy(H->bgraph);
   if (H->loop) cudaGraphExecDestroy(H->loop);
+  if (H->bloop) cudaGraphExecDestroy(H->bloop);
   H->graph = nullptr;
   H->bgraph = nullptr;
   H->loop = nullptr;
+  H->bloop = nullptr;
   return AMG_OK;
 }

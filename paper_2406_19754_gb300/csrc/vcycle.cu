@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
        sl += nw)
-    pre_slice<TPR, LdRO>(Ah, b, r, sl, ln);
+    if (Ah.live(sl)) pre_slice<TPR, LdRO>(Ah, b, r, sl, ln);
 }
 
 template <typename T>
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_post(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,
            const T* __restrict__ r, const int32_t* __restrict__ agg, const T* __restrict__ xc,
            XT* __restrict__ x, const double* __restrict__ q, Reduce red, PcgScalars* sc,
-           double* __restrict__ slice_part) {
+           double* __restrict__ slice_part, const T* __restrict__ xp, T* __restrict__ e) {
   // slice_part != null (batched systems): per-slice dot partials instead of
   // one grid-wide reduction; they are reduced per system afterwards.
   const Lanes<TPR> ln;
@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   for (int k = 0; k < ND; ++k) d[k] = 0.0;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
        sl += nw) {
+    if (!AP.live(sl)) continue;  // warp-uniform
     XT zi;
-    const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi);
+    const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi, xp, e);
     double ds[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) ds[k] = 0.0;
@@ -96,6 +97,46 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   }
   if constexpr (NDOT > 0)
     if (!slice_part) grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
+}
+
+// Pre-smoothing sweeps 2..nu on the residual recurrence: x += S r (x = S b
+// before the first of them), r_out = r - (A S) r.
+template <int TPR, typename V, typename T, typename BT>
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
+    k_sweep_pre(SellView<V> Ah, const T* __restrict__ s, const BT* __restrict__ b,
+                const T* __restrict__ r, T* __restrict__ r_out, T* __restrict__ x, int first) {
+  const Lanes<TPR> ln;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
+       sl += nw) {
+    if (!Ah.live(sl)) continue;
+    T ri = T(0), rn = T(0);
+    int64_t i;
+    sweep_slice<TPR, LdRO>(Ah, s, r, r_out, sl, ln, ri, rn, i);
+    if (i >= 0) {
+      const T si = s[i];
+      const T xi = first ? si * to_f(b[i], T(0)) : x[i];
+      x[i] = xi + si * ri;
+    }
+  }
+}
+
+// Post-smoothing sweeps 2..nu: r_out = r - (A S) r (the residual of y after
+// its last update), then y += S r_out.
+template <int TPR, typename V, typename T, typename YT>
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
+    k_sweep_post(SellView<V> Ah, const T* __restrict__ s, const T* __restrict__ r,
+                 T* __restrict__ r_out, YT* __restrict__ y) {
+  const Lanes<TPR> ln;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
+       sl += nw) {
+    if (!Ah.live(sl)) continue;
+    T ri = T(0), rn = T(0);
+    int64_t i;
+    sweep_slice<TPR, LdRO>(Ah, s, r, r_out, sl, ln, ri, rn, i);
+    if (i >= 0) y[i] = y[i] + to_f(s[i] * rn, YT(0));
+  }
 }
 
 static __global__ void k_vec_to_f32(int64_t n, const double* __restrict__ v,
@@ -164,8 +205,9 @@ template <typename BT, typename XT>
 __global__ void k_coarse(const int64_t* __restrict__ brow, const int64_t* __restrict__ bmat,
                          const double* __restrict__ Linv_all,
                          const double* __restrict__ LinvT_all, const BT* __restrict__ b_all,
-                         XT* __restrict__ x_all) {
+                         XT* __restrict__ x_all, const int* __restrict__ act) {
   extern __shared__ double csh[];
+  if (act && !act[blockIdx.x]) return;  // block = system of a batch; stopped
   coarse_block_solve<LdRO>(blockIdx.x, brow, bmat, Linv_all, LinvT_all, b_all, x_all, csh);
 }
 
@@ -190,15 +232,96 @@ __global__ void k_coarse_x(int64_t nco, int nblk, const int64_t* __restrict__ br
     coarse_x_row<LdRO>(g, nblk, brow, bmat, LinvT_all, y, x);
 }
 
+// Coarsest solve by PCG with the l1-Jacobi preconditioner (s = 1/d of the
+// coarsest level; Sec. 3, the VBM/VMATCH coarsest solver), zero initial guess,
+// in one CUDA block: at most maxit iterations, stopping once ||r|| <= tol ||b||
+// or when p^T A p <= 0.  FP64 throughout; dot products by a fixed block tree.
+// w: 5n doubles of scratch (x, r, z, p, q).
+__device__ double block_dot(int64_t n, const double* u, const double* v) {
+  __shared__ double total;
+  double t[1] = {0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t[0] += u[i] * v[i];
+  block_sum<1>(t);
+  if (threadIdx.x == 0) total = t[0];
+  __syncthreads();
+  const double res = total;
+  __syncthreads();
+  return res;
+}
+
+template <int TPR, typename BT, typename XT>
+__global__ void __launch_bounds__(1024, 1)
+    k_coarse_pcg(SellView<double> A, const double* __restrict__ sinv, const BT* __restrict__ b,
+                 XT* __restrict__ xo, double* w, int maxit, double tol) {
+  const int64_t n = A.n;
+  double* x = w;
+  double* r = w + n;
+  double* z = w + 2 * n;
+  double* p = w + 3 * n;
+  double* q = w + 4 * n;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    x[i] = 0.0;
+    r[i] = (double)b[i];
+  }
+  __syncthreads();
+  const double bnorm = sqrt(block_dot(n, r, r));
+  if (bnorm > 0.0) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      z[i] = sinv[i] * r[i];
+      p[i] = z[i];
+    }
+    __syncthreads();
+    double rz = block_dot(n, r, z);
+    const Lanes<TPR> ln;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = 0; k < maxit; ++k) {
+      for (int64_t sl = warp; sl < A.nslices; sl += nwarps) {
+        const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return p[j]; });
+        const int64_t i = lane_row(A, sl, ln);
+        if (i >= 0) q[i] = acc;
+      }
+      __syncthreads();
+      const double pq = block_dot(n, p, q);
+      if (!(pq > 0.0)) break;
+      const double alpha = rz / pq;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        x[i] = x[i] + alpha * p[i];
+        r[i] = r[i] - alpha * q[i];
+      }
+      __syncthreads();
+      if (sqrt(block_dot(n, r, r)) <= tol * bnorm) break;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) z[i] = sinv[i] * r[i];
+      __syncthreads();
+      const double rzn = block_dot(n, r, z);
+      const double beta = rzn / rz;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
+      __syncthreads();
+      rz = rzn;
+    }
+  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xo[i] = bnorm > 0.0 ? (XT)x[i] : XT(0);
+}
+
 // ------------------------------------------------------------------ driver
 
 template <typename BT, typename XT>
-static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s) {
+static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s,
+                        const int* act = nullptr) {
+  if (H->opt.coarse_solver == 1) {  // PCG with l1-Jacobi (non-batched handles only)
+    const Level& Lc = H->L.back();
+    const SellView<double> v = view<double>(Lc.A, Lc.A.v64);
+    AMG_DISPATCH_TPR(sell_code(Lc.A), (k_coarse_pcg<TPR, BT, XT><<<1, 1024, 0, s>>>(
+                                          v, Lc.s64, b, x, H->cpcg, H->opt.coarse_maxit,
+                                          H->opt.coarse_tol)));
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+  }
   int64_t m = 0;  // largest block
   for (int k = 0; k < H->nblk; ++k) m = std::max(m, H->cblk_row[k + 1] - H->cblk_row[k]);
   if (m <= COARSE_SMALL) {  // one CUDA block per diagonal block; 2m doubles <= 16 KB
     const size_t sm = sizeof(double) * 2 * (size_t)m;
-    k_coarse<BT, XT><<<H->nblk, 1024, sm, s>>>(H->d_brow, H->d_bmat, H->Linv, H->LinvT, b, x);
+    k_coarse<BT, XT><<<H->nblk, 1024, sm, s>>>(H->d_brow, H->d_bmat, H->Linv, H->LinvT, b, x,
+                                               act);
     AMG_LAUNCH_CHECK();
     return AMG_OK;
   }
@@ -212,29 +335,74 @@ static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s)
   return AMG_OK;
 }
 
+// act: per-system active flags of a batched PCG (slices of stopped systems
+// are skipped), or null.
 template <typename V, typename T, typename BT>
 static int launch_pre(const amg_handle* H, const Level& L, const V* ah, const BT* b, T* r,
-                      cudaStream_t s) {
+                      cudaStream_t s, const int* act = nullptr) {
   const int grid = sell_grid(L.A.nslices, H->num_sms);
-  const SellView<V> v = view<V>(L.A, ah);
+  SellView<V> v = view<V>(L.A, ah);
+  v.act = act;
   AMG_DISPATCH_TPR(sell_code(L.A),
                    (k_pre<TPR, V, T, BT><<<grid, SELL_BLOCK, 0, s>>>(v, b, r)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
 
+// Post-smoother operands of a level with several sweeps: the final
+// pre-smoothing residual, the pre-smoothed x, and where the residual of
+// y = xp + P x_c goes (null for one sweep: r is L.r and xp is S b).
+template <typename T>
+struct PostIn {
+  const T* r = nullptr;
+  const T* xp = nullptr;
+  T* e = nullptr;
+};
+
 template <typename V, typename T, typename BT, typename XT, int NDOT>
 static int launch_post(const amg_handle* H, const Level& L, const V* ap, const BT* b,
                        const T* xc, XT* x, const double* q, cudaStream_t s,
-                       double* slice_part) {
+                       double* slice_part, const int* act, const PostIn<T>& in) {
   const int grid = sell_grid(L.AP.nslices, H->num_sms);
-  const SellView<V> v = view<V>(L.AP, ap);
+  SellView<V> v = view<V>(L.AP, ap);
+  v.act = act;
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
+  const T* r = in.r ? in.r : (const T*)L.r;
   AMG_DISPATCH_TPR(sell_code(L.AP),
                    (k_post<TPR, V, T, BT, XT, NDOT><<<grid, SELL_BLOCK, 0, s>>>(
-                       v, b, sc, (const T*)L.r, L.agg, xc, x, q, H->red, H->sc, slice_part)));
+                       v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, slice_part, in.xp,
+                       in.e)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
+}
+
+// One further pre- (PRE) or post-smoothing sweep of level L on the residual
+// recurrence (k_sweep_pre / k_sweep_post).
+template <bool PRE, typename T, typename BT, typename YT>
+static int launch_sweep(const amg_handle* H, const Level& L, const BT* b, const T* r, T* r_out,
+                        YT* x, int first, cudaStream_t s, const int* act) {
+  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
+  auto go = [&](auto vtag, const auto* ah) -> int {
+    using V = decltype(vtag);
+    SellView<V> v = view<V>(L.A, ah);
+    v.act = act;
+    if constexpr (PRE) {
+      AMG_DISPATCH_TPR(sell_code(L.A), (k_sweep_pre<TPR, V, T, BT><<<grid, SELL_BLOCK, 0, s>>>(
+                                            v, sc, b, r, r_out, (T*)x, first)));
+    } else {
+      AMG_DISPATCH_TPR(sell_code(L.A), (k_sweep_post<TPR, V, T, YT><<<grid, SELL_BLOCK, 0, s>>>(
+                                            v, sc, r, r_out, x)));
+    }
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+  };
+  if constexpr (sizeof(T) == 8) {
+    return go(double(0), L.ah64);
+  } else {
+    if (L.vstore == VAL_BF16) return go(__nv_bfloat16(), L.ah16);
+    return go(float(0), L.ah32);
+  }
 }
 
 template <typename T>
@@ -247,20 +415,26 @@ static int launch_restrict(const amg_handle* H, const Level& L, const T* r, T* b
 }
 
 template <typename BT>
-static int pre_f32(const amg_handle* H, const Level& L, const BT* b, float* r, cudaStream_t s) {
-  if (L.vstore == VAL_BF16) return launch_pre<__nv_bfloat16, float, BT>(H, L, L.ah16, b, r, s);
-  return launch_pre<float, float, BT>(H, L, L.ah32, b, r, s);
+static int pre_f32(const amg_handle* H, const Level& L, const BT* b, float* r, cudaStream_t s,
+                   const int* act = nullptr) {
+  if (L.vstore == VAL_BF16)
+    return launch_pre<__nv_bfloat16, float, BT>(H, L, L.ah16, b, r, s, act);
+  return launch_pre<float, float, BT>(H, L, L.ah32, b, r, s, act);
 }
 
 template <typename T, typename BT, typename XT, int NDOT>
 static int post_any(const amg_handle* H, const Level& L, const BT* b, const T* xc, XT* x,
-                    const double* q, cudaStream_t s, double* slice_part = nullptr) {
+                    const double* q, cudaStream_t s, double* slice_part = nullptr,
+                    const int* act = nullptr, const PostIn<T>& in = PostIn<T>()) {
   if constexpr (sizeof(T) == 8) {
-    return launch_post<double, T, BT, XT, NDOT>(H, L, L.AP.v64, b, xc, x, q, s, slice_part);
+    return launch_post<double, T, BT, XT, NDOT>(H, L, L.AP.v64, b, xc, x, q, s, slice_part,
+                                                 act, in);
   } else {
     if (L.vstore == VAL_BF16)
-      return launch_post<__nv_bfloat16, T, BT, XT, NDOT>(H, L, L.AP.v16, b, xc, x, q, s, slice_part);
-    return launch_post<float, T, BT, XT, NDOT>(H, L, L.AP.v32, b, xc, x, q, s, slice_part);
+      return launch_post<__nv_bfloat16, T, BT, XT, NDOT>(H, L, L.AP.v16, b, xc, x, q, s,
+                                                          slice_part, act, in);
+    return launch_post<float, T, BT, XT, NDOT>(H, L, L.AP.v32, b, xc, x, q, s, slice_part,
+                                                act, in);
   }
 }
 
@@ -342,17 +516,16 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
                          const float* r32 = nullptr) {
   const int nl = (int)H->L.size();
   const double vb = sizeof(T);
+  // batched PCG (slice partials requested): skip the systems that stopped
+  const int* act = slice_part ? H->batch.active : nullptr;
   auto entry = [&](const Level& L, const Sell& M) {
     const double idx = M.d16 ? 2.0 + 4.0 / M.C : 4.0;
     return idx + (L.vstore == VAL_F64 ? 8.0 : L.vstore == VAL_F32 ? 4.0 : 2.0);
   };
   auto mbytes = [&](const Level& L) { return entry(L, L.A); };
   auto pbytes = [&](const Level& L) { return entry(L, L.AP); };
-  if (nl == 1) {
-    const double m = (double)H->nco;
-    PROF_BEGIN(0, 3, coarse_factor_bytes(H) + m * 16.0);
-    AMG_TRY(coarse_solve<double, double>(H, r0, z0, s));
-    PROF_END();
+  // (r, z) and (z, q) for PCG when they are not fused into the last kernel
+  auto separate_dots = [&]() -> int {
     if (dots > 0 && slice_part) {
       AMG_TRY(slice_dots(H, r0, z0, q, dots, slice_part, s));
     } else if (dots > 0) {
@@ -364,7 +537,21 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
       AMG_LAUNCH_CHECK();
     }
     return AMG_OK;
+  };
+  if (nl == 1) {
+    const double m = (double)H->nco;
+    PROF_BEGIN(0, 3, coarse_factor_bytes(H) + m * 16.0);
+    AMG_TRY(coarse_solve<double, double>(H, r0, z0, s, act));
+    PROF_END();
+    return separate_dots();
   }
+  // Levels with nu > 1 sweeps alternate two residual buffers: cur[l] says
+  // which one holds the current residual.
+  std::vector<int> cur(nl, 0);
+  auto rbuf = [&](const Level& L, int k) { return (T*)(k == 0 ? L.r : L.r2); };
+  auto sweep_bytes = [&](const Level& L) {  // A S, r in and out, s, x read and written
+    return (double)L.nnz * mbytes(L) + (double)L.n * 5.0 * vb;
+  };
   // Levels lt .. coarsest run in one persistent launch (tail.cu) when the
   // handle allows it; the others get one launch per step.
   const int lt = tail_start(H);
@@ -376,16 +563,32 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
     PROF_BEGIN(l, 0, bytes_pre(L, mbytes(L), vb, l > 0 ? vb : r32 ? 4.0 : 8.0));
     if constexpr (sizeof(T) == 8) {
       const double* b = l == 0 ? r0 : (const double*)L.b;
-      AMG_TRY((launch_pre<double, double, double>(H, L, L.ah64, b, r, s)));
+      AMG_TRY((launch_pre<double, double, double>(H, L, L.ah64, b, r, s, act)));
     } else {
       if (l == 0)
-        AMG_TRY(r32 ? pre_f32<float>(H, L, r32, r, s) : pre_f32<double>(H, L, r0, r, s));
+        AMG_TRY(r32 ? pre_f32<float>(H, L, r32, r, s, act)
+                    : pre_f32<double>(H, L, r0, r, s, act));
       else
-        AMG_TRY(pre_f32<float>(H, L, (const float*)L.b, r, s));
+        AMG_TRY(pre_f32<float>(H, L, (const float*)L.b, r, s, act));
     }
     PROF_END();
+    for (int64_t k = 2; k <= L.nu; ++k) {  // further pre-smoothing sweeps
+      const int c = cur[l];
+      PROF_BEGIN(l, 5, sweep_bytes(L));
+      if (l > 0)
+        AMG_TRY((launch_sweep<true, T, T, T>(H, L, (const T*)L.b, rbuf(L, c), rbuf(L, 1 - c),
+                                             (T*)L.xp, k == 2, s, act)));
+      else if (sizeof(T) == 4 && r32)
+        AMG_TRY((launch_sweep<true, T, float, T>(H, L, r32, rbuf(L, c), rbuf(L, 1 - c),
+                                                 (T*)L.xp, k == 2, s, act)));
+      else
+        AMG_TRY((launch_sweep<true, T, double, T>(H, L, r0, rbuf(L, c), rbuf(L, 1 - c),
+                                                  (T*)L.xp, k == 2, s, act)));
+      PROF_END();
+      cur[l] = 1 - c;
+    }
     PROF_BEGIN(l, 1, bytes_restrict(L, vb));
-    AMG_TRY(launch_restrict<T>(H, L, r, (T*)H->L[l + 1].b, s));
+    AMG_TRY(launch_restrict<T>(H, L, rbuf(L, cur[l]), (T*)H->L[l + 1].b, s));
     PROF_END();
   }
   const double mc = (double)H->nco;
@@ -397,32 +600,65 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
                bytes_post(L, pbytes(L), vb, vb, vb);
     }
     PROF_BEGIN(lt, 4, bytes);
-    AMG_TRY(tail_launch<T>(H, lt, s));
+    AMG_TRY(tail_launch<T>(H, lt, s, act));
     PROF_END();
   } else {
     PROF_BEGIN(nl - 1, 3, coarse_factor_bytes(H) + mc * 2.0 * vb);
-    AMG_TRY((coarse_solve<T, T>(H, (const T*)H->L[nl - 1].b, (T*)H->L[nl - 1].x, s)));
+    AMG_TRY((coarse_solve<T, T>(H, (const T*)H->L[nl - 1].b, (T*)H->L[nl - 1].x, s, act)));
     PROF_END();
   }
+  // The post-smoother of a level with nu > 1 sweeps: the first sweep also
+  // keeps the residual of y = xp + P x_c, the others step the recurrence.
+  auto post_in = [&](const Level& L, int l) {
+    PostIn<T> in;
+    if (L.nu > 1) {
+      in.r = rbuf(L, cur[l]);
+      in.xp = (const T*)L.xp;
+      in.e = rbuf(L, 1 - cur[l]);
+      cur[l] = 1 - cur[l];
+    }
+    return in;
+  };
+  auto post_sweeps = [&](const Level& L, int l, auto* y) -> int {
+    for (int64_t m = 2; m <= L.nu; ++m) {
+      const int c = cur[l];
+      PROF_BEGIN(l, 5, sweep_bytes(L));
+      AMG_TRY((launch_sweep<false, T, T>(H, L, (const T*)nullptr, rbuf(L, c), rbuf(L, 1 - c), y,
+                                         0, s, act)));
+      PROF_END();
+      cur[l] = 1 - c;
+    }
+    return AMG_OK;
+  };
   // upward: prolongation + post-smooth
   for (int l = ldown - 1; l >= 1; --l) {
     const Level& L = H->L[l];
     PROF_BEGIN(l, 2, bytes_post(L, pbytes(L), vb, vb, vb));
-    AMG_TRY((post_any<T, T, T, 0>(H, L, (const T*)L.b, (const T*)H->L[l + 1].x, (T*)L.x, q, s)));
+    AMG_TRY((post_any<T, T, T, 0>(H, L, (const T*)L.b, (const T*)H->L[l + 1].x, (T*)L.x, q, s,
+                                  nullptr, act, post_in(L, l))));
     PROF_END();
+    AMG_TRY(post_sweeps(L, l, (T*)L.x));
   }
   const Level& L0 = H->L[0];
   const T* xc = (const T*)H->L[1].x;
-  PROF_BEGIN(0, 2, bytes_post(L0, pbytes(L0), vb, 8.0, 8.0));
+  // one sweep: the dot products are fused into the post-smoother; several:
+  // they follow the last sweep
+  const int fused = L0.nu > 1 ? 0 : dots;
+  PROF_BEGIN(0, 2, bytes_post(L0, pbytes(L0), vb, 8.0, 8.0) + (fused > 1 ? 8.0 * L0.n : 0.0));
+  const PostIn<T> in0 = post_in(L0, 0);
   int rc;
-  if (dots == 0)
-    rc = post_any<T, double, double, 0>(H, L0, r0, xc, z0, q, s, slice_part);
-  else if (dots == 1)
-    rc = post_any<T, double, double, 1>(H, L0, r0, xc, z0, q, s, slice_part);
+  if (fused == 0)
+    rc = post_any<T, double, double, 0>(H, L0, r0, xc, z0, q, s, slice_part, act, in0);
+  else if (fused == 1)
+    rc = post_any<T, double, double, 1>(H, L0, r0, xc, z0, q, s, slice_part, act, in0);
   else
-    rc = post_any<T, double, double, 2>(H, L0, r0, xc, z0, q, s, slice_part);
+    rc = post_any<T, double, double, 2>(H, L0, r0, xc, z0, q, s, slice_part, act, in0);
   AMG_TRY(rc);
   PROF_END();
+  if (L0.nu > 1) {
+    AMG_TRY(post_sweeps(L0, 0, z0));
+    AMG_TRY(separate_dots());
+  }
   return AMG_OK;
 }
 
@@ -489,9 +725,12 @@ int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_t
     AMG_LAUNCH_CHECK();
     r32 = H->r32;
   }
+  // the level-0 post-smoother with the dot products PCG fuses into it: (r, z)
+  // for FP64, (r, z) and (z, q) for the flexible FP32 form (q: scratch)
+  const int dots = H->opt.precision == AMG_PREC_F32 ? 2 : 1;
   int rc = H->opt.precision == AMG_PREC_F32
-               ? vcycle_levels<float>(H, r, z, 0, nullptr, s, &prof, nullptr, r32)
-               : vcycle_levels<double>(H, r, z, 0, nullptr, s, &prof, nullptr);
+               ? vcycle_levels<float>(H, r, z, dots, H->q, s, &prof, nullptr, r32)
+               : vcycle_levels<double>(H, r, z, dots, H->q, s, &prof, nullptr);
   AMG_TRY(rc);
   AMG_TRY(prof.finish());
   const int m = (int)prof.rec.size();

@@ -48,3 +48,26 @@ def test_loop_graph_reused_and_rebuilt(amg):
     # a zero right-hand side stops before the first iteration
     x0, i0 = H.pcg(torch.zeros_like(b), tol=1e-8)
     assert i0["iterations"] == 0 and i0["status"] == 0 and not torch.any(x0)
+
+
+def _batch_systems():
+    return [poisson3d(14, 12, 10), diffusion3d(np.exp(gaussian_field((16, 14, 12), 1.5, 3.0, 3))),
+            poisson3d(9), diffusion3d(np.exp(gaussian_field((20, 10, 8), 0.7, 2.0, 4)))]
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_batch_loop_graph_matches_host_loop(amg, precision):
+    Ad = [amg.csr_to_device(S) for S in _batch_systems()]
+    H = amg.BatchHierarchy(Ad, precision=precision, max_coarse=30)
+    b = torch.as_tensor(uniform01(5, H.n), device="cuda")
+    x1, s1 = H.pcg(b, tol=1e-9)                    # loop graph
+    x2, s2 = H.pcg(b, tol=1e-9, use_graph=False)   # host loop, plain launches
+    assert [s["iterations"] for s in s1] == [s["iterations"] for s in s2]
+    assert [s["status"] for s in s1] == [s["status"] for s in s2] == [0] * 4
+    assert torch.equal(x1, x2)
+    # the same output buffer with another tolerance and cap: nothing stale
+    x = torch.zeros_like(b)
+    _, sa = H.pcg(b, x, tol=1e-4)
+    _, sb = H.pcg(b, x.zero_(), tol=1e-9, maxit=6)
+    assert all(s["iterations"] <= t["iterations"] for s, t in zip(sa, s1))
+    assert all(s["iterations"] == min(6, t["iterations"]) for s, t in zip(sb, s1))
