@@ -41,6 +41,20 @@ RHS_SEED = 2
 FIELD_ELL = 8.0
 DIFF_SIGMA, DIFF_FIELD_SEED, DIFF_RHS_SEED = 2.0, 3, 4
 BATCH_SYSTEMS, BATCH_SEED0 = 48, 200
+# the paper's own configuration (Sec. 3, VMATCH): 200^3 Poisson (8e6 unknowns),
+# b = 1, flexible CG to 1e-6; aggregates <= 8, variable V-cycle from two
+# l1-Jacobi sweeps, coarsest level by PCG-l1 (<= 40 iterations); its one-A100
+# solve time is the reference number
+PAPER_SIDE, PAPER_TOL, PAPER_A100_S = 200, 1e-6, 0.43282
+PAPER_OPTS = dict(sweeps=3, smooth_sweeps=2, variable_cycle=1, coarse_solver=1,
+                  coarse_maxit=40, coarse_tol=1e-4)
+METRIC_OF = {
+    "diffusion": "PCG-AMG seconds to 1e-8 rel. residual (256³ diffusion, sigma 2, 1 GB300)",
+    "batch": "batched PCG-AMG seconds to 1e-8 rel. residual (48 diffusion systems, 1 GB300)",
+    "paper": "FCG-AMG (VMATCH) seconds to 1e-6 rel. residual (200³ Poisson, b = 1, 1 GB300)",
+    "multi": "blocked PCG-AMG seconds to 1e-8 rel. residual for 64 RHS (128³ Poisson, 1 GB300)",
+}
+MULTI_SIDE, MULTI_RHS, MULTI_SEED0 = 128, 64, 100
 
 
 def _args():
@@ -49,10 +63,11 @@ def _args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--side", type=int, default=256)
-    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--side", type=int, default=None, help="grid side (256; 200 for paper)")
+    ap.add_argument("--tol", type=float, default=None, help="tolerance (1e-8; 1e-6 for paper)")
     ap.add_argument("--precision", choices=["f64", "f32"], default="f64")
-    ap.add_argument("--workload", choices=["poisson", "diffusion", "batch"], default="poisson")
+    ap.add_argument("--workload", choices=["poisson", "diffusion", "batch", "paper", "multi"],
+                    default="poisson")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--graph", choices=["loop", "iteration", "none"], default="loop",
                     help="PCG replay: the whole loop as one graph (default), one graph per "
@@ -64,7 +79,13 @@ def _args():
                          "(0 = one launch per step; default: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    return ap.parse_args()
+    a = ap.parse_args()
+    paper = a.workload == "paper"
+    if a.side is None:
+        a.side = PAPER_SIDE if paper else MULTI_SIDE if a.workload == "multi" else 256
+    if a.tol is None:
+        a.tol = PAPER_TOL if paper else 1e-8
+    return a
 
 
 def _dist():
@@ -262,6 +283,15 @@ def run_ours(a):
             b_host = uniform01(DIFF_RHS_SEED, n)
             workload = "diffusion3d_%d^3_sigma%g_ell%g_pcg_amg_v11_tol%g" % (
                 side, DIFF_SIGMA, FIELD_ELL, a.tol)
+        elif a.workload == "paper":
+            A = poisson3d(side)
+            b_host = np.ones(n)
+            workload = "poisson3d_%d^3_fcg_vmatch_tol%g" % (side, a.tol)
+        elif a.workload == "multi":
+            A = poisson3d(side)
+            b_host = np.ascontiguousarray(np.stack(
+                [uniform01(MULTI_SEED0 + c, n) for c in range(MULTI_RHS)], axis=1))
+            workload = "poisson3d_%d^3_x%d_rhs_pcg_amg_v11_tol%g" % (side, MULTI_RHS, a.tol)
         else:
             A = poisson3d(side)
             b_host = uniform01(RHS_SEED, n)
@@ -275,6 +305,9 @@ def run_ours(a):
     tail = {} if a.tail_rows is None else {"tail_rows": a.tail_rows}
     if a.compress:
         tail["compress_columns"] = 1
+    if a.workload == "paper":
+        tail.update(PAPER_OPTS)
+    beta = "flexible" if a.workload == "paper" else "auto"
 
     def make_hierarchy():
         if batch:
@@ -282,14 +315,22 @@ def run_ours(a):
                                       **tail)
         return amg.Hierarchy(*Ad, precision=a.precision, autotune=int(a.autotune), **tail)
 
+    multi = a.workload == "multi"
+
     def solve(bv, xv):
+        if multi:
+            _, stats = H.pcg_multi(bv, xv, tol=a.tol)
+            worst = min(s["status"] for s in stats) if any(s["status"] < 0 for s in stats) \
+                else max(s["status"] for s in stats)
+            return dict(iterations=max(s["iterations"] for s in stats), status=worst,
+                        per_rhs=[s["iterations"] for s in stats])
         if batch:
             _, stats = H.pcg(bv, xv, tol=a.tol, use_graph=GRAPH_MODE[a.graph])
             worst = min(s["status"] for s in stats) if any(s["status"] < 0 for s in stats) \
                 else max(s["status"] for s in stats)
             return dict(iterations=max(s["iterations"] for s in stats), status=worst,
                         per_system=[s["iterations"] for s in stats])
-        return H.pcg(bv, xv, tol=a.tol, use_graph=GRAPH_MODE[a.graph])[1]
+        return H.pcg(bv, xv, tol=a.tol, beta_form=beta, use_graph=GRAPH_MODE[a.graph])[1]
 
     # warm the module on a small problem, then time the setup of the real one
     amg.Hierarchy(*amg.csr_to_device(poisson3d(16), dev), precision=a.precision).close()
@@ -332,6 +373,22 @@ def run_ours(a):
     it = iters[-1]
     assert info["status"] == 0, info
 
+    # the blocked V-cycle of all right-hand sides against one column at a time
+    mvc = None
+    if multi:
+        b = b.contiguous()
+        Zm = torch.empty_like(b)
+        for _ in range(3):
+            H.vcycle_multi(b, Zm)
+        e0m, e1m = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0m.record()
+        for _ in range(5):
+            H.vcycle_multi(b, Zm)
+        e1m.record()
+        torch.cuda.synchronize()
+        mvc = e0m.elapsed_time(e1m) / 5
+        b_multi, b = b, b[:, 0].contiguous()
+
     # per-kernel V-cycle timing (CUDA events on the launching stream)
     agg = {}
     for _ in range(3):
@@ -350,18 +407,26 @@ def run_ours(a):
         V += 1
     if batch:
         launches = (2 + (V + 5) + (it - 1) * (V + 6) + 2) * a.steps
+    elif multi:
+        launches = None  # the blocked kernels (multi.cu) are not counted here
     else:
         launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1) * a.steps
+    nlaunch = {}  # launches per V-cycle of each (level, kind)
     for _ in range(reps):
         _, recs = H.vcycle_profile(b)
         for r_ in recs:
             key = (r_["level"], r_["kind"])
-            e = agg.setdefault(key, [0.0, r_["bytes"]])
+            e = agg.setdefault(key, [0.0, 0.0])
             e[0] += r_["ms"] / reps
+            e[1] += r_["bytes"] / reps
+    for r_ in recs:
+        key = (r_["level"], r_["kind"])
+        nlaunch[key] = nlaunch.get(key, 0) + 1
     vc_ms = sum(v[0] for v in agg.values())
     vc_bytes = sum(v[1] for v in agg.values())
     vcycle_gbs = vc_bytes / (vc_ms * 1e-3) / 1e9
     (dl, dk), (dms, dbytes) = max(agg.items(), key=lambda kv: kv[1][0])
+    dms, dbytes = dms / nlaunch[(dl, dk)], dbytes / nlaunch[(dl, dk)]  # per launch
     peak, peak_src = _peaks()
     dom_name = "vcycle_%s_level%d" % (dk, dl)
     wl_key = "%s%d_%s" % (a.workload, side, a.precision)
@@ -389,9 +454,10 @@ def run_ours(a):
     # end to end through the public API from pinned host memory
     e2e = None
     if not a.no_e2e:
+        bfull = b_multi if multi else b
         bh = torch.from_numpy(b_host).pin_memory()
-        xh = torch.empty(n, dtype=torch.float64).pin_memory()
-        bd = torch.empty_like(b)
+        xh = torch.empty(tuple(bfull.shape), dtype=torch.float64).pin_memory()
+        bd = torch.empty_like(bfull)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(a.steps):
@@ -402,8 +468,8 @@ def run_ours(a):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_s = e0.elapsed_time(e1) / 1e3 / a.steps
-        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * n,
-               "d2h_bytes_per_step": 8 * n}
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * bfull.numel(),
+               "d2h_bytes_per_step": 8 * bfull.numel()}
         assert np.allclose(xh[:8].numpy(), x[:8].cpu().numpy())
 
     cpu = None
@@ -420,7 +486,8 @@ def run_ours(a):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": per_solve, "unit": "s", "n_gpus": ws, "steps": a.steps,
+            "metric": METRIC_OF.get(a.workload, METRIC), "value": per_solve, "unit": "s",
+            "n_gpus": ws, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": per_solve * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if a.precision == "f64"
             else "f64 outer / f32 V-cycle", "data": "synthetic",
@@ -440,7 +507,8 @@ def run_ours(a):
             "ms_per_iteration": per_solve * 1e3 / max(it, 1),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
-            "vcycle_kernels": [{"level": k[0], "kind": k[1], "ms": round(v[0], 5),
+            "vcycle_kernels": [{"level": k[0], "kind": k[1], "launches": nlaunch[k],
+                                "ms": round(v[0], 5),
                                 "gbs": round(v[1] / (v[0] * 1e-3) / 1e9, 1)}
                                for k, v in sorted(agg.items())],
         }
@@ -452,6 +520,25 @@ def run_ours(a):
             line["config"]["rhs"] = "uniform[0,1) seed %d, concatenated" % RHS_SEED
         if a.workload == "diffusion":
             line["config"]["rhs"] = "uniform[0,1) seed %d" % DIFF_RHS_SEED
+        if multi:
+            line["config"]["rhs"] = ("%d columns uniform[0,1) seeds %d..%d, row-major"
+                                     % (MULTI_RHS, MULTI_SEED0, MULTI_SEED0 + MULTI_RHS - 1))
+            line["config"]["per_rhs_iterations"] = info["per_rhs"]
+            # one V-cycle of all columns (blocked SpMM kernels) against the
+            # single-vector V-cycle times the number of columns
+            line["multi"] = {"vcycle_all_rhs_ms": mvc, "vcycle_one_rhs_ms": vc_ms,
+                             "blocked_speedup_per_rhs": vc_ms * MULTI_RHS / mvc,
+                             "rhs_iterations_per_s": sum(info["per_rhs"]) / per_solve}
+        if a.workload == "paper":
+            line["config"]["rhs"] = "b = 1"
+            line["config"]["cycle"] = ("aggregates <= 8 (3 matching sweeps), variable V-cycle "
+                                       "(2 l1-Jacobi sweeps on level 0, doubled per level), "
+                                       "coarsest: PCG-l1 <= 40 iterations to 1e-4, FCG")
+            if side == PAPER_SIDE and a.tol == PAPER_TOL and ws == 1:
+                # the paper's VMATCH solve time on one A100 (8e6 unknowns, 1e-6)
+                line["vs_baseline"] = per_solve / PAPER_A100_S
+                line["baseline"] = {"value": PAPER_A100_S, "unit": "s", "hardware": "1 A100",
+                                    "iterations": 28}
         print(json.dumps(line), flush=True)
     H.close()
     if ws > 1:

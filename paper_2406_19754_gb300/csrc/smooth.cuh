@@ -70,10 +70,13 @@ __device__ __forceinline__ int64_t post_slice(const SellView<V>& AP, const BT* b
   const T acc = sell_row<TPR, T>(AP, sl, ln, [&](int J) { return Ld::ld(xc + J); });
   const int64_t i = lane_row(AP, sl, ln);
   if (i >= 0) {
+    // explicit FMAs: every kernel that runs this (and the multi-RHS kernels,
+    // which contract the same expressions) rounds identically
     const T si = s[i];
-    const T yi = (xp ? Ld::ld(xp + i) : si * to_f(Ld::ld(b + i), T(0))) + Ld::ld(xc + agg[i]);
+    const T xci = Ld::ld(xc + agg[i]);
+    const T yi = xp ? Ld::ld(xp + i) + xci : fma(si, to_f(Ld::ld(b + i), T(0)), xci);
     const T ei = Ld::ld(r + i) - acc;
-    z = to_f(yi + si * ei, XT(0));
+    z = to_f(fma(si, ei, yi), XT(0));
     x[i] = z;
     if (e) e[i] = ei;
   }
@@ -85,6 +88,21 @@ __device__ __forceinline__ int64_t post_slice(const SellView<V>& AP, const BT* b
 // element per entry), writes r' to r_out, and hands back this lane's row i
 // (-1 if none) with r_i and r'_i; the caller updates x (pre-smoother: x += S r,
 // post-smoother, which steps the residual first: y += S r').
+// The x updates of the sweeps, written out so every kernel rounds alike:
+// pre-smoother x += S r (from x = S b on the first sweep), post-smoother
+// y += S r' (y possibly wider than the V-cycle type).
+template <typename T>
+__device__ __forceinline__ T sweep_pre_x(T xi, T si, T ri) {
+  return fma(si, ri, xi);
+}
+template <typename T, typename YT>
+__device__ __forceinline__ YT sweep_post_y(YT yi, T si, T rn) {
+  if constexpr (sizeof(YT) == sizeof(T))
+    return fma(si, rn, yi);
+  else
+    return yi + to_f(si * rn, YT(0));
+}
+
 template <int TPR, typename Ld, typename V, typename T>
 __device__ __forceinline__ void sweep_slice(const SellView<V>& Ah, const T* s, const T* r,
                                             T* r_out, int64_t sl, const Lanes<TPR>& ln,
@@ -167,6 +185,76 @@ __device__ __forceinline__ void coarse_x_row(int64_t g, int nblk, const int64_t*
   for (int64_t i = k + lane; i < n; i += 32) acc = fma(row[i], Ld::ld(y + r0 + i), acc);
   acc = warp_sum(acc);
   if (lane == 0) x[g] = (XT)acc;
+}
+
+// Coarsest solve by PCG with the l1-Jacobi preconditioner (s = 1/d of the
+// coarsest level; Sec. 3, the VBM/VMATCH coarsest solver), zero initial guess,
+// in one CUDA block: at most maxit iterations, stopping once ||r|| <= tol ||b||
+// or when p^T A p <= 0.  FP64 throughout; dot products by a fixed block tree.
+// w: 5n doubles of scratch (x, r, z, p, q).  Every thread of the block calls
+// it; b may have been written by the same block before a __syncthreads.
+__device__ __forceinline__ double block_dot(int64_t n, const double* u, const double* v) {
+  __shared__ double total;
+  double t[1] = {0.0};
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t[0] += u[i] * v[i];
+  block_sum<1>(t);
+  if (threadIdx.x == 0) total = t[0];
+  __syncthreads();
+  const double res = total;
+  __syncthreads();
+  return res;
+}
+
+template <int TPR, typename BT, typename XT>
+__device__ void coarse_pcg_cta(const SellView<double>& A, const double* sinv, const BT* b,
+                               XT* xo, double* w, int maxit, double tol) {
+  const int64_t n = A.n;
+  double* x = w;
+  double* r = w + n;
+  double* z = w + 2 * n;
+  double* p = w + 3 * n;
+  double* q = w + 4 * n;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    x[i] = 0.0;
+    r[i] = (double)b[i];
+  }
+  __syncthreads();
+  const double bnorm = sqrt(block_dot(n, r, r));
+  if (bnorm > 0.0) {
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+      z[i] = sinv[i] * r[i];
+      p[i] = z[i];
+    }
+    __syncthreads();
+    double rz = block_dot(n, r, z);
+    const Lanes<TPR> ln;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int k = 0; k < maxit; ++k) {
+      for (int64_t sl = warp; sl < A.nslices; sl += nwarps) {
+        const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return p[j]; });
+        const int64_t i = lane_row(A, sl, ln);
+        if (i >= 0) q[i] = acc;
+      }
+      __syncthreads();
+      const double pq = block_dot(n, p, q);
+      if (!(pq > 0.0)) break;
+      const double alpha = rz / pq;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        x[i] = x[i] + alpha * p[i];
+        r[i] = r[i] - alpha * q[i];
+      }
+      __syncthreads();
+      if (sqrt(block_dot(n, r, r)) <= tol * bnorm) break;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) z[i] = sinv[i] * r[i];
+      __syncthreads();
+      const double rzn = block_dot(n, r, z);
+      const double beta = rzn / rz;
+      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
+      __syncthreads();
+      rz = rzn;
+    }
+  }
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xo[i] = bnorm > 0.0 ? (XT)x[i] : XT(0);
 }
 
 }  // namespace amg

@@ -63,11 +63,19 @@ struct TailLevel {
   void *b, *x, *r;  // this level
   void* bc;         // next level's b
   const void* xc;   // next level's x
+  int64_t nu;       // smoother sweeps; with nu > 1 also r2 and the pre-smoothed xp
+  void *r2, *xp;
 };
 
 struct TailParams {
   int nlev;   // smoothed levels lt .. lt + nlev - 1; the next one is the coarsest
   int small;  // coarsest blocks solved one per CTA (else row-parallel, two phases)
+  // coarsest solve by PCG-l1 (one CTA only): its matrix, scale and scratch
+  int pcg, pcg_maxit;
+  double pcg_tol;
+  SellDesc Ac;
+  const double* csinv;
+  double* cw;
   int nblk;
   int64_t nco;
   const int64_t* brow;
@@ -181,14 +189,39 @@ __device__ __forceinline__ void pre_rows(const TailLevel& L, int64_t gw, int64_t
 }
 
 template <int TPR, typename Ld, typename T, typename V>
-__device__ __forceinline__ void post_rows(const TailLevel& L, int64_t gw, int64_t nw) {
+__device__ __forceinline__ void post_rows(const TailLevel& L, const T* r, const T* xp, T* e,
+                                          int64_t gw, int64_t nw) {
   const Lanes<TPR> ln;
   const SellView<V> AP = dview<V>(L.AP);
   for (int64_t sl = gw; sl < AP.nslices; sl += nw) {
     if (!AP.live(sl)) continue;
     T z;
-    post_slice<TPR, Ld>(AP, (const T*)L.b, (const T*)L.s, (const T*)L.r, L.agg,
-                          (const T*)L.xc, (T*)L.x, sl, ln, z);
+    post_slice<TPR, Ld>(AP, (const T*)L.b, (const T*)L.s, r, L.agg, (const T*)L.xc, (T*)L.x,
+                        sl, ln, z, xp, e);
+  }
+}
+
+// Further sweeps on the residual recurrence (k_sweep_pre / k_sweep_post).
+template <int TPR, typename Ld, typename T, typename V, bool PRE>
+__device__ __forceinline__ void sweep_rows(const TailLevel& L, const T* r, T* r_out, int first,
+                                           int64_t gw, int64_t nw) {
+  const Lanes<TPR> ln;
+  const SellView<V> Ah = dview<V>(L.A);
+  const T* s = (const T*)L.s;
+  for (int64_t sl = gw; sl < Ah.nslices; sl += nw) {
+    if (!Ah.live(sl)) continue;
+    T ri = T(0), rn = T(0);
+    int64_t i;
+    sweep_slice<TPR, Ld>(Ah, s, r, r_out, sl, ln, ri, rn, i);
+    if (i < 0) continue;
+    if constexpr (PRE) {
+      T* x = (T*)L.xp;
+      const T xi = first ? s[i] * Ld::ld((const T*)L.b + i) : x[i];
+      x[i] = sweep_pre_x(xi, s[i], ri);
+    } else {
+      T* y = (T*)L.x;
+      y[i] = sweep_post_y(y[i], s[i], rn);
+    }
   }
 }
 
@@ -204,19 +237,32 @@ __device__ void tail_pre(const TailLevel& L, int64_t gw, int64_t nw) {
 }
 
 template <typename Ld, typename T>
-__device__ void tail_post(const TailLevel& L, int64_t gw, int64_t nw) {
+__device__ void tail_post(const TailLevel& L, const T* r, const T* xp, T* e, int64_t gw,
+                          int64_t nw) {
   if constexpr (sizeof(T) == 8) {
-    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, double>(L, gw, nw)));
+    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, double>(L, r, xp, e, gw, nw)));
   } else if (L.vstore == VAL_BF16) {
-    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, __nv_bfloat16>(L, gw, nw)));
+    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, __nv_bfloat16>(L, r, xp, e, gw, nw)));
   } else {
-    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, float>(L, gw, nw)));
+    TAIL_TPR(dcode(L.AP), (post_rows<TPR, Ld, T, float>(L, r, xp, e, gw, nw)));
+  }
+}
+
+template <typename Ld, typename T, bool PRE>
+__device__ void tail_sweep(const TailLevel& L, const T* r, T* r_out, int first, int64_t gw,
+                           int64_t nw) {
+  if constexpr (sizeof(T) == 8) {
+    TAIL_TPR(dcode(L.A), (sweep_rows<TPR, Ld, T, double, PRE>(L, r, r_out, first, gw, nw)));
+  } else if (L.vstore == VAL_BF16) {
+    TAIL_TPR(dcode(L.A),
+             (sweep_rows<TPR, Ld, T, __nv_bfloat16, PRE>(L, r, r_out, first, gw, nw)));
+  } else {
+    TAIL_TPR(dcode(L.A), (sweep_rows<TPR, Ld, T, float, PRE>(L, r, r_out, first, gw, nw)));
   }
 }
 
 template <typename Ld, typename T>
-__device__ void tail_restrict(const TailLevel& L, int64_t gt, int64_t nt) {
-  const T* r = (const T*)L.r;
+__device__ void tail_restrict(const TailLevel& L, const T* r, int64_t gt, int64_t nt) {
   T* bc = (T*)L.bc;
   for (int64_t I = gt; I < L.nc; I += nt)
     bc[I] = restrict_sum<Ld>(L.members + I * L.stride, L.stride, r);
@@ -239,6 +285,14 @@ template <bool ONE, typename Ld, typename T>
 __device__ bool tail_coarse(const TailParams& P, int64_t gw, int64_t nw, double* csh) {
   const T* b = (const T*)P.cb;
   T* x = (T*)P.cx;
+  if constexpr (ONE) {
+    if (P.pcg) {
+      const SellView<double> Ac = dview<double>(P.Ac);
+      TAIL_TPR(dcode(P.Ac), (coarse_pcg_cta<TPR>(Ac, P.csinv, b, x, P.cw, P.pcg_maxit,
+                                                  P.pcg_tol)));
+      return true;
+    }
+  }
   if (P.small) {
     for (int blk = blockIdx.x; blk < P.nblk; blk += gridDim.x)
       if (!P.act || P.act[blk])
@@ -271,19 +325,44 @@ __global__ void __launch_bounds__(TAIL_BLOCK, 1) k_tail(const __grid_constant__ 
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nt = (int64_t)gridDim.x * blockDim.x;
   const int64_t gw = gt >> 5, nw = nt >> 5;
+  // bit l of cur: which residual buffer of level l (r or r2) holds its
+  // residual after the pre-smoothing sweeps
+  unsigned cur = 0;
+  auto rb = [&](const TailLevel& L, int k) { return (T*)(k ? L.r2 : L.r); };
   bool ok = true;
   for (int l = 0; ok && l < P.nlev; ++l) {
-    tail_pre<Ld, T>(P.lv[l], gw, nw);
+    const TailLevel& L = P.lv[l];
+    tail_pre<Ld, T>(L, gw, nw);
     ok = tail_barrier<ONE>(P);
+    int c = 0;
+    for (int64_t k = 2; ok && k <= L.nu; ++k) {
+      tail_sweep<Ld, T, true>(L, rb(L, c), rb(L, 1 - c), k == 2, gw, nw);
+      ok = tail_barrier<ONE>(P);
+      c = 1 - c;
+    }
     if (!ok) break;
-    tail_restrict<Ld, T>(P.lv[l], gt, nt);
+    if (c) cur |= 1u << l;
+    tail_restrict<Ld, T>(L, rb(L, c), gt, nt);
     ok = tail_barrier<ONE>(P);
   }
   if (ok) ok = tail_coarse<ONE, Ld, T>(P, gw, nw, csh);
   if (ok) ok = tail_barrier<ONE>(P);
   for (int l = P.nlev - 1; ok && l >= 0; --l) {
-    tail_post<Ld, T>(P.lv[l], gw, nw);
-    if (l > 0) ok = tail_barrier<ONE>(P);
+    const TailLevel& L = P.lv[l];
+    int c = (cur >> l) & 1u;
+    if (L.nu > 1) {
+      tail_post<Ld, T>(L, rb(L, c), (const T*)L.xp, rb(L, 1 - c), gw, nw);
+      c = 1 - c;
+    } else {
+      tail_post<Ld, T>(L, (const T*)L.r, nullptr, nullptr, gw, nw);
+    }
+    for (int64_t m = 2; ok && m <= L.nu; ++m) {
+      ok = tail_barrier<ONE>(P);
+      if (!ok) break;
+      tail_sweep<Ld, T, false>(L, rb(L, c), rb(L, 1 - c), 0, gw, nw);
+      c = 1 - c;
+    }
+    if (ok && l > 0) ok = tail_barrier<ONE>(P);
   }
   if (!ok && threadIdx.x == 0) tail_report(P);
 }
@@ -340,13 +419,12 @@ int tail_init(amg_handle* H, cudaStream_t s) {
 int tail_start(const amg_handle* H) {
   const int nl = (int)H->L.size();
   if (H->opt.tail_rows <= 0 || H->tail_grid <= 0 || nl < 3) return -1;
-  if (H->opt.coarse_solver != 0) return -1;  // the PCG coarsest solve has its own kernel
   int lt = 1;
   while (lt < nl - 1 && H->L[lt].n > H->opt.tail_rows) ++lt;
   lt = std::max(lt, nl - 1 - TAIL_MAX_LEVELS);
   if (lt > nl - 2) return -1;
-  for (int l = lt; l < nl - 1; ++l)
-    if (H->L[l].nu > 1) return -1;  // one sweep per side only
+  // the PCG coarsest solve runs inside a one-CTA tail only
+  if (H->opt.coarse_solver != 0 && (H->L[lt].n > TAIL_ONE_CTA_ROWS || H->nblk != 1)) return -1;
   return lt;
 }
 
@@ -397,6 +475,9 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s, const int* act) {
     d.r = L.r;
     d.bc = H->L[lt + k + 1].b;
     d.xc = H->L[lt + k + 1].x;
+    d.nu = L.nu;
+    d.r2 = L.r2;
+    d.xp = L.xp;
     warps = std::max({warps, L.A.nslices, L.AP.nslices, (L.nc + 31) / 32});
   }
   const Level& Lc = H->L[nl - 1];
@@ -412,6 +493,14 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s, const int* act) {
   P.cb = Lc.b;
   P.cx = Lc.x;
   P.act = act;
+  if (H->opt.coarse_solver != 0) {
+    P.pcg = 1;
+    P.pcg_maxit = H->opt.coarse_maxit;
+    P.pcg_tol = H->opt.coarse_tol;
+    P.Ac = desc(Lc.A, Lc.A.v64, nullptr);
+    P.csinv = Lc.s64;
+    P.cw = H->cpcg;
+  }
   P.bar = H->tail_bar;
   P.unreachable = H->tail_debug ? 1u : 0u;
   P.wait_ns = H->tail_debug ? TAIL_DEBUG_WAIT_NS : TAIL_WAIT_NS;
@@ -458,6 +547,7 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s, const int* act) {
   }
   // small enough for one CTA: no grid barrier at all
   const bool one = H->L[lt].n <= TAIL_ONE_CTA_ROWS && P.nblk == 1;
+  if (P.pcg && !one) return AMG_ERR_ARG;
   const int64_t want = (warps * 32 + TAIL_BLOCK - 1) / TAIL_BLOCK;
   const int grid = one ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(want, H->tail_grid));
   cudaLaunchConfig_t cfg;

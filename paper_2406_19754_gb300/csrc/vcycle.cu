@@ -56,7 +56,10 @@ struct VcycleDotEpi {
   }
 };
 
-template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT>
+// MS: the level smooths more than once per side (xp and e are used); the
+// one-sweep instantiations do not carry them, which keeps their registers
+// within the occupancy bound.
+template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT, bool MS>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_post(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,
            const T* __restrict__ r, const int32_t* __restrict__ agg, const T* __restrict__ xc,
@@ -74,7 +77,8 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
        sl += nw) {
     if (!AP.live(sl)) continue;  // warp-uniform
     XT zi;
-    const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi, xp, e);
+    const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi,
+                                            MS ? xp : nullptr, MS ? e : nullptr);
     double ds[ND];
 #pragma unroll
     for (int k = 0; k < ND; ++k) ds[k] = 0.0;
@@ -116,7 +120,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     if (i >= 0) {
       const T si = s[i];
       const T xi = first ? si * to_f(b[i], T(0)) : x[i];
-      x[i] = xi + si * ri;
+      x[i] = sweep_pre_x(xi, si, ri);
     }
   }
 }
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     T ri = T(0), rn = T(0);
     int64_t i;
     sweep_slice<TPR, LdRO>(Ah, s, r, r_out, sl, ln, ri, rn, i);
-    if (i >= 0) y[i] = y[i] + to_f(s[i] * rn, YT(0));
+    if (i >= 0) y[i] = sweep_post_y(y[i], s[i], rn);
   }
 }
 
@@ -232,74 +236,13 @@ __global__ void k_coarse_x(int64_t nco, int nblk, const int64_t* __restrict__ br
     coarse_x_row<LdRO>(g, nblk, brow, bmat, LinvT_all, y, x);
 }
 
-// Coarsest solve by PCG with the l1-Jacobi preconditioner (s = 1/d of the
-// coarsest level; Sec. 3, the VBM/VMATCH coarsest solver), zero initial guess,
-// in one CUDA block: at most maxit iterations, stopping once ||r|| <= tol ||b||
-// or when p^T A p <= 0.  FP64 throughout; dot products by a fixed block tree.
-// w: 5n doubles of scratch (x, r, z, p, q).
-__device__ double block_dot(int64_t n, const double* u, const double* v) {
-  __shared__ double total;
-  double t[1] = {0.0};
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) t[0] += u[i] * v[i];
-  block_sum<1>(t);
-  if (threadIdx.x == 0) total = t[0];
-  __syncthreads();
-  const double res = total;
-  __syncthreads();
-  return res;
-}
-
+// Coarsest solve by PCG with the l1-Jacobi preconditioner in one CUDA block
+// (coarse_pcg_cta).
 template <int TPR, typename BT, typename XT>
 __global__ void __launch_bounds__(1024, 1)
     k_coarse_pcg(SellView<double> A, const double* __restrict__ sinv, const BT* __restrict__ b,
                  XT* __restrict__ xo, double* w, int maxit, double tol) {
-  const int64_t n = A.n;
-  double* x = w;
-  double* r = w + n;
-  double* z = w + 2 * n;
-  double* p = w + 3 * n;
-  double* q = w + 4 * n;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    x[i] = 0.0;
-    r[i] = (double)b[i];
-  }
-  __syncthreads();
-  const double bnorm = sqrt(block_dot(n, r, r));
-  if (bnorm > 0.0) {
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-      z[i] = sinv[i] * r[i];
-      p[i] = z[i];
-    }
-    __syncthreads();
-    double rz = block_dot(n, r, z);
-    const Lanes<TPR> ln;
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int k = 0; k < maxit; ++k) {
-      for (int64_t sl = warp; sl < A.nslices; sl += nwarps) {
-        const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return p[j]; });
-        const int64_t i = lane_row(A, sl, ln);
-        if (i >= 0) q[i] = acc;
-      }
-      __syncthreads();
-      const double pq = block_dot(n, p, q);
-      if (!(pq > 0.0)) break;
-      const double alpha = rz / pq;
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        x[i] = x[i] + alpha * p[i];
-        r[i] = r[i] - alpha * q[i];
-      }
-      __syncthreads();
-      if (sqrt(block_dot(n, r, r)) <= tol * bnorm) break;
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) z[i] = sinv[i] * r[i];
-      __syncthreads();
-      const double rzn = block_dot(n, r, z);
-      const double beta = rzn / rz;
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
-      __syncthreads();
-      rz = rzn;
-    }
-  }
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) xo[i] = bnorm > 0.0 ? (XT)x[i] : XT(0);
+  coarse_pcg_cta<TPR>(A, sinv, b, xo, w, maxit, tol);
 }
 
 // ------------------------------------------------------------------ driver
@@ -368,10 +311,21 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
   v.act = act;
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
   const T* r = in.r ? in.r : (const T*)L.r;
+  if constexpr (NDOT == 0) {
+    if (in.xp) {
+      AMG_DISPATCH_TPR(sell_code(L.AP),
+                       (k_post<TPR, V, T, BT, XT, 0, true><<<grid, SELL_BLOCK, 0, s>>>(
+                           v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, slice_part, in.xp,
+                           in.e)));
+      AMG_LAUNCH_CHECK();
+      return AMG_OK;
+    }
+  }
+  if (in.xp) return AMG_ERR_ARG;  // several sweeps: the dot products follow separately
   AMG_DISPATCH_TPR(sell_code(L.AP),
-                   (k_post<TPR, V, T, BT, XT, NDOT><<<grid, SELL_BLOCK, 0, s>>>(
-                       v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, slice_part, in.xp,
-                       in.e)));
+                   (k_post<TPR, V, T, BT, XT, NDOT, false><<<grid, SELL_BLOCK, 0, s>>>(
+                       v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, slice_part, nullptr,
+                       nullptr)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -497,6 +451,7 @@ static double bytes_post(const Level& L, double mb, double vb, double ib, double
 // Triangles of L^-1 and L^-T read by the coarse solve (lower/upper halves of
 // every diagonal block).
 static double coarse_factor_bytes(const amg_handle* H) {
+  if (H->opt.coarse_solver != 0) return 12.0 * (double)H->L.back().nnz;  // PCG: A per pass
   double t = 0.0;
   for (int k = 0; k < H->nblk; ++k) {
     const double m = (double)(H->cblk_row[k + 1] - H->cblk_row[k]);
@@ -597,7 +552,7 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
     for (int l = lt; l < nl - 1; ++l) {
       const Level& L = H->L[l];
       bytes += bytes_pre(L, mbytes(L), vb, vb) + bytes_restrict(L, vb) +
-               bytes_post(L, pbytes(L), vb, vb, vb);
+               bytes_post(L, pbytes(L), vb, vb, vb) + 2.0 * (double)(L.nu - 1) * sweep_bytes(L);
     }
     PROF_BEGIN(lt, 4, bytes);
     AMG_TRY(tail_launch<T>(H, lt, s, act));

@@ -36,6 +36,13 @@ LARGE = (64, 64, 64)   # level 1 has 65536 rows: a tail from it spans the grid
     (LARGE, dict(precision="f64", tail_rows=70000)),
     (LARGE, dict(precision="f32", tail_rows=70000, threads_per_row=2)),
     (LARGE, dict(precision="f32", tail_rows=20000, bf16_from_level=1)),
+    # several sweeps per side, the variable V-cycle, the PCG coarsest solve
+    (SMALL, dict(precision="f64", smooth_sweeps=2, variable_cycle=1, tail_rows=16384)),
+    (SMALL, dict(precision="f32", smooth_sweeps=3, tail_rows=16384)),
+    (SMALL, dict(precision="f64", smooth_sweeps=2, coarse_solver=1, tail_rows=16384)),
+    (SMALL, dict(precision="f64", coarse_solver=1, coarse_tol=0.0, coarse_maxit=9,
+                 tail_rows=16384)),
+    (LARGE, dict(precision="f64", smooth_sweeps=2, variable_cycle=1, tail_rows=70000)),
 ])
 def test_tail_vcycle_bitwise(amg, shape, opts):
     A = diffusion3d(np.exp(gaussian_field(shape, 1.5, 4.0, 21)))
