@@ -160,6 +160,21 @@ int amg_setup(const amg_csr* A, const amg_options* opt, amg_stream_t stream, amg
 int amg_destroy(amg_handle* H);
 
 /*
+ * New coefficient values for the matrix H was built from, with the same
+ * sparsity (Sec. 2.2: coefficients of a matrix whose structure is preserved
+ * are updated in place, and the hierarchy is rebuilt on the assembled one).
+ * Keeps H's aggregates and layout on every level (no matching); recomputes
+ * the Galerkin values, l1-Jacobi scales (damping weights reset to 1), the
+ * V-cycle operators and the coarsest factor.  A: device CSR with H's n, nnz,
+ * row pointers and columns (checked by a fingerprint of the pattern).
+ * Synchronous; H keeps its address, previously captured graphs are dropped.
+ * Errors: AMG_ERR_ARG (NULL, other sizes or pattern), AMG_ERR_UNSUPPORTED
+ * (batched handles), AMG_ERR_NOT_SPD, AMG_ERR_OOM, AMG_ERR_CUDA; on error H
+ * is unchanged.
+ */
+int amg_update_values(amg_handle* H, const amg_csr* A, amg_stream_t stream);
+
+/*
  * Replaces the level-0 smoother damping weights: s_i = omega_i * (1 / d_i)
  * with d_i the l1 row sum (Sec. 2.3, l1-Jacobi).  omega: device float32[n0],
  * each in (0, 1], or NULL to restore omega == 1.  Levels >= 1 keep plain

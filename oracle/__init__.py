@@ -54,6 +54,8 @@ def _declare(L):
                                     C.c_double, _I64, C.POINTER(C.c_int)]
     L.orc_free.argtypes = [_P]
     L.orc_set_cycle.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
+    L.orc_setup_reuse.restype = _P
+    L.orc_setup_reuse.argtypes = [_I64, _P, _P, _P, _P, _I64, _P]
     L.orc_levels.restype = C.c_int
     L.orc_levels.argtypes = [_P]
     L.orc_level_n.restype = _I64
@@ -261,6 +263,20 @@ class Hierarchy:
         self.sweeps = sweeps
         lib().orc_set_cycle(self.h, smooth_sweeps, 1 if variable else 0,
                             {"cholesky": 0, "pcg": 1}[coarse], coarse_maxit, coarse_tol)
+
+    def reuse(self, A, max_dense=8192):
+        """A hierarchy for new values of the matrix this one was built from
+        (same sparsity): these aggregates on every level, new Galerkin values,
+        smoother scales and coarse factor, the same cycle parameters."""
+        n, rp, ci, v = csr_args(A)
+        st = C.c_int(0)
+        H = Hierarchy.__new__(Hierarchy)
+        H._keep = (rp, ci, v)
+        H.h = lib().orc_setup_reuse(n, _p(rp), _p(ci), _p(v), self.h, max_dense, C.byref(st))
+        H.status = st.value
+        H.n = n
+        H.sweeps = self.sweeps
+        return H
 
     def __del__(self):
         if getattr(self, "h", None):

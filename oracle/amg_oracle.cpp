@@ -332,9 +332,13 @@ int64_t largest_block(const std::vector<int64_t>& sys, int64_t n) {
 // diagonally (empty for one system).  With systems, coarsening stops once
 // every system has at most max_coarse rows, so each keeps the coarsest level
 // it would get alone; the coarsest matrix stays block diagonal.
+// like: a hierarchy whose aggregates are reused level by level (new values,
+// the same structure: Sec. 2.2 updates coefficients of a matrix whose
+// structure is preserved and rebuilds on an assembled hierarchy); null to
+// build the aggregates by matching.
 int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
           double stall, int64_t max_dense, const double* omega,
-          std::vector<int64_t> sys = std::vector<int64_t>()) {
+          std::vector<int64_t> sys = std::vector<int64_t>(), const Hierarchy* like = nullptr) {
   H.sweeps = sweeps;
   H.lev.clear();
   const int stride = 1 << sweeps;
@@ -344,6 +348,16 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
     Level& L = H.lev[l];
     l1_scale(L.A, l == 0 ? omega : nullptr, L.dinv);
     const int64_t n = L.A.n;
+    if (like) {
+      if (l + 1 >= (int)like->lev.size()) break;
+      L.agg = like->lev[l].agg;
+      L.nc = like->lev[l].nc;
+      L.members = like->lev[l].members;
+      Level next;
+      galerkin(L.A, L.agg, L.nc, L.members, stride, next.A);
+      H.lev.push_back(std::move(next));
+      continue;
+    }
     if (largest_block(sys, n) <= max_coarse || l + 1 >= max_levels) break;
     std::vector<int32_t> comp(n);
     for (int64_t i = 0; i < n; ++i) comp[i] = (int32_t)i;
@@ -638,6 +652,29 @@ void* orc_setup_systems(int64_t n, const int64_t* rp, const int32_t* ci, const d
   std::vector<int64_t> sys(sys_off, sys_off + nsys + 1);
   *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
                   nullptr, sys);
+  return H;
+}
+
+// A hierarchy for new values of the matrix `like` was built from (same
+// sparsity): like's aggregates on every level, new Galerkin values, smoother
+// scales and coarse factor.  -1 if the structure differs.
+void* orc_setup_reuse(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                      void* like, int64_t max_dense, int* status) {
+  const Hierarchy* L = (const Hierarchy*)like;
+  Hierarchy* H = new Hierarchy();
+  Csr A = csr_copy(n, rp, ci, v);
+  const Csr& A0 = L->lev[0].A;
+  if (A.n != A0.n || A.rowptr != A0.rowptr || A.col != A0.col) {
+    *status = -1;
+    return H;
+  }
+  *status = build(*H, std::move(A), L->sweeps, 0, 0, 0.0, max_dense, nullptr,
+                  std::vector<int64_t>(), L);
+  H->nu0 = L->nu0;
+  H->variable = L->variable;
+  H->coarse = L->coarse;
+  H->coarse_maxit = L->coarse_maxit;
+  H->coarse_tol = L->coarse_tol;
   return H;
 }
 

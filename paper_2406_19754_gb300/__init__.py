@@ -86,6 +86,14 @@ class Hierarchy:
         self.h = h
         del keep
 
+    def update_values(self, rowptr, col, val, stream=None):
+        """New values of the same sparsity: rebuilds the hierarchy on its
+        existing aggregates (no matching)."""
+        A, keep = csr_struct(rowptr, col, val)
+        _check(self._lib.amg_update_values(self.h, C.byref(A), _stream(stream)),
+               "amg_update_values")
+        del keep
+
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             self._lib.amg_destroy(self.h)

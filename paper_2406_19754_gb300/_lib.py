@@ -68,6 +68,7 @@ SIGNATURES = {
     "pcg_default_options": (C.c_int, [C.POINTER(PcgOptions)]),
     "amg_status_string": (C.c_char_p, [C.c_int]),
     "amg_setup": (C.c_int, [C.POINTER(AmgCsr), C.POINTER(AmgOptions), _P, C.POINTER(_P)]),
+    "amg_update_values": (C.c_int, [_P, C.POINTER(AmgCsr), _P]),
     "amg_destroy": (C.c_int, [_P]),
     "amg_set_smoother_weights": (C.c_int, [_P, _P, _P]),
     "amg_vcycle_apply": (C.c_int, [_P, _P, _P, _P]),

@@ -2,6 +2,8 @@
 // lifecycle, and dispatch into the setup, V-cycle and PCG drivers.
 #include <string.h>
 
+#include <utility>
+
 #include "common.cuh"
 
 using namespace amg;
@@ -100,8 +102,41 @@ static void destroy(amg_handle* H) {
   delete H;
 }
 
+// Order-independent fingerprint of a CSR sparsity pattern: the wrapping sum
+// of splitmix64 hashes of (row, row pointer) and (position, column).
+__global__ void k_pattern_hash(int64_t n, const int64_t* rowptr, const int32_t* col,
+                               unsigned long long* out) {
+  const int64_t nnz = rowptr[n] - rowptr[0];
+  unsigned long long h = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n + nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i <= n)
+      h += mix64(((uint64_t)i << 40) ^ (uint64_t)(rowptr[i] - rowptr[0]));
+    else
+      h += mix64(0x9E3779B97F4A7C15ull ^ ((uint64_t)(i - n - 1) << 32) ^
+                 (uint64_t)(uint32_t)col[rowptr[0] + (i - n - 1)]);
+  }
+  h = warp_sum(h);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, h);
+}
+
+static int pattern_hash(const amg_csr* A, unsigned long long* h, cudaStream_t s, int num_sms) {
+  unsigned long long* d = nullptr;
+  AMG_CUDA_TRY(cudaMallocAsync((void**)&d, sizeof(*d), s));
+  AMG_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(*d), s));
+  k_pattern_hash<<<grid_for(A->n + A->nnz + 1, 256, num_sms, 4), 256, 0, s>>>(A->n, A->rowptr,
+                                                                               A->col, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(*h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(d, s);
+  AMG_CUDA_TRY(e);
+  return AMG_OK;
+}
+
 static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_handle** out,
-                  int nsys = 0, const amg_csr* systems = nullptr) {
+                  int nsys = 0, const amg_csr* systems = nullptr,
+                  const amg_handle* like = nullptr) {
   amg_handle* H = new amg_handle();
   *out = H;
   if (opt)
@@ -139,7 +174,8 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   AMG_CUDA_TRY(cudaMemsetAsync(H->red.ticket, 0, sizeof(unsigned), s));
   AMG_TRY(ar.alloc_n(&H->sc, 1));
   AMG_CUDA_TRY(cudaMemsetAsync(H->sc, 0, sizeof(PcgScalars), s));
-  AMG_TRY(setup_hierarchy(H, A, s));
+  if (!systems) AMG_TRY(pattern_hash(A, &H->pattern, s, H->num_sms));
+  AMG_TRY(setup_hierarchy(H, A, s, like));
   const int64_t n = A->n;
   AMG_TRY(ar.alloc_n(&H->r, n));
   AMG_TRY(ar.alloc_n(&H->z, n));
@@ -176,6 +212,29 @@ int amg_setup(const amg_csr* A, const amg_options* opt, amg_stream_t stream, amg
 
 int amg_destroy(amg_handle* H) {
   destroy(H);
+  return AMG_OK;
+}
+
+int amg_update_values(amg_handle* H, const amg_csr* A, amg_stream_t stream) {
+  if (!H) return AMG_ERR_ARG;
+  if (H->batched) return AMG_ERR_UNSUPPORTED;
+  int rc = check_csr(A);
+  if (rc < 0) return rc;
+  if (A->n != H->L[0].n || A->nnz != H->L[0].nnz) return AMG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long h = 0;
+  rc = pattern_hash(A, &h, s, H->num_sms);
+  if (rc < 0) return rc;
+  if (h != H->pattern) return AMG_ERR_ARG;
+  amg_handle* T = nullptr;
+  rc = create(A, &H->opt, s, &T, 0, nullptr, H);
+  if (rc < 0) {
+    cudaStreamSynchronize(s);
+    destroy(T);
+    return rc;
+  }
+  std::swap(*H, *T);  // H keeps its address; T now holds the old hierarchy
+  destroy(T);
   return AMG_OK;
 }
 

@@ -261,6 +261,7 @@ struct amg_handle {
   int* tail_fail = nullptr;
   int tail_grid = 0;
   int tail_debug = 0;  // amg_debug_tail_timeout
+  unsigned long long pattern = 0;  // fingerprint of the level-0 sparsity (value updates)
 };
 
 namespace amg {
@@ -399,7 +400,10 @@ __global__ void k_match_expand(const int32_t* __restrict__ wl, const int* __rest
 __global__ void k_match_final(int64_t n, int32_t* mate);
 
 // Setup (setup.cu)
-int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s);
+// like: reuse that hierarchy's aggregates on every level (new values, the
+// same structure) instead of matching.
+int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s,
+                    const amg_handle* like = nullptr);
 int match_pairwise(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
                    const double* val, int32_t* mate, int* rounds, cudaStream_t s);
 int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s);

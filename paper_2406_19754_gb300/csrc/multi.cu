@@ -61,6 +61,9 @@ __device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, i
   const RowSpan r = row_span(A, i, C);
 #pragma unroll
   for (int q = 0; q < KPL; ++q) acc[q] = AccT(0);
+  // unrolled so several entries' gathers are in flight at once (the FMAs
+  // still run in entry order)
+#pragma unroll 4
   for (int k = 0; k < r.w; ++k) {
     const int64_t e = r.off + (int64_t)k * r.stride;
     const int j = __ldg(A.col + e);

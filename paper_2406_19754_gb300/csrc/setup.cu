@@ -919,7 +919,7 @@ static int read_status(amg_handle* H, cudaStream_t s) {
   return h;
 }
 
-int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
+int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_handle* like) {
   const amg_options& o = H->opt;
   Arena& ar = H->arena;
   const int sms = H->num_sms;
@@ -945,6 +945,28 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     AMG_LAUNCH_CHECK();
     k_smoother_scale<<<g1, 256, 0, s>>>(n, H->L[l].d, nullptr, H->L[l].s64, H->L[l].s32);
     AMG_LAUNCH_CHECK();
+    if (like) {  // new values on an assembled hierarchy: its aggregates, no matching
+      ar.release(diag);
+      if (l + 1 >= (int)like->L.size()) break;
+      Level& L = H->L[l];
+      const Level& K = like->L[l];
+      L.nc = K.nc;
+      L.stride = K.stride;
+      AMG_TRY(ar.alloc_n(&L.agg, n));
+      AMG_TRY(ar.alloc_n(&L.members, L.nc * L.stride));
+      AMG_CUDA_TRY(cudaMemcpyAsync(L.agg, K.agg, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice,
+                                   s));
+      AMG_CUDA_TRY(cudaMemcpyAsync(L.members, K.members, sizeof(int32_t) * L.nc * L.stride,
+                                   cudaMemcpyDeviceToDevice, s));
+      Level next;
+      next.n = L.nc;
+      AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, L.stride, L.nc, &next.rowptr,
+                       &next.col, &next.val, &next.nnz, H->dev_status, sms, s));
+      const int st = read_status(H, s);
+      if (st < 0) return st;
+      H->L.push_back(next);
+      continue;
+    }
     if (largest_block(H->L[l], n) <= o.max_coarse || l + 1 >= o.max_levels) {
       ar.release(diag);
       break;
@@ -1136,7 +1158,9 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s) {
     };
     int tpr = o.threads_per_row > 0 ? o.threads_per_row : 1;
     if (o.slice_height > 0) tpr = 32 / o.slice_height;
-    if (o.autotune && smooth) {
+    if (like) {  // the assembled hierarchy's layout, tuned or not
+      tpr = like->L[l].A.tpr;
+    } else if (o.autotune && smooth) {
       const TuneKey key{L.n, (int)(10 * L.nnz / L.n), L.vstore, H->batched,
                         o.compress_columns != 0};
       if (!tune_lookup(key, &tpr)) {
