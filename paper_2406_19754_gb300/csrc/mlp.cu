@@ -38,7 +38,9 @@ struct mlp_handle {
 
 namespace amg {
 
-__device__ __forceinline__ float gelu_f(float u) { return 0.5f * u * (1.0f + erff(u * 0.70710678f)); }
+__device__ __forceinline__ float gelu_f(float u) {
+  return 0.5f * u * (1.0f + erff(u * 0.70710678f));
+}
 __device__ __forceinline__ float gelu_df(float u) {
   return 0.5f * (1.0f + erff(u * 0.70710678f)) + u * expf(-0.5f * u * u) * 0.39894228f;
 }

@@ -23,6 +23,7 @@ constexpr int MROWS_BLOCK = 256;  // 8 warps = 8 rows in flight per block
 struct MultiWs {
   int K = 0;
   double *R = nullptr, *Z = nullptr, *P = nullptr, *Q = nullptr;  // N x K
+  float* R32 = nullptr;  // FP32 copy of R for an FP32 V-cycle (else null)
   void** lb = nullptr;  // per level b, x, r (V-cycle type), host arrays of pointers
   void** lx = nullptr;
   void** lr = nullptr;
@@ -54,25 +55,50 @@ __device__ __forceinline__ RowSpan row_span(const SellView<V>& A, int64_t i, int
   return r;
 }
 
-// acc[c] = sum_k a_ik * g(col_k, c) for the lane's columns.
+// acc[c] = sum_k a_ik * g(col_k, c) for the lane's columns.  Entries go in
+// groups of MV_U: the group's columns and values are loaded first, then all
+// its gathers are issued, then the FMAs run in entry order, so a warp keeps
+// MV_U gathers in flight instead of waiting on each column index in turn.
+constexpr int MV_U = 4;
+// Row kernels (row_mv) are resident MV_BLOCKS blocks per SM (64 registers a
+// thread); their grids are sized to one full wave of that.
+constexpr int MV_BLOCKS = 4;
+
 template <int KPL, typename AccT, typename V, typename G>
 __device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, int K, int lane,
                                        AccT (&acc)[KPL], G g) {
   const RowSpan r = row_span(A, i, C);
 #pragma unroll
   for (int q = 0; q < KPL; ++q) acc[q] = AccT(0);
-  // unrolled so several entries' gathers are in flight at once (the FMAs
-  // still run in entry order)
-#pragma unroll 4
-  for (int k = 0; k < r.w; ++k) {
-    const int64_t e = r.off + (int64_t)k * r.stride;
-    const int j = __ldg(A.col + e);
-    const AccT a = to_f(__ldg(A.val + e), AccT(0));
+  for (int k0 = 0; k0 < r.w; k0 += MV_U) {
+    int jj[MV_U];
+    AccT aa[MV_U];
 #pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-      const int c = lane + 32 * q;
-      if (c < K) acc[q] = fma(a, g(j, c), acc[q]);
+    for (int u = 0; u < MV_U; ++u) {
+      jj[u] = 0;
+      aa[u] = AccT(0);
+      if (k0 + u < r.w) {
+        const int64_t e = r.off + (int64_t)(k0 + u) * r.stride;
+        jj[u] = __ldg(A.col + e);
+        aa[u] = to_f(__ldg(A.val + e), AccT(0));
+      }
     }
+    AccT gg[MV_U][KPL];
+#pragma unroll
+    for (int u = 0; u < MV_U; ++u)
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) {
+        const int c = lane + 32 * q;
+        gg[u][q] = (k0 + u < r.w && c < K) ? g(jj[u], c) : AccT(0);
+      }
+#pragma unroll
+    for (int u = 0; u < MV_U; ++u)
+      if (k0 + u < r.w)
+#pragma unroll
+        for (int q = 0; q < KPL; ++q) {
+          const int c = lane + 32 * q;
+          if (c < K) acc[q] = fma(aa[u], gg[u][q], acc[q]);
+        }
   }
 }
 
@@ -102,15 +128,32 @@ __device__ void cols_reduce(double (&v)[NV][KPL], int K, double* part, int maxb,
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+  // the last block: thread t adds every G-th block's partial of column t % K
+  // starting at block t / K (G = blockDim / K groups), then thread c < K adds
+  // the G group sums in order -- fixed assignment, fixed order
+  __shared__ double gs[NV][MROWS_BLOCK];
+  const int G = blockDim.x / K;
+  const int c0 = threadIdx.x % K, g0 = threadIdx.x / K;
+  double t0[NV];
+#pragma unroll
+  for (int m = 0; m < NV; ++m) t0[m] = 0.0;
+  if (g0 < G)
+#pragma unroll 8
+    for (int b = g0; b < (int)gridDim.x; b += G)
+#pragma unroll
+      for (int m = 0; m < NV; ++m) t0[m] += __ldcg(&part[((size_t)m * maxb + b) * K + c0]);
+#pragma unroll
+  for (int m = 0; m < NV; ++m) gs[m][threadIdx.x] = t0[m];
+  __syncthreads();
+  if (threadIdx.x < K) {
     double t[NV];
 #pragma unroll
     for (int m = 0; m < NV; ++m) {
       double s = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(&part[((size_t)m * maxb + b) * K + c]);
+      for (int g = 0; g < G; ++g) s += gs[m][g * K + threadIdx.x];
       t[m] = s;
     }
-    epi(c, t);
+    epi(threadIdx.x, t);
   }
   if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -118,7 +161,7 @@ __device__ void cols_reduce(double (&v)[NV][KPL], int K, double* part, int maxb,
 // ------------------------------------------------------------------ V-cycle kernels
 
 template <int KPL, typename V, typename T, typename BT>
-__global__ void __launch_bounds__(MROWS_BLOCK)
+__global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     k_m_pre(SellView<V> Ah, int C, int K, const BT* __restrict__ B, T* __restrict__ R) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -175,7 +218,7 @@ struct MultiRzEpi {
 };
 
 template <int KPL, typename V, typename T, typename BT, typename XT, bool DOTS>
-__global__ void __launch_bounds__(MROWS_BLOCK)
+__global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     k_m_post(SellView<V> AP, int C, int K, const BT* __restrict__ B, const T* __restrict__ s,
              const T* __restrict__ R, const int32_t* __restrict__ agg, const T* __restrict__ Xc,
              XT* __restrict__ Z, const double* __restrict__ Q, double* part, int maxb,
@@ -290,10 +333,10 @@ struct MultiInitEpi {
 };
 
 template <int KPL>
-__global__ void __launch_bounds__(MROWS_BLOCK)
+__global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     k_m_residual(SellView<double> A, int C, int K, const double* __restrict__ B,
                  const double* __restrict__ X, double* __restrict__ R, double* part, int maxb,
-                 unsigned* ticket, MultiInitEpi epi) {
+                 unsigned* ticket, MultiInitEpi epi, float* __restrict__ R32) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double d[2][KPL];
@@ -310,6 +353,7 @@ __global__ void __launch_bounds__(MROWS_BLOCK)
         const double bi = B[i * K + c];
         const double ri = bi - acc[q];
         R[i * K + c] = ri;
+        if (R32) R32[i * K + c] = (float)ri;
         d[0][q] += ri * ri;
         d[1][q] += bi * bi;
       }
@@ -338,7 +382,7 @@ struct MultiPqEpi {
 };
 
 template <int KPL>
-__global__ void __launch_bounds__(MROWS_BLOCK)
+__global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     k_m_spmm_dot(SellView<double> A, int C, int K, const double* __restrict__ P,
                  double* __restrict__ Q, double* part, int maxb, unsigned* ticket, MultiPqEpi epi) {
   const int lane = threadIdx.x & 31;
@@ -393,7 +437,8 @@ template <int KPL>
 __global__ void __launch_bounds__(MROWS_BLOCK)
     k_m_update(int64_t n, int K, double* __restrict__ X, double* __restrict__ R,
                const double* __restrict__ P, const double* __restrict__ Q, const Scal* sc,
-               double* part, int maxb, unsigned* ticket, MultiRrEpi epi) {
+               double* part, int maxb, unsigned* ticket, MultiRrEpi epi,
+               float* __restrict__ R32) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double al[KPL], d[1][KPL];
@@ -414,6 +459,7 @@ __global__ void __launch_bounds__(MROWS_BLOCK)
         X[e] = X[e] + al[q] * P[e];
         const double ri = R[e] - al[q] * Q[e];
         R[e] = ri;
+        if (R32) R32[e] = (float)ri;
         d[0][q] += ri * ri;
       }
     }
@@ -458,10 +504,16 @@ __global__ void k_m_p_update(int64_t n, int K, double* __restrict__ P, const dou
 static int mgrid(const amg_handle* H, int64_t rows) {
   return grid_for(rows * 32, MROWS_BLOCK, H->num_sms, 8);
 }
+static int mgrid_mv(const amg_handle* H, int64_t rows) {
+  return grid_for(rows * 32, MROWS_BLOCK, H->num_sms, MV_BLOCKS);
+}
 
+// R32: the FP32 copy of R0 (FP32 hierarchies inside PCG), read by the
+// level-0 pre-smoother instead of converting each gathered FP64 element.
 template <typename T>
 static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, double* Z0,
-                    bool dots, const double* Q, int beta_form, bool first, cudaStream_t s) {
+                    bool dots, const double* Q, int beta_form, bool first, cudaStream_t s,
+                    const float* R32) {
   const int K = W.K;
   const int nl = (int)H->L.size();
   const int maxb = H->red.max_blocks;
@@ -479,7 +531,7 @@ static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, dou
   for (int l = 0; l < nl - 1; ++l) {
     const Level& L = H->L[l];
     T* r = (T*)W.lr[l];
-    const int g = mgrid(H, L.n);
+    const int g = mgrid_mv(H, L.n);
     if constexpr (sizeof(T) == 8) {
       const double* b = l == 0 ? R0 : (const double*)W.lb[l];
       const SellView<double> v = view<double>(L.A, L.ah64);
@@ -490,6 +542,10 @@ static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, dou
         const SellView<__nv_bfloat16> v = view<__nv_bfloat16>(L.A, L.ah16);
         AMG_DISPATCH_KPL(K, (k_m_pre<KPL, __nv_bfloat16, float, float><<<g, MROWS_BLOCK, 0, s>>>(
                                 v, L.A.C, K, (const float*)W.lb[l], r)));
+      } else if (l == 0 && R32) {
+        const SellView<float> v = view<float>(L.A, L.ah32);
+        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, float, float, float><<<g, MROWS_BLOCK, 0, s>>>(
+                                v, L.A.C, K, R32, r)));
       } else if (l == 0) {
         const SellView<float> v = view<float>(L.A, L.ah32);
         AMG_DISPATCH_KPL(K, (k_m_pre<KPL, float, float, double><<<g, MROWS_BLOCK, 0, s>>>(
@@ -508,7 +564,7 @@ static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, dou
   AMG_TRY(coarse((const T*)W.lb[nl - 1], (T*)W.lx[nl - 1]));
   for (int l = nl - 2; l >= 0; --l) {
     const Level& L = H->L[l];
-    const int g = mgrid(H, L.n);
+    const int g = mgrid_mv(H, L.n);
     const T* xc = (const T*)W.lx[l + 1];
     const T* sv = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
     const T* rv = (const T*)W.lr[l];
@@ -560,10 +616,11 @@ static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, dou
 }
 
 static int m_vcycle_any(const amg_handle* H, const MultiWs& W, const double* R0, double* Z0,
-                        bool dots, const double* Q, int beta_form, bool first, cudaStream_t s) {
+                        bool dots, const double* Q, int beta_form, bool first, cudaStream_t s,
+                        const float* R32 = nullptr) {
   if (H->opt.precision == AMG_PREC_F32)
-    return m_vcycle<float>(H, W, R0, Z0, dots, Q, beta_form, first, s);
-  return m_vcycle<double>(H, W, R0, Z0, dots, Q, beta_form, first, s);
+    return m_vcycle<float>(H, W, R0, Z0, dots, Q, beta_form, first, s, R32);
+  return m_vcycle<double>(H, W, R0, Z0, dots, Q, beta_form, first, s, nullptr);
 }
 
 // Workspace for K right-hand sides, kept in the handle (reallocated if K grows).
@@ -576,7 +633,8 @@ static int multi_ws(amg_handle* H, int K, MultiWs** out) {
   }
   if (W) {  // grow: drop the old buffers
     Arena& ar = H->arena;
-    for (void* p : {(void*)W->R, (void*)W->Z, (void*)W->P, (void*)W->Q, (void*)W->cy,
+    for (void* p : {(void*)W->R, (void*)W->R32, (void*)W->Z, (void*)W->P, (void*)W->Q,
+                    (void*)W->cy,
                     (void*)W->part, (void*)W->ticket, (void*)W->sc, (void*)W->nactive})
       ar.release(p);
     for (size_t l = 0; l < H->L.size(); ++l) {
@@ -598,6 +656,7 @@ static int multi_ws(amg_handle* H, int K, MultiWs** out) {
   const int64_t n = H->L[0].n;
   const size_t vb = H->opt.precision == AMG_PREC_F32 ? 4 : 8;
   AMG_TRY(ar.alloc_n(&W->R, n * K));
+  if (H->opt.precision == AMG_PREC_F32 && H->L.size() > 1) AMG_TRY(ar.alloc_n(&W->R32, n * K));
   AMG_TRY(ar.alloc_n(&W->Z, n * K));
   AMG_TRY(ar.alloc_n(&W->P, n * K));
   AMG_TRY(ar.alloc_n(&W->Q, n * K));
@@ -652,12 +711,12 @@ int pcg_multi_run(amg_handle* H, int K, const double* B, double* X, const pcg_op
   const int maxb = H->red.max_blocks;
   const SellView<double> A = view<double>(L0.A, L0.A.v64);
   const int C = L0.A.C;
-  const int g = mgrid(H, n);
+  const int g = mgrid(H, n), gmv = mgrid_mv(H, n);
   AMG_CUDA_TRY(cudaEventRecord(H->ev0, s));
   AMG_CUDA_TRY(cudaMemsetAsync(W->nactive, 0, sizeof(int), s));
   MultiInitEpi ie{W->sc, o->tol, o->maxit, W->nactive, 0};
-  AMG_DISPATCH_KPL(K, (k_m_residual<KPL><<<g, MROWS_BLOCK, 0, s>>>(A, C, K, B, X, W->R, W->part,
-                                                                  maxb, W->ticket, ie)));
+  AMG_DISPATCH_KPL(K, (k_m_residual<KPL><<<gmv, MROWS_BLOCK, 0, s>>>(
+                          A, C, K, B, X, W->R, W->part, maxb, W->ticket, ie, W->R32)));
   AMG_LAUNCH_CHECK();
   int act = 0;
   auto read_act = [&]() -> int {
@@ -670,29 +729,29 @@ int pcg_multi_run(amg_handle* H, int K, const double* B, double* X, const pcg_op
   MultiRrEpi re{W->sc, o->tol, o->maxit, W->nactive};
   int k = 0;
   if (act > 0) {
-    AMG_TRY(m_vcycle_any(H, *W, W->R, W->Z, true, W->Q, beta_form, true, s));
+    AMG_TRY(m_vcycle_any(H, *W, W->R, W->Z, true, W->Q, beta_form, true, s, W->R32));
     AMG_CUDA_TRY(cudaMemcpyAsync(W->P, W->Z, sizeof(double) * n * K, cudaMemcpyDeviceToDevice, s));
     for (;;) {
-      AMG_DISPATCH_KPL(K, (k_m_spmm_dot<KPL><<<g, MROWS_BLOCK, 0, s>>>(A, C, K, W->P, W->Q, W->part,
-                                                                      maxb, W->ticket, pe)));
+      AMG_DISPATCH_KPL(K, (k_m_spmm_dot<KPL><<<gmv, MROWS_BLOCK, 0, s>>>(
+                              A, C, K, W->P, W->Q, W->part, maxb, W->ticket, pe)));
       AMG_LAUNCH_CHECK();
       AMG_CUDA_TRY(cudaMemsetAsync(W->nactive, 0, sizeof(int), s));
       AMG_DISPATCH_KPL(K, (k_m_update<KPL><<<g, MROWS_BLOCK, 0, s>>>(n, K, X, W->R, W->P, W->Q,
                                                                     W->sc, W->part, maxb,
-                                                                    W->ticket, re)));
+                                                                    W->ticket, re, W->R32)));
       AMG_LAUNCH_CHECK();
       ++k;
       AMG_TRY(read_act());
       if (act == 0 || k >= o->maxit) break;
-      AMG_TRY(m_vcycle_any(H, *W, W->R, W->Z, true, W->Q, beta_form, false, s));
+      AMG_TRY(m_vcycle_any(H, *W, W->R, W->Z, true, W->Q, beta_form, false, s, W->R32));
       AMG_DISPATCH_KPL(K, (k_m_p_update<KPL><<<g, MROWS_BLOCK, 0, s>>>(n, K, W->P, W->Z, W->sc)));
       AMG_LAUNCH_CHECK();
     }
   }
   AMG_CUDA_TRY(cudaEventRecord(H->ev1, s));
   MultiInitEpi te{W->sc, o->tol, o->maxit, W->nactive, 1};
-  AMG_DISPATCH_KPL(K, (k_m_residual<KPL><<<g, MROWS_BLOCK, 0, s>>>(A, C, K, B, X, W->Z, W->part,
-                                                                  maxb, W->ticket, te)));
+  AMG_DISPATCH_KPL(K, (k_m_residual<KPL><<<gmv, MROWS_BLOCK, 0, s>>>(
+                          A, C, K, B, X, W->Z, W->part, maxb, W->ticket, te, nullptr)));
   AMG_LAUNCH_CHECK();
   AMG_CUDA_TRY(cudaMemcpyAsync(W->sc_host, W->sc, sizeof(Scal) * K, cudaMemcpyDeviceToHost, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));

@@ -1079,7 +1079,8 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
                                                         : std::vector<int64_t>{0, Lc.n};
     const int nb = (int)brow.size() - 1;
     std::vector<int64_t> bmat(nb + 1, 0);
-    for (int b = 0; b < nb; ++b) bmat[b + 1] = bmat[b] + (brow[b + 1] - brow[b]) * (brow[b + 1] - brow[b]);
+    for (int b = 0; b < nb; ++b)
+      bmat[b + 1] = bmat[b] + (brow[b + 1] - brow[b]) * (brow[b + 1] - brow[b]);
     H->nblk = nb;
     H->cblk_row = brow;
     const int64_t* rp = H->L.size() == 1 ? A->rowptr : Lc.rowptr;

@@ -407,11 +407,11 @@ int tail_init(amg_handle* H, cudaStream_t s) {
   const size_t smem = sizeof(double) * 2 * (size_t)COARSE_SMALL;
   int occ = 0;
   if (H->opt.precision == AMG_PREC_F32)
-    AMG_CUDA_TRY(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tail<float, false>, TAIL_BLOCK, smem));
+    AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tail<float, false>,
+                                                               TAIL_BLOCK, smem));
   else
-    AMG_CUDA_TRY(
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tail<double, false>, TAIL_BLOCK, smem));
+    AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tail<double, false>,
+                                                               TAIL_BLOCK, smem));
   H->tail_grid = std::min(occ, 1) * H->num_sms;
   return AMG_OK;
 }

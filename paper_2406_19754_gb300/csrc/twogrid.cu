@@ -169,7 +169,9 @@ int twogrid_loss(amg_handle* H, int nsamples, int K, const double* e0, double* l
   po.tol = 1e-12;
   po.maxit = 1000;
   po.beta_form = PCG_BETA_FR;
-  auto spmv = [&](const double* x, double* y) { return sell_spmv64(L0.A, 1.0, x, 0.0, y, H->num_sms, s); };
+  auto spmv = [&](const double* x, double* y) {
+    return sell_spmv64(L0.A, 1.0, x, 0.0, y, H->num_sms, s);
+  };
   auto smooth = [&](const double* x, double* o, double* Ax) -> int {
     AMG_DISPATCH_TPR(sell_code(L0.A),
                      (k_tg_smooth<TPR><<<gs, SELL_BLOCK, 0, s>>>(A, sv, x, o, Ax)));

@@ -58,7 +58,9 @@ struct VcycleDotEpi {
 
 // MS: the level smooths more than once per side (xp and e are used); the
 // one-sweep instantiations do not carry them, which keeps their registers
-// within the occupancy bound.
+// within the occupancy bound.  (With dot products the 32-register bound makes
+// the reduction tail spill a few values; a 40-register bound at 6 blocks per
+// SM measured slower.)
 template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT, bool MS>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_post(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,

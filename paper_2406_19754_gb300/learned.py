@@ -77,9 +77,10 @@ class Mlp:
                "mlp_features")
         return feat
 
-    def forward(self, feat, stream=None):
+    def forward(self, feat, out=None, stream=None):
         feat = _dev(feat, torch.float32, "feat")
-        om = torch.empty(feat.shape[0], dtype=torch.float32, device=feat.device)
+        om = out if out is not None else torch.empty(feat.shape[0], dtype=torch.float32,
+                                                       device=feat.device)
         _check(self._lib.mlp_forward(self.h, feat.shape[0], _ptr(feat), _ptr(om),
                                      _stream(stream)), "mlp_forward")
         return om
@@ -188,6 +189,23 @@ def evaluate(weights: str | None, side: int = 256, sigma: float = 2.5, seed: int
         mlp.load(weights)
     feat = mlp.features(Ad, (side, side, side))
     om = mlp.forward(feat)
+    # inference cost per evaluation: features + forward + new smoother scales
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(repeats):
+        feat = mlp.features(Ad, (side, side, side))
+        om = mlp.forward(feat)
+        H.set_smoother_weights(om)
+    e1.record()
+    torch.cuda.synchronize()
+    out["inference_ms"] = e0.elapsed_time(e1) / repeats
+    fw0, fw1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fw0.record()
+    for _ in range(repeats):
+        mlp.forward(feat, out=om)
+    fw1.record()
+    torch.cuda.synchronize()
+    out["forward_ms"] = fw0.elapsed_time(fw1) / repeats
     H.set_smoother_weights(om)
     out["learned"] = dict(zip(("iterations", "seconds", "true_relres"), timed()))
     out["omega_mean"] = float(om.mean())
