@@ -54,6 +54,11 @@ def _declare(L):
                                     C.c_double, _I64, C.POINTER(C.c_int)]
     L.orc_free.argtypes = [_P]
     L.orc_set_cycle.argtypes = [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double]
+    L.orc_setup_smoothed.restype = _P
+    L.orc_setup_smoothed.argtypes = [_I64, _P, _P, _P, C.c_int, _I64, C.c_int, C.c_double, _I64,
+                                     _P]
+    L.orc_level_prolongator.restype = _I64
+    L.orc_level_prolongator.argtypes = [_P, C.c_int, _P, _P, _P, _P]
     L.orc_setup_reuse.restype = _P
     L.orc_setup_reuse.argtypes = [_I64, _P, _P, _P, _P, _I64, _P]
     L.orc_levels.restype = C.c_int
@@ -239,7 +244,7 @@ class Hierarchy:
 
     def __init__(self, A, sweeps=2, max_coarse=200, max_levels=30, stall=0.9,
                  max_dense=8192, omega=None, systems=None, smooth_sweeps=1, variable=False,
-                 coarse="cholesky", coarse_maxit=40, coarse_tol=1e-4):
+                 coarse="cholesky", coarse_maxit=40, coarse_tol=1e-4, smoothed=False):
         """systems: row offsets (nsys + 1) of independent systems stacked block
         diagonally in A; coarsening then stops when each has <= max_coarse rows.
         smooth_sweeps: l1-Jacobi sweeps nu_0 before and after the coarse
@@ -249,7 +254,11 @@ class Hierarchy:
         n, rp, ci, v = csr_args(A)
         self._keep = (rp, ci, v)
         st = C.c_int(0)
-        if systems is not None:
+        if smoothed:
+            assert systems is None and omega is None
+            self.h = lib().orc_setup_smoothed(n, _p(rp), _p(ci), _p(v), sweeps, max_coarse,
+                                              max_levels, stall, max_dense, C.byref(st))
+        elif systems is not None:
             so = _i64(systems)
             self.h = lib().orc_setup_systems(n, _p(rp), _p(ci), _p(v), len(so) - 1, _p(so),
                                              sweeps, max_coarse, max_levels, stall, max_dense,
@@ -305,6 +314,17 @@ class Hierarchy:
         a = np.empty(self.level_n(l), dtype=np.int32)
         lib().orc_level_agg(self.h, l, _p(a))
         return a
+
+    def level_prolongator(self, l):
+        """Smoothed P of level l as CSR (rowptr, col, val) and its damping w."""
+        nnz = lib().orc_level_prolongator(self.h, l, None, None, None, None)
+        n = self.level_n(l)
+        rp = np.empty(n + 1, dtype=np.int64)
+        ci = np.empty(nnz, dtype=np.int32)
+        v = np.empty(nnz)
+        w = C.c_double(0.0)
+        lib().orc_level_prolongator(self.h, l, _p(rp), _p(ci), _p(v), C.byref(w))
+        return (rp, ci, v), w.value
 
     def level_dinv(self, l):
         d = np.empty(self.level_n(l))

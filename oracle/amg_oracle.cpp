@@ -42,6 +42,14 @@
 //    l1-Jacobi sweeps before and nu after the coarse correction, the first
 //    pre-sweep from a zero guess.  The variable V-cycle (VMATCH) uses nu_0
 //    sweeps on level 0, doubled on each coarser level: nu_l = nu_0 * 2^l.
+//  * Smoothed prolongator (Sec. 2.3, SMATCH): P = (I - w D^-1 A) P_hat with
+//    D = diag(A) and w = 1 / ||D^-1 A||_inf = 1 / max_i (sum_j |a_ij|) / a_ii.
+//    Entry (i, J) of P is [agg(i) = J] - w * ((A P_hat)_iJ / a_ii), where
+//    (A P_hat)_iJ sums a_ij over agg(j) = J in ascending j; P's columns are
+//    kept ascending.  The coarse matrix is P^T (A P) by two sparse products;
+//    each output entry sums its contributions in ascending order of the
+//    inner index, each as one product and one addition (no fused multiply-
+//    add).  The V-cycle restricts with P^T and prolongs with P.
 //  * Iterative coarsest solve (VBM, Sec. 3): PCG with the coarsest level's
 //    l1-Jacobi scaling as preconditioner, zero initial guess, at most maxit
 //    iterations; it stops once ||r|| <= tol * ||b|| (the paper gives only the
@@ -72,10 +80,14 @@ struct Level {
   std::vector<int32_t> agg;      // row -> aggregate on the next level
   std::vector<int32_t> members;  // stride (1 << sweeps), ascending, -1 padded
   int64_t nc = 0;
+  // smoothed prolongator (empty when P is the 0/1 aggregate map) and P^T
+  Csr P, Pt;
+  double wp = 0.0;  // its damping w = 1 / ||D^-1 A||_inf
 };
 
 struct Hierarchy {
   int sweeps = 2;
+  int smooth_p = 0;  // 1: smoothed prolongators (Sec. 2.3)
   std::vector<Level> lev;
   std::vector<double> chol;  // dense lower factor of the coarsest matrix, row-major
   int64_t nco = 0;
@@ -266,6 +278,112 @@ void l1_scale(const Csr& A, const double* omega, std::vector<double>& dinv) {
   }
 }
 
+// ---------------------------------------------------------------- smoothed P
+
+// w = 1 / max_i (sum_j |a_ij|) / a_ii.
+double prolongator_damping(const Csr& A) {
+  double m = 0.0;
+  for (int64_t i = 0; i < A.n; ++i) {
+    double s = 0.0, d = 0.0;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      s += std::fabs(A.val[e]);
+      if (A.col[e] == i) d = A.val[e];
+    }
+    m = std::max(m, s / d);
+  }
+  return 1.0 / m;
+}
+
+// P = P_hat - w D^-1 (A P_hat), columns ascending.
+void smoothed_prolongator(const Csr& A, const std::vector<int32_t>& agg, int64_t nc, double w,
+                          Csr& P) {
+  P.n = A.n;
+  P.rowptr.assign(A.n + 1, 0);
+  P.col.clear();
+  P.val.clear();
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t i = 0; i < A.n; ++i) {
+    row.clear();
+    double aii = 0.0;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      if (A.col[e] == i) aii = A.val[e];
+      const int32_t J = agg[A.col[e]];
+      bool found = false;
+      for (auto& c : row)
+        if (c.first == J) {
+          c.second = c.second + A.val[e];
+          found = true;
+        }
+      if (!found) row.push_back({J, A.val[e]});
+    }
+    std::sort(row.begin(), row.end(),
+              [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                return a.first < b.first;
+              });
+    for (const auto& c : row) {
+      const double ind = c.first == agg[i] ? 1.0 : 0.0;
+      P.col.push_back(c.first);
+      P.val.push_back(ind - w * (c.second / aii));
+    }
+    P.rowptr[i + 1] = (int64_t)P.col.size();
+  }
+  (void)nc;
+}
+
+// C = X Y (X: n x m, Y: m x k CSR, columns ascending in each row): entry
+// (i, J) sums x_ik * y_kJ over the entries k of row i in ascending order.
+void spgemm(const Csr& X, const Csr& Y, Csr& Cm) {
+  Cm.n = X.n;
+  Cm.rowptr.assign(X.n + 1, 0);
+  Cm.col.clear();
+  Cm.val.clear();
+  std::vector<std::pair<int32_t, double>> acc;  // (J, sum), first-touch order
+  for (int64_t i = 0; i < X.n; ++i) {
+    acc.clear();
+    for (int64_t e = X.rowptr[i]; e < X.rowptr[i + 1]; ++e) {
+      const int64_t k = X.col[e];
+      for (int64_t f = Y.rowptr[k]; f < Y.rowptr[k + 1]; ++f) {
+        const double t = X.val[e] * Y.val[f];
+        bool found = false;
+        for (auto& c : acc)
+          if (c.first == Y.col[f]) {
+            c.second = c.second + t;
+            found = true;
+            break;
+          }
+        if (!found) acc.push_back({Y.col[f], t});
+      }
+    }
+    std::sort(acc.begin(), acc.end(),
+              [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                return a.first < b.first;
+              });
+    for (const auto& c : acc) {
+      Cm.col.push_back(c.first);
+      Cm.val.push_back(c.second);
+    }
+    Cm.rowptr[i + 1] = (int64_t)Cm.col.size();
+  }
+}
+
+Csr transpose(const Csr& X, int64_t ncols) {
+  Csr T;
+  T.n = ncols;
+  T.rowptr.assign(ncols + 1, 0);
+  for (int32_t c : X.col) ++T.rowptr[c + 1];
+  for (int64_t J = 0; J < ncols; ++J) T.rowptr[J + 1] += T.rowptr[J];
+  T.col.resize(X.col.size());
+  T.val.resize(X.col.size());
+  std::vector<int64_t> pos(T.rowptr.begin(), T.rowptr.end() - 1);
+  for (int64_t i = 0; i < X.n; ++i)  // rows ascending: each column of T ascending
+    for (int64_t e = X.rowptr[i]; e < X.rowptr[i + 1]; ++e) {
+      const int64_t p = pos[X.col[e]]++;
+      T.col[p] = (int32_t)i;
+      T.val[p] = X.val[e];
+    }
+  return T;
+}
+
 // ---------------------------------------------------------------- Cholesky
 
 // Right-looking Cholesky of a dense SPD n x n matrix (row-major, full).
@@ -319,6 +437,21 @@ Csr csr_copy(int64_t n, const int64_t* rp, const int32_t* ci, const double* v) {
   return A;
 }
 
+// The next level's matrix: P_hat^T A P_hat in canonical order, or with the
+// smoothed prolongator P^T (A P) (which also keeps P and P^T on the level).
+void coarse_matrix(const Hierarchy& H, Level& L, int stride, Csr& Ac) {
+  if (!H.smooth_p) {
+    galerkin(L.A, L.agg, L.nc, L.members, stride, Ac);
+    return;
+  }
+  L.wp = prolongator_damping(L.A);
+  smoothed_prolongator(L.A, L.agg, L.nc, L.wp, L.P);
+  L.Pt = transpose(L.P, L.nc);
+  Csr Q;
+  spgemm(L.A, L.P, Q);
+  spgemm(L.Pt, Q, Ac);
+}
+
 // Returns 0 or a negative status (-4 not SPD coarse matrix, -1 arguments).
 // Largest diagonal block (system) of a level; the whole level without systems.
 int64_t largest_block(const std::vector<int64_t>& sys, int64_t n) {
@@ -338,8 +471,10 @@ int64_t largest_block(const std::vector<int64_t>& sys, int64_t n) {
 // build the aggregates by matching.
 int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
           double stall, int64_t max_dense, const double* omega,
-          std::vector<int64_t> sys = std::vector<int64_t>(), const Hierarchy* like = nullptr) {
+          std::vector<int64_t> sys = std::vector<int64_t>(), const Hierarchy* like = nullptr,
+          int smooth_p = 0) {
   H.sweeps = sweeps;
+  H.smooth_p = like ? like->smooth_p : smooth_p;
   H.lev.clear();
   const int stride = 1 << sweeps;
   H.lev.emplace_back();
@@ -354,7 +489,7 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
       L.nc = like->lev[l].nc;
       L.members = like->lev[l].members;
       Level next;
-      galerkin(L.A, L.agg, L.nc, L.members, stride, next.A);
+      coarse_matrix(H, L, stride, next.A);
       H.lev.push_back(std::move(next));
       continue;
     }
@@ -380,7 +515,7 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
     L.nc = nc;
     members_of(comp, nc, stride, L.members);
     Level next;
-    galerkin(L.A, L.agg, nc, L.members, stride, next.A);
+    coarse_matrix(H, L, stride, next.A);
     H.lev.push_back(std::move(next));
     if (sys.size() >= 2) {  // aggregates never span systems
       std::vector<int64_t> nxt(sys.size());
@@ -455,17 +590,26 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
   spmv(L.A, x, r.data());
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];  // residual
   const int stride = 1 << H.sweeps;
-  for (int64_t I = 0; I < L.nc; ++I) {  // restriction b_c = P^T r
-    double s = 0.0;
-    for (int k = 0; k < stride; ++k) {
-      int32_t i = L.members[I * stride + k];
-      if (i < 0) break;
-      s = (k == 0) ? r[i] : s + r[i];
+  if (H.smooth_p) {
+    spmv(L.Pt, r.data(), bc.data());  // restriction b_c = P^T r
+  } else {
+    for (int64_t I = 0; I < L.nc; ++I) {  // restriction b_c = P^T r
+      double s = 0.0;
+      for (int k = 0; k < stride; ++k) {
+        int32_t i = L.members[I * stride + k];
+        if (i < 0) break;
+        s = (k == 0) ? r[i] : s + r[i];
+      }
+      bc[I] = s;
     }
-    bc[I] = s;
   }
   vcycle(H, l + 1, bc.data(), xc.data());
-  for (int64_t i = 0; i < n; ++i) x[i] = x[i] + xc[L.agg[i]];  // prolongation
+  if (H.smooth_p) {  // prolongation x += P x_c
+    spmv(L.P, xc.data(), r.data());
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] + r[i];
+  } else {
+    for (int64_t i = 0; i < n; ++i) x[i] = x[i] + xc[L.agg[i]];
+  }
   for (int64_t k = 0; k < nu; ++k) jacobi_sweep(L, b, x, r.data());  // post-smooth
 }
 
@@ -641,6 +785,26 @@ void* orc_setup(int64_t n, const int64_t* rp, const int32_t* ci, const double* v
   *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
                   omega);
   return H;
+}
+
+// orc_setup with smoothed prolongators (smooth_p = 1, Sec. 2.3).
+void* orc_setup_smoothed(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                         int sweeps, int64_t max_coarse, int max_levels, double stall,
+                         int64_t max_dense, int* status) {
+  Hierarchy* H = new Hierarchy();
+  *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
+                  nullptr, std::vector<int64_t>(), nullptr, 1);
+  return H;
+}
+
+// P (n x n_c, smoothed) of level l and its damping w; rp/ci/v null to get nnz.
+int64_t orc_level_prolongator(void* h, int l, int64_t* rp, int32_t* ci, double* v, double* w) {
+  const Level& L = ((Hierarchy*)h)->lev[l];
+  if (w) *w = L.wp;
+  if (rp) std::memcpy(rp, L.P.rowptr.data(), sizeof(int64_t) * (L.P.n + 1));
+  if (ci) std::memcpy(ci, L.P.col.data(), sizeof(int32_t) * L.P.nnz());
+  if (v) std::memcpy(v, L.P.val.data(), sizeof(double) * L.P.nnz());
+  return L.P.nnz();
 }
 
 // Hierarchy of nsys systems stacked block diagonally (sys_off: nsys + 1 row
