@@ -83,8 +83,11 @@ typedef struct amg_options {
                             default 8192, at most 16384 */
   int precision;         /* AMG_PREC_F64 (default) or AMG_PREC_F32 */
   int bf16_from_level;   /* with F32: levels >= this keep BF16 values; 0 = off */
-  int slice_height;      /* sliced-ELL slice height 8/16/32/64; 0 = default 32 */
-  int threads_per_row;   /* 1/2/4/8 threads per row; 0 = default */
+  int slice_height;      /* sliced-ELL rows per slice 1/2/4/8/16/32 (slice height
+                            x threads per row = 32); 0 = default */
+  int threads_per_row;   /* 1/2/4/8/16/32 threads per row; 0 = default: 1 (32
+                            rows a slice), more on levels whose rows average
+                            64 entries or more (about one thread per 16) */
   int autotune;          /* 1: choose slice height / threads per row per level by
                             timing the kernels at setup */
   int64_t tail_rows;     /* levels (other than level 0) with at most this many
@@ -111,6 +114,13 @@ typedef struct amg_options {
                             4-byte indices.  Same results bit for bit; fewer
                             bytes, but slower on GB300 (more load instructions
                             for fewer bytes each) */
+  int smooth_prolongator; /* 1: smoothed prolongators P = (I - w D^-1 A) P_hat,
+                            w = 1 / ||D^-1 A||_inf, coarse matrices P^T (A P)
+                            (Sec. 2.3, SMATCH); restriction by P^T, prolongation
+                            by P.  FP64 only; not with batched systems,
+                            several right-hand sides or the two-grid solver;
+                            tail_rows is ignored.  0 (default): P_hat, the 0/1
+                            aggregate map */
 } amg_options;
 
 /* PCG controls (Sec. 3, psb_krylov arguments). */
@@ -370,10 +380,11 @@ int amg_level_info(const amg_handle* H, int level, int64_t* n, int64_t* nnz);
  * whether column indices are compressed: slot e of ELL column k of a slice
  * then holds a 2-byte offset from a 4-byte base shared by the C slots of that
  * column (else a plain 4-byte index).  Compression is used whenever every
- * slice's offsets fit 16 bits; results are identical either way.  The
- * layout of A P (the post-smoother's operator) is reported when `ap` is 1.
- * No counterpart in the paper.  Errors: AMG_ERR_ARG (bad level, NULL out,
- * ap = 1 on the coarsest level).
+ * slice's offsets fit 16 bits; results are identical either way.  `ap`
+ * picks the operator: 0 A, 1 A P (the post-smoother's operator), and with
+ * smoothed prolongators 2 P and 3 R = P^T (restriction).  No counterpart in
+ * the paper.  Errors: AMG_ERR_ARG (bad level, NULL out, ap outside 0..3,
+ * ap > 0 on the coarsest level, ap >= 2 without smoothed prolongators).
  */
 typedef struct amg_layout {
   int slice_height;
@@ -392,6 +403,18 @@ int amg_level_layout(const amg_handle* H, int level, int ap, amg_layout* out);
  */
 int amg_level_export(const amg_handle* H, int level, int64_t* rowptr, int32_t* col,
                      double* val, int32_t* agg, double* sscale, amg_stream_t stream);
+
+/*
+ * The smoothed prolongator of level l (option smooth_prolongator; Sec. 2.3):
+ * P = (I - w D^-1 A_l) P_hat, n_l x n_{l+1}, columns ascending in every row,
+ * copied into caller device buffers (each may be NULL): rowptr int64[n_l+1],
+ * col int32[nnz], val float64[nnz].  nnz and w (the damping
+ * 1 / max_i sum_j |a_ij| / a_ii): host, may be NULL.  Asynchronous.
+ * Errors: AMG_ERR_ARG (coarsest or bad level, handle without smoothed
+ * prolongators).
+ */
+int amg_level_prolongator(const amg_handle* H, int level, int64_t* rowptr, int32_t* col,
+                          double* val, int64_t* nnz, double* w, amg_stream_t stream);
 
 /*
  * Pairwise locally-dominant weighted matching of the graph of A (Sec. 2.3;

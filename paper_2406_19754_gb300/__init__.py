@@ -117,10 +117,11 @@ class Hierarchy:
         return n.value, nnz.value
 
     def level_layout(self, l, ap=False):
-        """Kernel storage of level l's matrix (or of A P): dict with
+        """Kernel storage of level l's matrix (ap False/0), of A P (True/1),
+        or with smoothed prolongators of P (2) or R = P^T (3): dict with
         slice_height, threads_per_row, slots, compressed."""
         o = _lib.AmgLayout()
-        _check(self._lib.amg_level_layout(self.h, l, 1 if ap else 0, C.byref(o)))
+        _check(self._lib.amg_level_layout(self.h, l, int(ap), C.byref(o)))
         return dict(slice_height=o.slice_height, threads_per_row=o.threads_per_row,
                     slots=o.slots, compressed=bool(o.compressed))
 
@@ -143,6 +144,22 @@ class Hierarchy:
         _check(self._lib.amg_level_export(self.h, l, _ptr(rp), _ptr(cl), _ptr(vl), _ptr(agg),
                                           _ptr(ss), _stream(stream)), "amg_level_export")
         return out
+
+    def level_prolongator(self, l, stream=None):
+        """Smoothed prolongator of level l (option smooth_prolongator):
+        ((rowptr, col, val) CUDA tensors, damping w)."""
+        nnz, w = C.c_int64(), C.c_double()
+        _check(self._lib.amg_level_prolongator(self.h, l, None, None, None, C.byref(nnz),
+                                               C.byref(w), _stream(stream)),
+               "amg_level_prolongator")
+        n = self.level_info(l)[0]
+        dev = torch.device("cuda")
+        rp = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        cl = torch.empty(nnz.value, dtype=torch.int32, device=dev)
+        vl = torch.empty(nnz.value, dtype=torch.float64, device=dev)
+        _check(self._lib.amg_level_prolongator(self.h, l, _ptr(rp), _ptr(cl), _ptr(vl), None,
+                                               None, _stream(stream)), "amg_level_prolongator")
+        return (rp, cl, vl), w.value
 
     def operator_complexity(self):
         nnz = [self.level_info(l)[1] for l in range(self.levels)]

@@ -39,7 +39,8 @@ class AmgOptions(C.Structure):
                 ("tail_rows", C.c_int64), ("smooth_sweeps", C.c_int),
                 ("variable_cycle", C.c_int), ("coarse_solver", C.c_int),
                 ("coarse_maxit", C.c_int), ("coarse_tol", C.c_double),
-                ("compress_columns", C.c_int)]
+                ("compress_columns", C.c_int),
+                ("smooth_prolongator", C.c_int)]
 
 
 class PcgOptions(C.Structure):
@@ -99,6 +100,8 @@ SIGNATURES = {
     "amg_level_info": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "amg_level_layout": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(AmgLayout)]),
     "amg_level_export": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "amg_level_prolongator": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_double), _P]),
     "amg_pairwise_match": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_pairwise_match_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_debug_fail_alloc_after": (C.c_int, [C.c_long]),

@@ -30,6 +30,7 @@ int amg_default_options(amg_options* o) {
   o->coarse_maxit = 40;
   o->coarse_tol = 1e-4;
   o->compress_columns = 0;
+  o->smooth_prolongator = 0;
   return AMG_OK;
 }
 
@@ -67,14 +68,15 @@ static int check_options(const amg_options& o) {
   if (o.precision != AMG_PREC_F64 && o.precision != AMG_PREC_F32) return AMG_ERR_ARG;
   if (o.bf16_from_level < 0 || o.tail_rows < 0) return AMG_ERR_ARG;
   if (o.compress_columns != 0 && o.compress_columns != 1) return AMG_ERR_ARG;
+  if (o.smooth_prolongator != 0 && o.smooth_prolongator != 1) return AMG_ERR_ARG;
   if (o.smooth_sweeps < 1 || o.smooth_sweeps > 8) return AMG_ERR_ARG;
   if (o.variable_cycle != 0 && o.variable_cycle != 1) return AMG_ERR_ARG;
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return AMG_ERR_ARG;
   if (o.coarse_maxit < 0 || o.coarse_maxit > 100000 || !(o.coarse_tol >= 0.0))
     return AMG_ERR_ARG;
   const int C = o.slice_height, t = o.threads_per_row;
-  if (C != 0 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
-  if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8) return AMG_ERR_ARG;
+  if (C != 0 && C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
+  if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return AMG_ERR_ARG;
   if (C && t && C * t != 32) return AMG_ERR_ARG;
   return AMG_OK;
 }
@@ -149,6 +151,9 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   int32_t* cat_ci = nullptr;
   double* cat_va = nullptr;
   if (systems && H->opt.coarse_solver != 0) return AMG_ERR_UNSUPPORTED;
+  if (H->opt.smooth_prolongator &&
+      (systems || H->opt.precision != AMG_PREC_F64 || H->opt.autotune))
+    return AMG_ERR_UNSUPPORTED;
   if (systems) {  // batched: one block-diagonal matrix with system-aligned slices
     int dev = 0, sms = 0;
     AMG_CUDA_TRY(cudaGetDevice(&dev));
@@ -324,14 +329,14 @@ int pcg_solve(amg_handle* H, const double* b, double* x, const pcg_options* o, p
 int amg_vcycle_apply_multi(amg_handle* H, int nrhs, const double* R, double* Z,
                            amg_stream_t stream) {
   if (!H || !R || !Z || (const double*)Z == R || nrhs < 1 || nrhs > 64) return AMG_ERR_ARG;
-  if (H->L.size() < 2 || H->L[0].A.row0) return AMG_ERR_UNSUPPORTED;
+  if (H->L.size() < 2 || H->L[0].A.row0 || H->opt.smooth_prolongator) return AMG_ERR_UNSUPPORTED;
   return vcycle_multi(H, nrhs, R, Z, (cudaStream_t)stream);
 }
 
 int pcg_solve_multi(amg_handle* H, int nrhs, const double* B, double* X, const pcg_options* o,
                     pcg_stats* st, amg_stream_t stream) {
   if (!H || !B || !X || nrhs < 1 || nrhs > 64) return AMG_ERR_ARG;
-  if (H->L.size() < 2 || H->L[0].A.row0) return AMG_ERR_UNSUPPORTED;
+  if (H->L.size() < 2 || H->L[0].A.row0 || H->opt.smooth_prolongator) return AMG_ERR_UNSUPPORTED;
   pcg_options def;
   pcg_default_options(&def);
   const pcg_options* op = o ? o : &def;
@@ -344,6 +349,7 @@ int pcg_solve_multi(amg_handle* H, int nrhs, const double* B, double* X, const p
 int amg_twogrid_loss(amg_handle* H, int nsamples, int ncycles, const double* e0, double* loss,
                      float* domega, amg_stream_t stream) {
   if (!H || nsamples < 1 || ncycles < 1 || !e0 || !loss) return AMG_ERR_ARG;
+  if (H->opt.smooth_prolongator) return AMG_ERR_UNSUPPORTED;
   return twogrid_loss(H, nsamples, ncycles, e0, loss, domega, (cudaStream_t)stream);
 }
 
@@ -361,9 +367,12 @@ int amg_level_info(const amg_handle* H, int level, int64_t* n, int64_t* nnz) {
 }
 
 int amg_level_layout(const amg_handle* H, int level, int ap, amg_layout* out) {
-  if (!H || !out || level < 0 || level >= (int)H->L.size()) return AMG_ERR_ARG;
+  if (!H || !out || level < 0 || level >= (int)H->L.size() || ap < 0 || ap > 3)
+    return AMG_ERR_ARG;
   if (ap && level == (int)H->L.size() - 1) return AMG_ERR_ARG;
-  const Sell& M = ap ? H->L[level].AP : H->L[level].A;
+  if (ap >= 2 && !H->opt.smooth_prolongator) return AMG_ERR_ARG;
+  const Level& L = H->L[level];
+  const Sell& M = ap == 0 ? L.A : ap == 1 ? L.AP : ap == 2 ? L.P : L.R;
   out->slice_height = M.C;
   out->threads_per_row = M.tpr;
   out->slots = M.nnz_pad;
@@ -389,6 +398,26 @@ int amg_level_export(const amg_handle* H, int level, int64_t* rowptr, int32_t* c
     AMG_CUDA_TRY(cudaMemcpyAsync(agg, L.agg, sizeof(int32_t) * L.n, cudaMemcpyDeviceToDevice, s));
   if (sscale)
     AMG_CUDA_TRY(cudaMemcpyAsync(sscale, L.s64, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, s));
+  return AMG_OK;
+}
+
+int amg_level_prolongator(const amg_handle* H, int level, int64_t* rowptr, int32_t* col,
+                          double* val, int64_t* nnz, double* w, amg_stream_t stream) {
+  if (!H || level < 0 || level + 1 >= (int)H->L.size() || !H->opt.smooth_prolongator)
+    return AMG_ERR_ARG;
+  const Level& L = H->L[level];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nnz) *nnz = L.p_nnz;
+  if (w) *w = L.wp;
+  if (rowptr)
+    AMG_CUDA_TRY(cudaMemcpyAsync(rowptr, L.p_rp, sizeof(int64_t) * (L.n + 1),
+                                 cudaMemcpyDeviceToDevice, s));
+  if (col)
+    AMG_CUDA_TRY(cudaMemcpyAsync(col, L.p_ci, sizeof(int32_t) * L.p_nnz,
+                                 cudaMemcpyDeviceToDevice, s));
+  if (val)
+    AMG_CUDA_TRY(cudaMemcpyAsync(val, L.p_v, sizeof(double) * L.p_nnz, cudaMemcpyDeviceToDevice,
+                                 s));
   return AMG_OK;
 }
 

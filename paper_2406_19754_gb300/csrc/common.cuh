@@ -141,6 +141,24 @@ struct Level {
   void* xp = nullptr;
   // batched systems: first row of each system on this level (nsys + 1, host)
   std::vector<int64_t> sys_off;
+  // smoothed prolongator (option smooth_prolongator, Sec. 2.3): P = (I - w
+  // D^-1 A) P_hat (n x nc CSR, kept for export, and sliced ELL with A's
+  // slices), its transpose R = P^T as sliced ELL (restriction), and AP above
+  // then holds A P.  The CSRs of R and A P live only until setup has made
+  // their sliced-ELL copies.
+  double wp = 0.0;
+  int64_t* p_rp = nullptr;
+  int32_t* p_ci = nullptr;
+  double* p_v = nullptr;
+  int64_t p_nnz = 0;
+  int64_t* t_rp = nullptr;
+  int32_t* t_ci = nullptr;
+  double* t_v = nullptr;
+  int64_t* q_rp = nullptr;
+  int32_t* q_ci = nullptr;
+  double* q_v = nullptr;
+  int64_t q_nnz = 0;
+  Sell P, R;
 };
 
 // Batched PCG state (pcg_solve_batch): per-system scalars and per-slice
@@ -431,6 +449,21 @@ int tail_reset(amg_handle* H, cudaStream_t s);
 // Synchronous: AMG_ERR_DEVICE_CHECK (and a reset) if a persistent launch gave
 // up waiting at a barrier since the last check, else AMG_OK.
 int tail_check(amg_handle* H, cudaStream_t s);
+
+// Sparse products for smoothed prolongators (spgemm.cu).  C = X Y with the
+// sums of every entry in ascending inner-index order (no fused multiply-
+// add); the transpose with ascending columns; P = P_hat - w D^-1 (A P_hat)
+// in place over the CSR of A P_hat (columns sorted), w = 1/||D^-1 A||_inf.
+int spgemm(Arena& ar, int64_t n, const int64_t* X_rp, const int32_t* X_ci, const double* X_v,
+           const int64_t* Y_rp, const int32_t* Y_ci, const double* Y_v, int64_t** C_rp,
+           int32_t** C_ci, double** C_v, int64_t* C_nnz, int* dev_status, int num_sms,
+           cudaStream_t s);
+int transpose_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rp, const int32_t* ci,
+                  const double* v, int64_t nnz, int64_t** T_rp, int32_t** T_ci, double** T_v,
+                  int num_sms, cudaStream_t s);
+int smoothed_prolongator(Arena& ar, int64_t n, const int64_t* A_rp, const int32_t* A_ci,
+                         const double* A_v, const int32_t* agg, const int64_t* rp, int32_t* ci,
+                         double* v, double* w_out, int num_sms, cudaStream_t s);
 
 // exec = [ctl] -> while (condition) { body; ctl }, where ctl launches the
 // kernel that sets the condition through the handle (pcg.cu).

@@ -227,7 +227,7 @@ int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, co
                                                              rowptr, col, val, out.sliceptr,
                                                              aligned, uoff, out.col, out.v64);
   AMG_LAUNCH_CHECK();
-  if (compress) AMG_TRY(sell_compress(ar, out, s));
+  if (compress && tpr <= 8) AMG_TRY(sell_compress(ar, out, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   ar.release(aligned);
   ar.release(uoff);

@@ -17,13 +17,14 @@ constexpr int SELL_BLOCK = 256;  // threads per block (8 slices in flight)
 // which the streaming kernels need to keep enough loads in flight.
 #define SELL_MIN_BLOCKS 8
 
-// Layout code of a SELL kernel instantiation: threads per row (1, 2, 4 or 8)
-// plus SELL_D16 when the matrix stores compressed columns.
-constexpr int SELL_D16 = 16;
+// Layout code of a SELL kernel instantiation: threads per row (1, 2, 4, 8,
+// or 16 and 32 for wide rows) plus SELL_D16 when the matrix stores
+// compressed columns (1..8 threads per row only).
+constexpr int SELL_D16 = 64;
 
 template <int TPR>
 struct Lanes {
-  static constexpr int W = TPR & 15;  // threads per row
+  static constexpr int W = TPR & 63;  // threads per row
   static constexpr bool D16 = (TPR & SELL_D16) != 0;
   static constexpr int C = 32 / W;
   int r, t;
@@ -81,10 +82,12 @@ __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const 
     AMG_SELL_CASE(2, __VA_ARGS__)          \
     AMG_SELL_CASE(4, __VA_ARGS__)          \
     AMG_SELL_CASE(8, __VA_ARGS__)          \
-    AMG_SELL_CASE(17, __VA_ARGS__)         \
-    AMG_SELL_CASE(18, __VA_ARGS__)         \
-    AMG_SELL_CASE(20, __VA_ARGS__)         \
-    AMG_SELL_CASE(24, __VA_ARGS__)         \
+    AMG_SELL_CASE(16, __VA_ARGS__)         \
+    AMG_SELL_CASE(32, __VA_ARGS__)         \
+    AMG_SELL_CASE(65, __VA_ARGS__)         \
+    AMG_SELL_CASE(66, __VA_ARGS__)         \
+    AMG_SELL_CASE(68, __VA_ARGS__)         \
+    AMG_SELL_CASE(72, __VA_ARGS__)         \
     default:                               \
       return AMG_ERR_ARG;                  \
   }

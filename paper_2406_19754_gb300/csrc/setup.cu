@@ -76,6 +76,41 @@ __device__ __forceinline__ bool heavier(const EdgeKey& a, const EdgeKey& b) {
   return a.hi < b.hi;
 }
 
+// The value of edge {i, j} is the entry stored in row min(i, j): matrices
+// that are symmetric in exact arithmetic need not be symmetric bit for bit
+// (smoothed coarse matrices P^T (A P) are not), and both endpoints must see
+// the same key.  aij: the entry of row i.  Rows are searched by bisection
+// (ascending columns), then by a scan; false when row j holds no column i
+// (a structurally unsymmetric pattern: the edge is then not eligible).
+__device__ __forceinline__ bool edge_value(const int64_t* __restrict__ rowptr,
+                                           const int32_t* __restrict__ col,
+                                           const double* __restrict__ val, int32_t i, int32_t j,
+                                           double aij, double* out) {
+  if (j > i) {
+    *out = aij;
+    return true;
+  }
+  const int64_t b = rowptr[j], end = rowptr[j + 1];
+  int64_t lo = b, hi = end;
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (col[mid] < i)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo < end && col[lo] == i) {
+    *out = val[lo];
+    return true;
+  }
+  for (int64_t e = b; e < end; ++e)
+    if (col[e] == i) {
+      *out = val[e];
+      return true;
+    }
+  return false;
+}
+
 // mate[i]: >= 0 matched, -1 active, -2 no eligible partner left (singleton).
 // flag[i]: 1 while i sits on the next frontier list.
 __global__ void k_match_cand(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
@@ -95,8 +130,9 @@ __global__ void k_match_cand(const int32_t* __restrict__ wl, const int* __restri
     for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
       const int32_t j = col[e];
       if (j == i || mate[j] != -1) continue;
-      const double c =
-          __dsub_rn(1.0, __ddiv_rn(__dmul_rn(2.0, val[e]), __dadd_rn(di, diag[j])));
+      double a;
+      if (!edge_value(rowptr, col, val, i, j, val[e], &a)) continue;
+      const double c = __dsub_rn(1.0, __ddiv_rn(__dmul_rn(2.0, a), __dadd_rn(di, diag[j])));
       if (!(c > 0.0)) continue;
       EdgeKey k;
       k.c = c;
@@ -836,6 +872,74 @@ static int build_ap(Arena& ar, Level& L, const int64_t* rp, const int32_t* ci, c
   return AMG_OK;
 }
 
+// Coarse matrix with the smoothed prolongator (Sec. 2.3, SMATCH): A P_hat
+// (k_ap_*: per row, each aggregate's sum in stored order), P = P_hat -
+// w D^-1 (A P_hat) in place, R = P^T, Q = A P and A_c = R Q, every sum in
+// ascending inner index.  P, R and Q stay on the level until setup has built
+// the V-cycle operators from them.
+static int smoothed_galerkin(Arena& ar, Level& L, int64_t n, const int64_t* rp,
+                             const int32_t* ci, const double* va, Level& next, int* dev_status,
+                             int num_sms, cudaStream_t s) {
+  int64_t* cnt = nullptr;
+  AMG_TRY(ar.alloc_n(&cnt, n + 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (n + 1), s));
+  const int g = grid_for(n, 256, num_sms, 8);
+  k_ap_count<<<g, 256, 0, s>>>(n, rp, ci, L.agg, cnt);
+  AMG_LAUNCH_CHECK();
+  AMG_TRY(ar.alloc_n(&L.p_rp, n + 1));
+  AMG_TRY(scan_exclusive_i64(ar, cnt, L.p_rp, n + 1, &L.p_nnz, s));
+  ar.release(cnt);
+  AMG_TRY(ar.alloc_n(&L.p_ci, L.p_nnz));
+  AMG_TRY(ar.alloc_n(&L.p_v, L.p_nnz));
+  k_ap_fill<<<g, 256, 0, s>>>(n, rp, ci, va, L.agg, L.p_rp, L.p_ci, L.p_v);
+  AMG_LAUNCH_CHECK();
+  AMG_TRY(smoothed_prolongator(ar, n, rp, ci, va, L.agg, L.p_rp, L.p_ci, L.p_v, &L.wp, num_sms,
+                               s));
+  AMG_TRY(transpose_csr(ar, n, L.nc, L.p_rp, L.p_ci, L.p_v, L.p_nnz, &L.t_rp, &L.t_ci, &L.t_v,
+                        num_sms, s));
+  AMG_TRY(spgemm(ar, n, rp, ci, va, L.p_rp, L.p_ci, L.p_v, &L.q_rp, &L.q_ci, &L.q_v, &L.q_nnz,
+                 dev_status, num_sms, s));
+  AMG_TRY(spgemm(ar, L.nc, L.t_rp, L.t_ci, L.t_v, L.q_rp, L.q_ci, L.q_v, &next.rowptr, &next.col,
+                 &next.val, &next.nnz, dev_status, num_sms, s));
+  return AMG_OK;
+}
+
+// Threads per row when the options fix none: one (32 rows a slice) for
+// ordinary rows; rows of 64 entries or more (coarse levels of smoothed
+// hierarchies reach hundreds) get about one thread per 16 entries, a power of
+// two from 4 up to a whole warp.
+static int auto_tpr(int64_t rows, int64_t nnz) {
+  const double m = (double)nnz / (double)std::max<int64_t>(rows, 1);
+  if (m < 64.0) return 1;
+  int t = 4;
+  while (t < 32 && 16.0 * t < m) t <<= 1;
+  return t;
+}
+
+// Sliced-ELL copies of A P, P (both with A's slices and plain column
+// indices, so one kernel walks both with the same layout code) and R = P^T
+// of a smoothed level; R's rows (the fine rows around an aggregate) are
+// long, so it gets its own threads per row (at least 4 once they average 16
+// entries).
+static int build_smoothed_ops(Arena& ar, Level& L, bool compress, cudaStream_t s) {
+  L.ap_nnz = L.q_nnz;
+  AMG_TRY(sell_from_csr(ar, L.n, L.nc, L.q_rp, L.q_ci, L.q_v, L.A.C, L.A.tpr, L.AP, s, nullptr,
+                        false));
+  AMG_TRY(sell_from_csr(ar, L.n, L.nc, L.p_rp, L.p_ci, L.p_v, L.A.C, L.A.tpr, L.P, s, nullptr,
+                        false));
+  const int rt = std::max(auto_tpr(L.nc, L.p_nnz), L.p_nnz >= 16 * L.nc ? 4 : 1);
+  AMG_TRY(sell_from_csr(ar, L.nc, L.n, L.t_rp, L.t_ci, L.t_v, 32 / rt, rt, L.R, s, nullptr,
+                        compress));
+  AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  for (void* p : {(void*)L.t_rp, (void*)L.t_ci, (void*)L.t_v, (void*)L.q_rp, (void*)L.q_ci,
+                  (void*)L.q_v})
+    ar.release(p);
+  L.t_rp = L.q_rp = nullptr;
+  L.t_ci = L.q_ci = nullptr;
+  L.t_v = L.q_v = nullptr;
+  return AMG_OK;
+}
+
 // ------------------------------------------------------------------ autotuner
 // Threads per row (and so slice height 32/tpr) per level, chosen by timing the
 // level's smoother kernels in every layout; choices are remembered for the
@@ -882,6 +986,8 @@ static void release_sell(Arena& ar, Sell& A) {
 static void release_level_ops(Arena& ar, Level& L) {
   release_sell(ar, L.A);
   release_sell(ar, L.AP);
+  release_sell(ar, L.P);
+  release_sell(ar, L.R);
   ar.release(L.ah64);
   ar.release(L.ah32);
   ar.release(L.ah16);
@@ -960,8 +1066,11 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
                                    cudaMemcpyDeviceToDevice, s));
       Level next;
       next.n = L.nc;
-      AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, L.stride, L.nc, &next.rowptr,
-                       &next.col, &next.val, &next.nnz, H->dev_status, sms, s));
+      if (o.smooth_prolongator)
+        AMG_TRY(smoothed_galerkin(ar, L, n, rp, ci, va, next, H->dev_status, sms, s));
+      else
+        AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, L.stride, L.nc, &next.rowptr,
+                         &next.col, &next.val, &next.nnz, H->dev_status, sms, s));
       const int st = read_status(H, s);
       if (st < 0) return st;
       H->L.push_back(next);
@@ -1058,8 +1167,11 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
         next.sys_off[k] = a;
       }
     }
-    AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, stride, nc, &next.rowptr, &next.col,
-                     &next.val, &next.nnz, H->dev_status, sms, s));
+    if (o.smooth_prolongator)
+      AMG_TRY(smoothed_galerkin(ar, L, n, rp, ci, va, next, H->dev_status, sms, s));
+    else
+      AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, stride, nc, &next.rowptr, &next.col,
+                       &next.val, &next.nnz, H->dev_status, sms, s));
     st = read_status(H, s);
     if (st < 0) return st;
     H->L.push_back(next);
@@ -1153,11 +1265,14 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
                             H->batched ? &L.sys_off : nullptr, cmp));
       if (smooth) {
         AMG_TRY(build_ah(ar, L, sms, s));
-        AMG_TRY(build_ap(ar, L, rp, ci, va, cmp, sms, s));
+        if (o.smooth_prolongator)
+          AMG_TRY(build_smoothed_ops(ar, L, cmp, s));
+        else
+          AMG_TRY(build_ap(ar, L, rp, ci, va, cmp, sms, s));
       }
       return AMG_OK;
     };
-    int tpr = o.threads_per_row > 0 ? o.threads_per_row : 1;
+    int tpr = o.threads_per_row > 0 ? o.threads_per_row : auto_tpr(L.n, L.nnz);
     if (o.slice_height > 0) tpr = 32 / o.slice_height;
     if (like) {  // the assembled hierarchy's layout, tuned or not
       tpr = like->L[l].A.tpr;
@@ -1166,7 +1281,9 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
                         o.compress_columns != 0};
       if (!tune_lookup(key, &tpr)) {
         float best = 1e30f;
-        for (int cand : {1, 2, 4, 8}) {
+        const int ncand = L.nnz >= 64 * L.n ? 6 : 4;  // 16 and 32 for wide rows
+        for (int k = 0; k < ncand; ++k) {
+          const int cand = 1 << k;
           AMG_TRY(build(cand));
           float ms = 0.f;
           AMG_TRY(time_level(H, (int)l, 3, tb, tz, &ms, s));

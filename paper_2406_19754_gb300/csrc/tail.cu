@@ -168,10 +168,12 @@ __device__ void tail_report(const TailParams& P) {
     AMG_SELL_CASE(2, __VA_ARGS__)   \
     AMG_SELL_CASE(4, __VA_ARGS__)   \
     AMG_SELL_CASE(8, __VA_ARGS__)   \
-    AMG_SELL_CASE(17, __VA_ARGS__)  \
-    AMG_SELL_CASE(18, __VA_ARGS__)  \
-    AMG_SELL_CASE(20, __VA_ARGS__)  \
-    AMG_SELL_CASE(24, __VA_ARGS__)  \
+    AMG_SELL_CASE(16, __VA_ARGS__)  \
+    AMG_SELL_CASE(32, __VA_ARGS__)  \
+    AMG_SELL_CASE(65, __VA_ARGS__)  \
+    AMG_SELL_CASE(66, __VA_ARGS__)  \
+    AMG_SELL_CASE(68, __VA_ARGS__)  \
+    AMG_SELL_CASE(72, __VA_ARGS__)  \
     default:                        \
       break;                        \
   }
@@ -419,6 +421,7 @@ int tail_init(amg_handle* H, cudaStream_t s) {
 int tail_start(const amg_handle* H) {
   const int nl = (int)H->L.size();
   if (H->opt.tail_rows <= 0 || H->tail_grid <= 0 || nl < 3) return -1;
+  if (H->opt.smooth_prolongator) return -1;  // the tail restricts and prolongs by aggregates
   int lt = 1;
   while (lt < nl - 1 && H->L[lt].n > H->opt.tail_rows) ++lt;
   lt = std::max(lt, nl - 1 - TAIL_MAX_LEVELS);

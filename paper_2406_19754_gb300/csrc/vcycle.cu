@@ -105,6 +105,33 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     if (!slice_part) grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
 }
 
+// Post-smoother of a level with a smoothed prolongator P (Sec. 2.3; A P in
+// AQ, P with the same slices): z = y + S (r - (A P) x_c), y = x_pre + P x_c,
+// x_pre the pre-smoothed x (xp, or S b after one sweep); e, if set, receives
+// r - (A P) x_c for further sweeps.  FP64 only.
+template <int TPR>
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
+    k_post_sm(SellView<double> AQ, SellView<double> P, const double* __restrict__ b,
+              const double* __restrict__ s, const double* __restrict__ r,
+              const double* __restrict__ xc, const double* __restrict__ xp,
+              double* __restrict__ x, double* __restrict__ e) {
+  const Lanes<TPR> ln;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AQ.nslices;
+       sl += nw) {
+    const double aq = sell_row<TPR, double>(AQ, sl, ln, [&](int J) { return __ldg(xc + J); });
+    const double px = sell_row<TPR, double>(P, sl, ln, [&](int J) { return __ldg(xc + J); });
+    const int64_t i = lane_row(AQ, sl, ln);
+    if (i >= 0) {
+      const double si = s[i];
+      const double yi = (xp ? xp[i] : si * b[i]) + px;
+      const double ei = r[i] - aq;
+      x[i] = fma(si, ei, yi);
+      if (e) e[i] = ei;
+    }
+  }
+}
+
 // Pre-smoothing sweeps 2..nu on the residual recurrence: x += S r (x = S b
 // before the first of them), r_out = r - (A S) r.
 template <int TPR, typename V, typename T, typename BT>
@@ -364,6 +391,10 @@ static int launch_sweep(const amg_handle* H, const Level& L, const BT* b, const 
 template <typename T>
 static int launch_restrict(const amg_handle* H, const Level& L, const T* r, T* bc,
                            cudaStream_t s) {
+  if constexpr (sizeof(T) == 8) {
+    if (H->opt.smooth_prolongator)  // b_c = R r, R = P^T
+      return sell_spmv64(L.R, 1.0, r, 0.0, bc, H->num_sms, s);
+  }
   k_restrict<T><<<grid_for(L.nc, 256, H->num_sms, 8), 256, 0, s>>>(L.nc, L.stride, L.members, r,
                                                                    bc);
   AMG_LAUNCH_CHECK();
@@ -378,10 +409,28 @@ static int pre_f32(const amg_handle* H, const Level& L, const BT* b, float* r, c
   return launch_pre<float, float, BT>(H, L, L.ah32, b, r, s, act);
 }
 
+// Post-smoother of a smoothed-prolongator level (k_post_sm; no dot products).
+static int launch_post_sm(const amg_handle* H, const Level& L, const double* b, const double* xc,
+                          double* x, cudaStream_t s, const PostIn<double>& in) {
+  const int grid = sell_grid(L.AP.nslices, H->num_sms);
+  const SellView<double> q = view<double>(L.AP, L.AP.v64);
+  const SellView<double> p = view<double>(L.P, L.P.v64);
+  const double* r = in.r ? in.r : (const double*)L.r;
+  if (sell_code(L.AP) != sell_code(L.P)) return AMG_ERR_UNSUPPORTED;
+  AMG_DISPATCH_TPR(sell_code(L.AP), (k_post_sm<TPR><<<grid, SELL_BLOCK, 0, s>>>(
+                                        q, p, b, L.s64, r, xc, in.xp, x, in.e)));
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
 template <typename T, typename BT, typename XT, int NDOT>
 static int post_any(const amg_handle* H, const Level& L, const BT* b, const T* xc, XT* x,
                     const double* q, cudaStream_t s, double* slice_part = nullptr,
                     const int* act = nullptr, const PostIn<T>& in = PostIn<T>()) {
+  if constexpr (sizeof(T) == 8 && sizeof(BT) == 8 && sizeof(XT) == 8 && NDOT == 0) {
+    if (H->opt.smooth_prolongator)
+      return launch_post_sm(H, L, (const double*)b, (const double*)xc, (double*)x, s, in);
+  }
   if constexpr (sizeof(T) == 8) {
     return launch_post<double, T, BT, XT, NDOT>(H, L, L.AP.v64, b, xc, x, q, s, slice_part,
                                                  act, in);
@@ -442,10 +491,17 @@ struct Prof {
 static double bytes_pre(const Level& L, double mb, double vb, double ib) {
   return (double)L.nnz * mb + (double)L.n * (ib + vb);  // Ah, b, r
 }
+// With a smoothed prolongator the restriction streams R = P^T (12 bytes an
+// entry) instead of the member lists, and the post-smoother streams P in
+// place of the aggregate map.
 static double bytes_restrict(const Level& L, double vb) {
+  if (L.R.nslices) return (double)L.p_nnz * 12.0 + (double)L.n * vb + (double)L.nc * vb;
   return (double)L.n * (vb + 4.0) + (double)L.nc * vb;  // r, members, b_c
 }
 static double bytes_post(const Level& L, double mb, double vb, double ib, double ob) {
+  if (L.P.nslices)  // A P, P, b, s, r, z, x_c
+    return (double)(L.ap_nnz + L.p_nnz) * mb + (double)L.n * (ib + vb + vb + ob) +
+           (double)L.nc * vb;
   // AP, b, s, r, agg, z, x_c
   return (double)L.ap_nnz * mb + (double)L.n * (ib + vb + vb + 4.0 + ob) + (double)L.nc * vb;
 }
@@ -600,7 +656,8 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
   const T* xc = (const T*)H->L[1].x;
   // one sweep: the dot products are fused into the post-smoother; several:
   // they follow the last sweep
-  const int fused = L0.nu > 1 ? 0 : dots;
+  const bool smoothed = H->opt.smooth_prolongator != 0;
+  const int fused = L0.nu > 1 || smoothed ? 0 : dots;
   PROF_BEGIN(0, 2, bytes_post(L0, pbytes(L0), vb, 8.0, 8.0) + (fused > 1 ? 8.0 * L0.n : 0.0));
   const PostIn<T> in0 = post_in(L0, 0);
   int rc;
@@ -612,10 +669,8 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
     rc = post_any<T, double, double, 2>(H, L0, r0, xc, z0, q, s, slice_part, act, in0);
   AMG_TRY(rc);
   PROF_END();
-  if (L0.nu > 1) {
-    AMG_TRY(post_sweeps(L0, 0, z0));
-    AMG_TRY(separate_dots());
-  }
+  if (L0.nu > 1) AMG_TRY(post_sweeps(L0, 0, z0));
+  if (L0.nu > 1 || smoothed) AMG_TRY(separate_dots());
   return AMG_OK;
 }
 

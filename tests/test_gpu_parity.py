@@ -67,7 +67,7 @@ def test_hierarchy_bit_exact(amg, orc, case, sweeps):
             assert np.array_equal(_np(ex["agg"]), Ho.level_agg(l))
 
 
-@pytest.mark.parametrize("tpr", [1, 2, 4, 8])
+@pytest.mark.parametrize("tpr", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("case", CASES[:3], ids=lambda c: c[0])
 def test_spmv_every_level(amg, orc, case, tpr):
     _, A = case
@@ -85,7 +85,7 @@ def test_spmv_every_level(amg, orc, case, tpr):
         assert np.max(np.abs(got - want)) <= 1e-13 * scale
 
 
-@pytest.mark.parametrize("tpr", [1, 4])
+@pytest.mark.parametrize("tpr", [1, 4, 32])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
 def test_vcycle_fp64_matches_oracle(amg, orc, case, tpr):
     _, A = case

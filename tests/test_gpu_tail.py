@@ -32,6 +32,8 @@ LARGE = (64, 64, 64)   # level 1 has 65536 rows: a tail from it spans the grid
     (SMALL, dict(precision="f32", bf16_from_level=2)),
     (SMALL, dict(precision="f64", threads_per_row=2)),
     (SMALL, dict(precision="f32", threads_per_row=4, slice_height=8)),
+    (SMALL, dict(precision="f64", threads_per_row=16)),
+    (SMALL, dict(precision="f32", threads_per_row=32, tail_rows=16384)),
     (SMALL, dict(precision="f64", tail_rows=16384)),
     (LARGE, dict(precision="f64", tail_rows=70000)),
     (LARGE, dict(precision="f32", tail_rows=70000, threads_per_row=2)),

@@ -93,3 +93,16 @@ def test_smoothed_reuse_recomputes_the_prolongator(orc):
     b = uniform01(5, 9 * 8 * 7)
     if all(np.array_equal(F.level_agg(l), H.level_agg(l)) for l in range(F.levels - 1)):
         assert np.array_equal(F.vcycle(b), R.vcycle(b))
+
+
+def test_matching_takes_each_edge_from_its_upper_row(orc):
+    """Smoothed coarse matrices are symmetric only up to rounding; the matching
+    reads edge {i, j} from row min(i, j), so replacing every value below the
+    diagonal changes nothing, while changing the values above it does."""
+    rp, ci, v = poisson3d(12)
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    u = uniform01(12, len(v))
+    lower = (rp, ci, np.where(ci < rows, v * (1.0 + 1e-3 * u), v))
+    upper = (rp, ci, np.where(ci > rows, v * (1.0 + 1e-3 * u), v))
+    assert np.array_equal(orc.match(lower), orc.match((rp, ci, v)))
+    assert not np.array_equal(orc.match(upper), orc.match((rp, ci, v)))

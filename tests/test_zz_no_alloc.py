@@ -33,6 +33,10 @@ def test_noalloc_matches_allocating_entry_point_twice(amg):
     cases = [poisson3d(48, 40, 36),  # 69,120 rows
              diffusion3d(np.exp(gaussian_field((30, 30, 30), 2.0, 4.0, 11))),
              random_spd_graph(500, 0.02, 4, positive_offdiag=True)]
+    # values that differ across the diagonal: each edge's value from its upper row
+    rp, ci, v = poisson3d(20)
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    cases.append((rp, ci, np.where(ci < rows, v * (1.0 + 1e-3 * np.sin(np.arange(len(v)))), v)))
     for A in cases:
         Ad = amg.csr_to_device(A)
         rc0, want, r0 = _match(lib, "amg_pairwise_match", Ad)
