@@ -57,6 +57,11 @@ def _declare(L):
     L.orc_setup_smoothed.restype = _P
     L.orc_setup_smoothed.argtypes = [_I64, _P, _P, _P, C.c_int, _I64, C.c_int, C.c_double, _I64,
                                      _P]
+    L.orc_setup_general.restype = _P
+    L.orc_setup_general.argtypes = [_I64, _P, _P, _P, C.c_int, _I64, C.c_int, C.c_double, _I64,
+                                    C.c_int, C.c_int, C.c_double, _P]
+    L.orc_vbm_aggregate.restype = _I64
+    L.orc_vbm_aggregate.argtypes = [_I64, _P, _P, _P, C.c_double, _P]
     L.orc_level_prolongator.restype = _I64
     L.orc_level_prolongator.argtypes = [_P, C.c_int, _P, _P, _P, _P]
     L.orc_setup_reuse.restype = _P
@@ -204,6 +209,14 @@ def match(A, w=None):
     return mate
 
 
+def vbm_aggregate(A, theta=0.01):
+    """Decoupled Vanek-Mandel-Brezina aggregates of A: (agg, nc)."""
+    n, rp, ci, v = csr_args(A)
+    agg = np.empty(n, dtype=np.int32)
+    nc = lib().orc_vbm_aggregate(n, _p(rp), _p(ci), _p(v), theta, _p(agg))
+    return agg, int(nc)
+
+
 def number_pairs(mate):
     mate = _i32(mate)
     agg = np.empty(len(mate), dtype=np.int32)
@@ -244,20 +257,25 @@ class Hierarchy:
 
     def __init__(self, A, sweeps=2, max_coarse=200, max_levels=30, stall=0.9,
                  max_dense=8192, omega=None, systems=None, smooth_sweeps=1, variable=False,
-                 coarse="cholesky", coarse_maxit=40, coarse_tol=1e-4, smoothed=False):
+                 coarse="cholesky", coarse_maxit=40, coarse_tol=1e-4, smoothed=False,
+                 aggregation="matching", theta=0.01):
         """systems: row offsets (nsys + 1) of independent systems stacked block
         diagonally in A; coarsening then stops when each has <= max_coarse rows.
         smooth_sweeps: l1-Jacobi sweeps nu_0 before and after the coarse
         correction; variable: nu_l = nu_0 * 2^l (variable V-cycle, Sec. 3);
         coarse: "cholesky" (dense) or "pcg" (PCG with l1-Jacobi, at most
-        coarse_maxit iterations, stop at ||r|| <= coarse_tol ||b||)."""
+        coarse_maxit iterations, stop at ||r|| <= coarse_tol ||b||).
+        aggregation: "matching" (`sweeps` matching sweeps) or "vbm" (decoupled
+        Vanek-Mandel-Brezina with strength threshold theta)."""
         n, rp, ci, v = csr_args(A)
         self._keep = (rp, ci, v)
         st = C.c_int(0)
-        if smoothed:
+        agg = {"matching": 0, "vbm": 1}[aggregation]
+        if smoothed or agg:
             assert systems is None and omega is None
-            self.h = lib().orc_setup_smoothed(n, _p(rp), _p(ci), _p(v), sweeps, max_coarse,
-                                              max_levels, stall, max_dense, C.byref(st))
+            self.h = lib().orc_setup_general(n, _p(rp), _p(ci), _p(v), sweeps, max_coarse,
+                                             max_levels, stall, max_dense, 1 if smoothed else 0,
+                                             agg, theta, C.byref(st))
         elif systems is not None:
             so = _i64(systems)
             self.h = lib().orc_setup_systems(n, _p(rp), _p(ci), _p(v), len(so) - 1, _p(so),

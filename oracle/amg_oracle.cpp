@@ -50,6 +50,20 @@
 //    each output entry sums its contributions in ascending order of the
 //    inner index, each as one product and one addition (no fused multiply-
 //    add).  The V-cycle restricts with P^T and prolongs with P.
+//  * Decoupled Vanek-Mandel-Brezina aggregation (Sec. 2.3, VBM), on one
+//    process, so "decoupled" changes nothing.  Strong neighbourhood
+//    N_i = {i} + {j != i : |a_ij| >= theta * sqrt(a_ii * a_jj)}, the value of
+//    edge {i, j} read from row min(i, j) (as for the matching weights; an edge
+//    missing from that row is not strong).  Phase 1: rows in ascending order;
+//    a row whose whole N_i is unaggregated starts the aggregate N_i.
+//    Phase 2 ("remaining nodes are added to the nearest aggregates"): every
+//    row left joins the phase-1 aggregate of its strong neighbour with the
+//    largest |a_ij| (the smaller j on ties).  Phase 3: rows still left, in
+//    ascending order, start an aggregate with their unaggregated strong
+//    neighbours (empty when the pattern is symmetric: a row outside every
+//    phase-1 aggregate shares a strong neighbour with one).  Aggregates are
+//    numbered as they are created; P_hat has w = 1 (the constant near-kernel
+//    vector).  The paper leaves theta to the user; the default is 0.01.
 //  * Iterative coarsest solve (VBM, Sec. 3): PCG with the coarsest level's
 //    l1-Jacobi scaling as preconditioner, zero initial guess, at most maxit
 //    iterations; it stops once ||r|| <= tol * ||b|| (the paper gives only the
@@ -78,7 +92,8 @@ struct Level {
   Csr A;
   std::vector<double> dinv;      // smoother scale s_i
   std::vector<int32_t> agg;      // row -> aggregate on the next level
-  std::vector<int32_t> members;  // stride (1 << sweeps), ascending, -1 padded
+  std::vector<int32_t> members;  // nc x stride, ascending, -1 padded
+  int stride = 0;  // 1 << sweeps (matching), or >= the largest aggregate (VBM)
   int64_t nc = 0;
   // smoothed prolongator (empty when P is the 0/1 aggregate map) and P^T
   Csr P, Pt;
@@ -88,6 +103,8 @@ struct Level {
 struct Hierarchy {
   int sweeps = 2;
   int smooth_p = 0;  // 1: smoothed prolongators (Sec. 2.3)
+  int aggregation = 0;  // 0: matching sweeps; 1: VBM with strength theta
+  double theta = 0.01;
   std::vector<Level> lev;
   std::vector<double> chol;  // dense lower factor of the coarsest matrix, row-major
   int64_t nco = 0;
@@ -183,6 +200,89 @@ void match_greedy(const Csr& A, const double* w, std::vector<int32_t>& mate) {
       mate[ed.hi] = ed.lo;
     }
   }
+}
+
+// ---------------------------------------------------------------- VBM
+
+// Value of edge {i, j} (i != j): the entry of row min(i, j); false if absent.
+bool edge_value(const Csr& A, int64_t i, int64_t j, double aij_row_i, double* out) {
+  if (j > i) {
+    *out = aij_row_i;
+    return true;
+  }
+  for (int64_t e = A.rowptr[j]; e < A.rowptr[j + 1]; ++e)
+    if (A.col[e] == i) {
+      *out = A.val[e];
+      return true;
+    }
+  return false;
+}
+
+// Decoupled VBM aggregation (see the header); returns the aggregate count.
+int64_t vbm_aggregate(const Csr& A, double theta, std::vector<int32_t>& agg) {
+  const int64_t n = A.n;
+  std::vector<double> d(n);
+  for (int64_t i = 0; i < n; ++i) d[i] = diag_of(A, i);
+  // strong[e]: entry e of row i is a strong neighbour j != i
+  std::vector<char> strong(A.col.size(), 0);
+  std::vector<double> mag(A.col.size(), 0.0);  // |edge value|
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      const int64_t j = A.col[e];
+      double a;
+      if (j == i || !edge_value(A, i, j, A.val[e], &a)) continue;
+      mag[e] = std::fabs(a);
+      strong[e] = mag[e] >= theta * std::sqrt(d[i] * d[j]);
+    }
+  agg.assign(n, -1);
+  int64_t nc = 0;
+  // phase 1
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    bool free = true;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1] && free; ++e)
+      if (strong[e] && agg[A.col[e]] >= 0) free = false;
+    if (!free) continue;
+    agg[i] = (int32_t)nc;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e)
+      if (strong[e]) agg[A.col[e]] = (int32_t)nc;
+    ++nc;
+  }
+  // phase 2: against the phase-1 aggregates only
+  const std::vector<int32_t> agg1 = agg;
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg1[i] >= 0) continue;
+    int64_t best = -1;
+    double bm = 0.0;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      const int64_t j = A.col[e];
+      if (!strong[e] || agg1[j] < 0) continue;
+      if (best < 0 || mag[e] > bm || (mag[e] == bm && j < best)) {
+        best = j;
+        bm = mag[e];
+      }
+    }
+    if (best >= 0) agg[i] = agg1[best];
+  }
+  // phase 3
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    agg[i] = (int32_t)nc;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e)
+      if (strong[e] && agg[A.col[e]] < 0) agg[A.col[e]] = (int32_t)nc;
+    ++nc;
+  }
+  return nc;
+}
+
+// Smallest power of two >= the largest aggregate.
+int member_stride(const std::vector<int32_t>& agg, int64_t nc) {
+  std::vector<int> cnt(nc, 0);
+  int m = 1;
+  for (int32_t a : agg) m = std::max(m, ++cnt[a]);
+  int s = 1;
+  while (s < m) s <<= 1;
+  return s;
 }
 
 // Aggregates numbered in the order of their smallest member.
@@ -472,11 +572,12 @@ int64_t largest_block(const std::vector<int64_t>& sys, int64_t n) {
 int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
           double stall, int64_t max_dense, const double* omega,
           std::vector<int64_t> sys = std::vector<int64_t>(), const Hierarchy* like = nullptr,
-          int smooth_p = 0) {
+          int smooth_p = 0, int aggregation = 0, double theta = 0.01) {
   H.sweeps = sweeps;
   H.smooth_p = like ? like->smooth_p : smooth_p;
+  H.aggregation = like ? like->aggregation : aggregation;
+  H.theta = like ? like->theta : theta;
   H.lev.clear();
-  const int stride = 1 << sweeps;
   H.lev.emplace_back();
   H.lev[0].A = std::move(A0);
   for (int l = 0;; ++l) {
@@ -488,8 +589,9 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
       L.agg = like->lev[l].agg;
       L.nc = like->lev[l].nc;
       L.members = like->lev[l].members;
+      L.stride = like->lev[l].stride;
       Level next;
-      coarse_matrix(H, L, stride, next.A);
+      coarse_matrix(H, L, L.stride, next.A);
       H.lev.push_back(std::move(next));
       continue;
     }
@@ -498,7 +600,8 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
     for (int64_t i = 0; i < n; ++i) comp[i] = (int32_t)i;
     int64_t nc = n;
     Csr Acur = L.A;  // sweep 1 matches A_l itself
-    for (int s = 0; s < sweeps; ++s) {
+    if (H.aggregation == 1) nc = vbm_aggregate(L.A, H.theta, comp);
+    for (int s = 0; s < sweeps && H.aggregation == 0; ++s) {
       std::vector<int32_t> mate, ags;
       match_greedy(Acur, nullptr, mate);
       nc = number_pairs(mate, ags);
@@ -513,9 +616,10 @@ int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
     if ((double)nc > stall * (double)n) break;
     L.agg = comp;
     L.nc = nc;
-    members_of(comp, nc, stride, L.members);
+    L.stride = H.aggregation == 1 ? member_stride(comp, nc) : 1 << sweeps;
+    members_of(comp, nc, L.stride, L.members);
     Level next;
-    coarse_matrix(H, L, stride, next.A);
+    coarse_matrix(H, L, L.stride, next.A);
     H.lev.push_back(std::move(next));
     if (sys.size() >= 2) {  // aggregates never span systems
       std::vector<int64_t> nxt(sys.size());
@@ -589,7 +693,7 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
   for (int64_t k = 1; k < nu; ++k) jacobi_sweep(L, b, x, r.data());
   spmv(L.A, x, r.data());
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];  // residual
-  const int stride = 1 << H.sweeps;
+  const int stride = L.stride;
   if (H.smooth_p) {
     spmv(L.Pt, r.data(), bc.data());  // restriction b_c = P^T r
   } else {
@@ -795,6 +899,27 @@ void* orc_setup_smoothed(int64_t n, const int64_t* rp, const int32_t* ci, const 
   *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
                   nullptr, std::vector<int64_t>(), nullptr, 1);
   return H;
+}
+
+// orc_setup with every hierarchy option: smoothed prolongators (smooth_p)
+// and the aggregation (0 matching sweeps, 1 VBM with strength theta).
+void* orc_setup_general(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                        int sweeps, int64_t max_coarse, int max_levels, double stall,
+                        int64_t max_dense, int smooth_p, int aggregation, double theta,
+                        int* status) {
+  Hierarchy* H = new Hierarchy();
+  *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
+                  nullptr, std::vector<int64_t>(), nullptr, smooth_p, aggregation, theta);
+  return H;
+}
+
+// VBM aggregates of one matrix; returns their count.
+int64_t orc_vbm_aggregate(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                          double theta, int32_t* agg) {
+  std::vector<int32_t> a;
+  const int64_t nc = vbm_aggregate(csr_copy(n, rp, ci, v), theta, a);
+  std::memcpy(agg, a.data(), sizeof(int32_t) * n);
+  return nc;
 }
 
 // P (n x n_c, smoothed) of level l and its damping w; rp/ci/v null to get nnz.
