@@ -121,6 +121,14 @@ typedef struct amg_options {
                             several right-hand sides or the two-grid solver;
                             tail_rows is ignored.  0 (default): P_hat, the 0/1
                             aggregate map */
+  int aggregation;       /* 0 (default): `sweeps` pairwise matching sweeps
+                            (Sec. 2.3, coupled aggregation by compatible
+                            weighted matching); 1: decoupled Vanek-Mandel-Brezina
+                            aggregation (Sec. 2.3, VBM) with strength threshold
+                            vbm_theta (`sweeps` is then unused) */
+  double vbm_theta;      /* VBM strength threshold theta in [0, 1): j is a strong
+                            neighbour of i when |a_ij| >= theta sqrt(a_ii a_jj);
+                            default 0.01 */
 } amg_options;
 
 /* PCG controls (Sec. 3, psb_krylov arguments). */

@@ -62,6 +62,9 @@ def options(**kw) -> AmgOptions:
     prec = kw.pop("precision", None)
     if prec is not None:
         o.precision = {"f64": AMG_PREC_F64, "f32": AMG_PREC_F32}.get(prec, prec)
+    agg = kw.pop("aggregation", None)
+    if agg is not None:
+        o.aggregation = {"matching": 0, "vbm": 1}.get(agg, agg)
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError("unknown option %r" % k)

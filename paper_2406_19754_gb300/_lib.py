@@ -40,7 +40,9 @@ class AmgOptions(C.Structure):
                 ("variable_cycle", C.c_int), ("coarse_solver", C.c_int),
                 ("coarse_maxit", C.c_int), ("coarse_tol", C.c_double),
                 ("compress_columns", C.c_int),
-                ("smooth_prolongator", C.c_int)]
+                ("smooth_prolongator", C.c_int),
+                ("aggregation", C.c_int),
+                ("vbm_theta", C.c_double)]
 
 
 class PcgOptions(C.Structure):

@@ -31,6 +31,8 @@ int amg_default_options(amg_options* o) {
   o->coarse_tol = 1e-4;
   o->compress_columns = 0;
   o->smooth_prolongator = 0;
+  o->aggregation = 0;
+  o->vbm_theta = 0.01;
   return AMG_OK;
 }
 
@@ -69,6 +71,8 @@ static int check_options(const amg_options& o) {
   if (o.bf16_from_level < 0 || o.tail_rows < 0) return AMG_ERR_ARG;
   if (o.compress_columns != 0 && o.compress_columns != 1) return AMG_ERR_ARG;
   if (o.smooth_prolongator != 0 && o.smooth_prolongator != 1) return AMG_ERR_ARG;
+  if (o.aggregation != 0 && o.aggregation != 1) return AMG_ERR_ARG;
+  if (!(o.vbm_theta >= 0.0 && o.vbm_theta < 1.0)) return AMG_ERR_ARG;
   if (o.smooth_sweeps < 1 || o.smooth_sweeps > 8) return AMG_ERR_ARG;
   if (o.variable_cycle != 0 && o.variable_cycle != 1) return AMG_ERR_ARG;
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return AMG_ERR_ARG;

@@ -400,8 +400,50 @@ int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, doubl
                 int num_sms, cudaStream_t s);
 
 // Matching kernels (setup.cu), also launched by the allocation-free variant
+// Matching and VBM aggregation: the value of edge {i, j} is the entry stored
+// in row min(i, j).  Matrices that are symmetric in exact arithmetic need not
+// be symmetric bit for bit (smoothed coarse matrices P^T (A P) are not), and
+// both endpoints must see the same value.  aij: the entry of row i.  Rows are searched by bisection
+// (ascending columns), then by a scan; false when row j holds no column i
+// (a structurally unsymmetric pattern: the edge is then not eligible).
+__device__ __forceinline__ bool edge_value(const int64_t* __restrict__ rowptr,
+                                           const int32_t* __restrict__ col,
+                                           const double* __restrict__ val, int32_t i, int32_t j,
+                                           double aij, double* out) {
+  if (j > i) {
+    *out = aij;
+    return true;
+  }
+  const int64_t b = rowptr[j], end = rowptr[j + 1];
+  int64_t lo = b, hi = end;
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (col[mid] < i)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo < end && col[lo] == i) {
+    *out = val[lo];
+    return true;
+  }
+  for (int64_t e = b; e < end; ++e)
+    if (col[e] == i) {
+      *out = val[e];
+      return true;
+    }
+  return false;
+}
+
 __global__ void k_l1_diag(int64_t n, const int64_t* rowptr, const int32_t* col,
                           const double* val, double* d, double* diag);
+// Decoupled Vanek-Mandel-Brezina aggregation (vbm.cu): agg (n, device) gets
+// the aggregate of every row, *nc their count, *stride the smallest power of
+// two >= the largest aggregate.  diag: a_ii.  AMG_ERR_UNSUPPORTED when rows
+// are left for the third phase (structurally unsymmetric patterns).
+int vbm_aggregate(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+                  const double* val, const double* diag, double theta, int32_t* agg, int64_t* nc,
+                  int* stride, int num_sms, cudaStream_t s);
 __global__ void k_iota(int64_t n, int32_t* a);
 __global__ void k_match_cand(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
                              const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,

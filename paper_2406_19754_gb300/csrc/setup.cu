@@ -76,41 +76,6 @@ __device__ __forceinline__ bool heavier(const EdgeKey& a, const EdgeKey& b) {
   return a.hi < b.hi;
 }
 
-// The value of edge {i, j} is the entry stored in row min(i, j): matrices
-// that are symmetric in exact arithmetic need not be symmetric bit for bit
-// (smoothed coarse matrices P^T (A P) are not), and both endpoints must see
-// the same key.  aij: the entry of row i.  Rows are searched by bisection
-// (ascending columns), then by a scan; false when row j holds no column i
-// (a structurally unsymmetric pattern: the edge is then not eligible).
-__device__ __forceinline__ bool edge_value(const int64_t* __restrict__ rowptr,
-                                           const int32_t* __restrict__ col,
-                                           const double* __restrict__ val, int32_t i, int32_t j,
-                                           double aij, double* out) {
-  if (j > i) {
-    *out = aij;
-    return true;
-  }
-  const int64_t b = rowptr[j], end = rowptr[j + 1];
-  int64_t lo = b, hi = end;
-  while (lo < hi) {
-    const int64_t mid = lo + ((hi - lo) >> 1);
-    if (col[mid] < i)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  if (lo < end && col[lo] == i) {
-    *out = val[lo];
-    return true;
-  }
-  for (int64_t e = b; e < end; ++e)
-    if (col[e] == i) {
-      *out = val[e];
-      return true;
-    }
-  return false;
-}
-
 // mate[i]: >= 0 matched, -1 active, -2 no eligible partner left (singleton).
 // flag[i]: 1 while i sits on the next frontier list.
 __global__ void k_match_cand(const int32_t* __restrict__ wl, const int* __restrict__ nwl,
@@ -1094,7 +1059,10 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
     int64_t* t_rp = nullptr;
     int32_t* t_ci = nullptr;
     double* t_va = nullptr;
-    for (int sw = 0; sw < o.sweeps; ++sw) {
+    int lstride = stride;  // member-table width of this level
+    if (o.aggregation == 1)
+      AMG_TRY(vbm_aggregate(ar, n, rp, ci, va, diag, o.vbm_theta, comp, &nc, &lstride, sms, s));
+    for (int sw = 0; sw < o.sweeps && o.aggregation == 0; ++sw) {
       int32_t *mate = nullptr, *flag = nullptr, *id = nullptr;
       AMG_TRY(ar.alloc_n(&mate, cn));
       AMG_TRY(match_rounds(ar, cn, crp, cci, cva, cdiag, mate, nullptr, sms, s));
@@ -1152,9 +1120,9 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
     Level& L = H->L[l];
     L.agg = comp;
     L.nc = nc;
-    L.stride = stride;
-    AMG_TRY(ar.alloc_n(&L.members, nc * stride));
-    AMG_TRY(build_members(ar, n, L.agg, nc, stride, L.members, H->dev_status, sms, s));
+    L.stride = lstride;
+    AMG_TRY(ar.alloc_n(&L.members, nc * lstride));
+    AMG_TRY(build_members(ar, n, L.agg, nc, lstride, L.members, H->dev_status, sms, s));
     Level next;
     next.n = nc;
     if (H->batched) {  // aggregates never span systems: system k starts at agg(first row)
@@ -1170,8 +1138,8 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
     if (o.smooth_prolongator)
       AMG_TRY(smoothed_galerkin(ar, L, n, rp, ci, va, next, H->dev_status, sms, s));
     else
-      AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, stride, nc, &next.rowptr, &next.col,
-                       &next.val, &next.nnz, H->dev_status, sms, s));
+      AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, lstride, nc, &next.rowptr,
+                       &next.col, &next.val, &next.nnz, H->dev_status, sms, s));
     st = read_status(H, s);
     if (st < 0) return st;
     H->L.push_back(next);
