@@ -399,13 +399,13 @@ int sell_compress(Arena& ar, Sell& A, cudaStream_t s);
 int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, double* y,
                 int num_sms, cudaStream_t s);
 
-// Matching kernels (setup.cu), also launched by the allocation-free variant
 // Matching and VBM aggregation: the value of edge {i, j} is the entry stored
 // in row min(i, j).  Matrices that are symmetric in exact arithmetic need not
 // be symmetric bit for bit (smoothed coarse matrices P^T (A P) are not), and
-// both endpoints must see the same value.  aij: the entry of row i.  Rows are searched by bisection
-// (ascending columns), then by a scan; false when row j holds no column i
-// (a structurally unsymmetric pattern: the edge is then not eligible).
+// both endpoints must see the same value.  aij: the entry of row i.  Rows are
+// searched by bisection (ascending columns), then by a scan; false when row j
+// holds no column i (a structurally unsymmetric pattern: the edge is then not
+// eligible).
 __device__ __forceinline__ bool edge_value(const int64_t* __restrict__ rowptr,
                                            const int32_t* __restrict__ col,
                                            const double* __restrict__ val, int32_t i, int32_t j,
@@ -435,6 +435,7 @@ __device__ __forceinline__ bool edge_value(const int64_t* __restrict__ rowptr,
   return false;
 }
 
+// Matching kernels (setup.cu), also launched by the allocation-free variant
 __global__ void k_l1_diag(int64_t n, const int64_t* rowptr, const int32_t* col,
                           const double* val, double* d, double* diag);
 // Decoupled Vanek-Mandel-Brezina aggregation (vbm.cu): agg (n, device) gets
