@@ -58,51 +58,62 @@ struct VcycleDotEpi {
 
 // MS: the level smooths more than once per side (xp and e are used); the
 // one-sweep instantiations do not carry them, which keeps their registers
-// within the occupancy bound.  (With dot products the 32-register bound makes
-// the reduction tail spill a few values; a 40-register bound at 6 blocks per
-// SM measured slower.)
-template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT, bool MS>
+// within the occupancy bound.  NDOT > 0 (level 0 of PCG): the kernel also
+// forms (r, z) and, for NDOT = 2, (z, q).  SP = false (one system): grid-wide
+// sums, with no warp-collective operation inside the streaming loop (a
+// per-slice warp reduction there cost 10% on 256^3 Poisson); SP = true
+// (batched systems): per-slice partials in slice_part[2 sl], [2 sl + 1],
+// reduced per system afterwards.
+template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT, bool MS,
+          bool SP = false>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_post(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,
            const T* __restrict__ r, const int32_t* __restrict__ agg, const T* __restrict__ xc,
            XT* __restrict__ x, const double* __restrict__ q, Reduce red, PcgScalars* sc,
-           double* __restrict__ slice_part, const T* __restrict__ xp, T* __restrict__ e) {
-  // slice_part != null (batched systems): per-slice dot partials instead of
-  // one grid-wide reduction; they are reduced per system afterwards.
+           const T* __restrict__ xp, T* __restrict__ e, double* __restrict__ slice_part) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   constexpr int ND = NDOT > 0 ? NDOT : 1;
-  double d[ND];
+  // the running sums sit in shared memory (one slot per thread, the same
+  // additions in the same order as registers would do): the streaming loop
+  // already fills the 32-register budget of full occupancy
+  __shared__ double dacc[ND][NDOT > 0 && !SP ? SELL_BLOCK : 1];
+  if constexpr (NDOT > 0 && !SP) {
 #pragma unroll
-  for (int k = 0; k < ND; ++k) d[k] = 0.0;
+    for (int k = 0; k < NDOT; ++k) dacc[k][threadIdx.x] = 0.0;
+  }
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
        sl += nw) {
     if (!AP.live(sl)) continue;  // warp-uniform
     XT zi;
     const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi,
                                             MS ? xp : nullptr, MS ? e : nullptr);
-    double ds[ND];
+    if constexpr (NDOT > 0 && SP) {
+      double ds[NDOT];
 #pragma unroll
-    for (int k = 0; k < ND; ++k) ds[k] = 0.0;
-    if (i >= 0) {
-      if (NDOT > 0) ds[0] = (double)b[i] * (double)zi;
-      if (NDOT > 1) ds[NDOT > 1 ? 1 : 0] = (double)zi * q[i];
-    }
-    if constexpr (NDOT > 0) {
-      if (slice_part) {
+      for (int k = 0; k < NDOT; ++k) ds[k] = 0.0;
+      if (i >= 0) {
+        ds[0] = (double)b[i] * (double)zi;
+        if (NDOT > 1) ds[NDOT > 1 ? 1 : 0] = (double)zi * q[i];
+      }
 #pragma unroll
-        for (int k = 0; k < NDOT; ++k) {
-          const double v = warp_sum(ds[k]);
-          if ((threadIdx.x & 31) == 0) slice_part[sl * 2 + k] = v;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NDOT; ++k) d[k] += ds[k];
+      for (int k = 0; k < NDOT; ++k) {
+        const double v = warp_sum(ds[k]);
+        if ((threadIdx.x & 31) == 0) slice_part[sl * 2 + k] = v;
+      }
+    } else if constexpr (NDOT > 0) {
+      if (i >= 0) {
+        dacc[0][threadIdx.x] += (double)b[i] * (double)zi;
+        if (NDOT > 1) dacc[NDOT > 1 ? 1 : 0][threadIdx.x] += (double)zi * q[i];
       }
     }
   }
-  if constexpr (NDOT > 0)
-    if (!slice_part) grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
+  if constexpr (NDOT > 0 && !SP) {
+    double d[ND];
+#pragma unroll
+    for (int k = 0; k < NDOT; ++k) d[k] = dacc[k][threadIdx.x];
+    grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
+  }
 }
 
 // Post-smoother of a level with a smoothed prolongator P (Sec. 2.3; A P in
@@ -344,16 +355,26 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
     if (in.xp) {
       AMG_DISPATCH_TPR(sell_code(L.AP),
                        (k_post<TPR, V, T, BT, XT, 0, true><<<grid, SELL_BLOCK, 0, s>>>(
-                           v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, slice_part, in.xp,
-                           in.e)));
+                           v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, in.xp, in.e,
+                           nullptr)));
       AMG_LAUNCH_CHECK();
       return AMG_OK;
     }
   }
   if (in.xp) return AMG_ERR_ARG;  // several sweeps: the dot products follow separately
+  if constexpr (NDOT > 0) {
+    if (slice_part) {
+      AMG_DISPATCH_TPR(sell_code(L.AP),
+                       (k_post<TPR, V, T, BT, XT, NDOT, false, true><<<grid, SELL_BLOCK, 0, s>>>(
+                           v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, nullptr, nullptr,
+                           slice_part)));
+      AMG_LAUNCH_CHECK();
+      return AMG_OK;
+    }
+  }
   AMG_DISPATCH_TPR(sell_code(L.AP),
                    (k_post<TPR, V, T, BT, XT, NDOT, false><<<grid, SELL_BLOCK, 0, s>>>(
-                       v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, slice_part, nullptr,
+                       v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, nullptr, nullptr,
                        nullptr)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -657,7 +678,8 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
   // one sweep: the dot products are fused into the post-smoother; several:
   // they follow the last sweep
   const bool smoothed = H->opt.smooth_prolongator != 0;
-  const int fused = L0.nu > 1 || smoothed ? 0 : dots;
+  const bool separate = L0.nu > 1 || smoothed;
+  const int fused = separate ? 0 : dots;
   PROF_BEGIN(0, 2, bytes_post(L0, pbytes(L0), vb, 8.0, 8.0) + (fused > 1 ? 8.0 * L0.n : 0.0));
   const PostIn<T> in0 = post_in(L0, 0);
   int rc;
@@ -670,7 +692,7 @@ static int vcycle_levels(const amg_handle* H, const double* r0, double* z0, int 
   AMG_TRY(rc);
   PROF_END();
   if (L0.nu > 1) AMG_TRY(post_sweeps(L0, 0, z0));
-  if (L0.nu > 1 || smoothed) AMG_TRY(separate_dots());
+  if (separate) AMG_TRY(separate_dots());
   return AMG_OK;
 }
 
