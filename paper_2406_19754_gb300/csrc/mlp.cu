@@ -47,20 +47,27 @@ __device__ __forceinline__ float gelu_df(float u) {
 
 // Features of row i of a 7-point operator on an nx x ny x nz grid:
 // a_ij / a_ii towards -x, +x, -y, +y, -z, +z (0 if absent), the l1 ratio,
-// log(max|a_ij| / min|a_ij|) and the neighbour count / 6.
+// log(max|a_ij| / min|a_ij|) and the neighbour count / 6.  FP32 arithmetic
+// on the FP64 entries (the features are FP32; GB300's FP64 pipe made the
+// divisions and the logarithm the cost of this kernel): one reciprocal of
+// a_ii, and the logarithm as log1p((max - min) / min), which stays accurate
+// when max and min are close.
 __global__ void k_features(int64_t n, int64_t nx, int64_t nxy, const int64_t* __restrict__ rp,
                            const int32_t* __restrict__ ci, const double* __restrict__ v,
                            float* __restrict__ feat) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double aii = 0.0;
-    for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
-      if (ci[e] == i) aii = v[e];
-    double off[6] = {0, 0, 0, 0, 0, 0}, l1 = 0.0, amax = 0.0, amin = 0.0;
+    const int64_t e0 = rp[i], e1 = rp[i + 1];
+    float aii = 0.0f;
+    for (int64_t e = e0; e < e1; ++e)
+      if (ci[e] == i) aii = (float)v[e];
+    const float inv = 1.0f / aii;
+    float off[6] = {0, 0, 0, 0, 0, 0}, l1 = 0.0f, amax = 0.0f, amin = 0.0f;
     int cnt = 0;
-    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+    for (int64_t e = e0; e < e1; ++e) {
       const int64_t d = (int64_t)ci[e] - i;
       if (d == 0) continue;
+      const float a = (float)v[e];
       int slot = -1;
       if (d == -1) slot = 0;
       else if (d == 1) slot = 1;
@@ -68,17 +75,17 @@ __global__ void k_features(int64_t n, int64_t nx, int64_t nxy, const int64_t* __
       else if (d == nx) slot = 3;
       else if (d == -nxy) slot = 4;
       else if (d == nxy) slot = 5;
-      if (slot >= 0) off[slot] = v[e] / aii;
-      const double m = fabs(v[e]);
+      if (slot >= 0) off[slot] = a * inv;
+      const float m = fabsf(a);
       l1 += m;
-      amax = cnt == 0 ? m : fmax(amax, m);
-      amin = cnt == 0 ? m : fmin(amin, m);
+      amax = cnt == 0 ? m : fmaxf(amax, m);
+      amin = cnt == 0 ? m : fminf(amin, m);
       ++cnt;
     }
     float* f = feat + i * NF;
-    for (int k = 0; k < 6; ++k) f[k] = (float)off[k];
-    f[6] = (float)(l1 / aii);
-    f[7] = (cnt > 0 && amin > 0.0) ? (float)log(amax / amin) : 0.0f;
+    for (int k = 0; k < 6; ++k) f[k] = off[k];
+    f[6] = l1 * inv;
+    f[7] = (cnt > 0 && amin > 0.0f) ? log1pf((amax - amin) / amin) : 0.0f;
     f[8] = (float)cnt / 6.0f;
   }
 }
@@ -110,19 +117,80 @@ __device__ __forceinline__ void mlp_row(const float* __restrict__ p, const float
   a.sg = 1.0f / (1.0f + expf(-z));
 }
 
-__global__ void k_mlp_forward(int64_t n, const float* __restrict__ params,
-                              const float* __restrict__ feat, float* __restrict__ omega) {
-  __shared__ float p[NPARAM];
-  for (int k = threadIdx.x; k < NPARAM; k += blockDim.x) p[k] = params[k];
-  __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float f[NF];
+// Forward pass by tiles of 32 rows, one warp per tile: lane o evaluates
+// neuron o of each layer for the tile's rows with its weights in registers;
+// the tile's features and activations sit in shared memory and are read as
+// broadcasts (four at a time where rows are 16-byte aligned), so no weight is
+// re-read per row.  Each output is the same chain of fmaf calls, in the same
+// order, as mlp_row, so omega is the same bits as a thread-per-row pass.
+constexpr int FW_WARPS = 4;
+constexpr int FW_FLD = 12;  // padded feature row (3 float4)
+constexpr int FW_HLD = 36;  // padded activation row (float4-aligned, fewer conflicts)
+
+__global__ void __launch_bounds__(FW_WARPS * 32)
+    k_mlp_forward_tiled(int64_t n, const float* __restrict__ params,
+                        const float* __restrict__ feat, float* __restrict__ omega) {
+  __shared__ __align__(16) float fs[FW_WARPS][32 * FW_FLD];
+  __shared__ __align__(16) float hs[FW_WARPS][32 * FW_HLD];
+  __shared__ float zs[FW_WARPS][32 * 33];
+  __shared__ float w3s[NH];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float w1[NF], w2[NH];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) f[k] = feat[i * NF + k];
-    RowAct a;
-    mlp_row(p, f, a);
-    omega[i] = fmaxf(a.sg, OMEGA_MIN);
+  for (int i = 0; i < NF; ++i) w1[i] = params[OFF_W1 + lane * NF + i];
+#pragma unroll
+  for (int i = 0; i < NH; ++i) w2[i] = params[OFF_W2 + lane * NH + i];
+  const float b1 = params[OFF_B1 + lane], b2 = params[OFF_B2 + lane], b3 = params[OFF_B3];
+  if (threadIdx.x < NH) w3s[threadIdx.x] = params[OFF_W3 + threadIdx.x];
+  __syncthreads();
+  float* f = fs[w];
+  float* h = hs[w];
+  float* zr = zs[w];
+  const int64_t ntiles = (n + 31) / 32;
+  for (int64_t t = (int64_t)blockIdx.x * FW_WARPS + w; t < ntiles;
+       t += (int64_t)gridDim.x * FW_WARPS) {
+    const int64_t r0 = t * 32;
+    const int rows = (int)(n - r0 < 32 ? n - r0 : 32);
+    for (int k = lane; k < rows * NF; k += 32) f[(k / NF) * FW_FLD + k % NF] = feat[r0 * NF + k];
+    __syncwarp();
+    for (int r = 0; r < rows; ++r) {  // layer 1
+      const float4 fa = *(const float4*)(f + r * FW_FLD);
+      const float4 fb = *(const float4*)(f + r * FW_FLD + 4);
+      const float f8 = f[r * FW_FLD + 8];
+      float s = b1;
+      s = fmaf(w1[0], fa.x, s);
+      s = fmaf(w1[1], fa.y, s);
+      s = fmaf(w1[2], fa.z, s);
+      s = fmaf(w1[3], fa.w, s);
+      s = fmaf(w1[4], fb.x, s);
+      s = fmaf(w1[5], fb.y, s);
+      s = fmaf(w1[6], fb.z, s);
+      s = fmaf(w1[7], fb.w, s);
+      s = fmaf(w1[8], f8, s);
+      h[r * FW_HLD + lane] = gelu_f(s);
+    }
+    __syncwarp();
+    for (int r = 0; r < rows; ++r) {  // layer 2, and the products of layer 3
+      float s = b2;
+#pragma unroll
+      for (int i = 0; i < NH; i += 4) {
+        const float4 hv = *(const float4*)(h + r * FW_HLD + i);
+        s = fmaf(w2[i], hv.x, s);
+        s = fmaf(w2[i + 1], hv.y, s);
+        s = fmaf(w2[i + 2], hv.z, s);
+        s = fmaf(w2[i + 3], hv.w, s);
+      }
+      zr[r * 33 + lane] = gelu_f(s);
+    }
+    __syncwarp();
+    if (lane < rows) {  // layer 3: lane r finishes row r
+      float z = b3;
+#pragma unroll 8
+      for (int i = 0; i < NH; ++i) z = fmaf(w3s[i], zr[lane * 33 + i], z);
+      const float sg = 1.0f / (1.0f + expf(-z));
+      omega[r0 + lane] = fmaxf(sg, OMEGA_MIN);
+    }
+    __syncwarp();
   }
 }
 
@@ -332,8 +400,9 @@ int mlp_forward(const mlp_handle* M, int64_t n, const float* feat, float* omega,
                 amg_stream_t stream) {
   if (!M || n < 0 || !feat || !omega) return AMG_ERR_ARG;
   if (n == 0) return AMG_OK;
-  k_mlp_forward<<<grid_for(n, 128, M->num_sms, 8), 128, 0, (cudaStream_t)stream>>>(
-      n, M->params, feat, omega);
+  // 5 blocks fit an SM (41.6 KB of shared memory each): one wave
+  k_mlp_forward_tiled<<<grid_for((n + 31) / 32, FW_WARPS, M->num_sms, 5), FW_WARPS * 32, 0,
+                        (cudaStream_t)stream>>>(n, M->params, feat, omega);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }

@@ -239,15 +239,28 @@ __device__ void coarse_pcg_cta(const SellView<double>& A, const double* sinv, co
       const double pq = block_dot(n, p, q);
       if (!(pq > 0.0)) break;
       const double alpha = rz / pq;
+      // x, r, z and the sums (r, r), (r, z) in one pass: each thread adds the
+      // rows it updates, in the order block_dot would, so the sums are the
+      // same bits as two separate block_dot calls
+      double t[2] = {0.0, 0.0};
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         x[i] = x[i] + alpha * p[i];
-        r[i] = r[i] - alpha * q[i];
+        const double ri = r[i] - alpha * q[i];
+        const double zi = sinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        t[0] += ri * ri;
+        t[1] += ri * zi;
+      }
+      block_sum<2>(t);
+      __shared__ double rr_rz[2];
+      if (threadIdx.x == 0) {
+        rr_rz[0] = t[0];
+        rr_rz[1] = t[1];
       }
       __syncthreads();
-      if (sqrt(block_dot(n, r, r)) <= tol * bnorm) break;
-      for (int64_t i = threadIdx.x; i < n; i += blockDim.x) z[i] = sinv[i] * r[i];
-      __syncthreads();
-      const double rzn = block_dot(n, r, z);
+      const double rr = rr_rz[0], rzn = rr_rz[1];
+      if (sqrt(rr) <= tol * bnorm) break;
       const double beta = rzn / rz;
       for (int64_t i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
       __syncthreads();

@@ -277,13 +277,20 @@ __global__ void k_coarse_x(int64_t nco, int nblk, const int64_t* __restrict__ br
 }
 
 // Coarsest solve by PCG with the l1-Jacobi preconditioner in one CUDA block
-// (coarse_pcg_cta).
+// (coarse_pcg_cta).  w null: the five work vectors live in dynamic shared
+// memory (latency-bound iterations; the same arithmetic either way).
 template <int TPR, typename BT, typename XT>
 __global__ void __launch_bounds__(1024, 1)
     k_coarse_pcg(SellView<double> A, const double* __restrict__ sinv, const BT* __restrict__ b,
                  XT* __restrict__ xo, double* w, int maxit, double tol) {
-  coarse_pcg_cta<TPR>(A, sinv, b, xo, w, maxit, tol);
+  extern __shared__ double wsh[];
+  coarse_pcg_cta<TPR>(A, sinv, b, xo, w ? w : wsh, maxit, tol);
 }
+
+// Largest PCG coarsest level whose work vectors go to shared memory (within
+// the default 48 KB of dynamic shared memory, so no attribute call is needed
+// while a graph is being captured).
+constexpr int64_t COARSE_PCG_SMEM_ROWS = 1152;  // 5 x 1152 doubles = 45 KB, plus the static sums
 
 // ------------------------------------------------------------------ driver
 
@@ -293,8 +300,11 @@ static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s,
   if (H->opt.coarse_solver == 1) {  // PCG with l1-Jacobi (non-batched handles only)
     const Level& Lc = H->L.back();
     const SellView<double> v = view<double>(Lc.A, Lc.A.v64);
-    AMG_DISPATCH_TPR(sell_code(Lc.A), (k_coarse_pcg<TPR, BT, XT><<<1, 1024, 0, s>>>(
-                                          v, Lc.s64, b, x, H->cpcg, H->opt.coarse_maxit,
+    const bool sh = Lc.n <= COARSE_PCG_SMEM_ROWS;
+    const size_t smem = sh ? sizeof(double) * 5 * (size_t)Lc.n : 0;
+    double* w = sh ? nullptr : H->cpcg;
+    AMG_DISPATCH_TPR(sell_code(Lc.A), (k_coarse_pcg<TPR, BT, XT><<<1, 1024, smem, s>>>(
+                                          v, Lc.s64, b, x, w, H->opt.coarse_maxit,
                                           H->opt.coarse_tol)));
     AMG_LAUNCH_CHECK();
     return AMG_OK;
