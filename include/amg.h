@@ -117,10 +117,10 @@ typedef struct amg_options {
   int smooth_prolongator; /* 1: smoothed prolongators P = (I - w D^-1 A) P_hat,
                             w = 1 / ||D^-1 A||_inf, coarse matrices P^T (A P)
                             (Sec. 2.3, SMATCH); restriction by P^T, prolongation
-                            by P.  FP64 only; not with batched systems,
-                            several right-hand sides or the two-grid solver;
-                            tail_rows is ignored.  0 (default): P_hat, the 0/1
-                            aggregate map */
+                            by P.  Not with batched systems, several
+                            right-hand sides, the two-grid loss or the
+                            autotuner; tail_rows is ignored.  0 (default):
+                            P_hat, the 0/1 aggregate map */
   int aggregation;       /* 0 (default): `sweeps` pairwise matching sweeps
                             (Sec. 2.3, coupled aggregation by compatible
                             weighted matching); 1: decoupled Vanek-Mandel-Brezina

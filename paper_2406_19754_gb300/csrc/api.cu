@@ -155,9 +155,7 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   int32_t* cat_ci = nullptr;
   double* cat_va = nullptr;
   if (systems && H->opt.coarse_solver != 0) return AMG_ERR_UNSUPPORTED;
-  if (H->opt.smooth_prolongator &&
-      (systems || H->opt.precision != AMG_PREC_F64 || H->opt.autotune))
-    return AMG_ERR_UNSUPPORTED;
+  if (H->opt.smooth_prolongator && (systems || H->opt.autotune)) return AMG_ERR_UNSUPPORTED;
   if (systems) {  // batched: one block-diagonal matrix with system-aligned slices
     int dev = 0, sms = 0;
     AMG_CUDA_TRY(cudaGetDevice(&dev));

@@ -895,6 +895,8 @@ static int build_smoothed_ops(Arena& ar, Level& L, bool compress, cudaStream_t s
   const int rt = std::max(auto_tpr(L.nc, L.p_nnz), L.p_nnz >= 16 * L.nc ? 4 : 1);
   AMG_TRY(sell_from_csr(ar, L.nc, L.n, L.t_rp, L.t_ci, L.t_v, 32 / rt, rt, L.R, s, nullptr,
                         compress));
+  if (L.vstore != VAL_F64)
+    for (Sell* M : {&L.AP, &L.P, &L.R}) AMG_TRY(sell_make_copies(ar, *M, L.vstore, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   for (void* p : {(void*)L.t_rp, (void*)L.t_ci, (void*)L.t_v, (void*)L.q_rp, (void*)L.q_ci,
                   (void*)L.q_v})

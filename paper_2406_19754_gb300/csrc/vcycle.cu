@@ -119,27 +119,41 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
 // Post-smoother of a level with a smoothed prolongator P (Sec. 2.3; A P in
 // AQ, P with the same slices): z = y + S (r - (A P) x_c), y = x_pre + P x_c,
 // x_pre the pre-smoothed x (xp, or S b after one sweep); e, if set, receives
-// r - (A P) x_c for further sweeps.  FP64 only.
-template <int TPR>
+// r - (A P) x_c for further sweeps.  V: stored values, T: V-cycle vectors,
+// BT / XT: this level's b and output (FP64 on level 0).
+template <int TPR, typename V, typename T, typename BT, typename XT>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
-    k_post_sm(SellView<double> AQ, SellView<double> P, const double* __restrict__ b,
-              const double* __restrict__ s, const double* __restrict__ r,
-              const double* __restrict__ xc, const double* __restrict__ xp,
-              double* __restrict__ x, double* __restrict__ e) {
+    k_post_sm(SellView<V> AQ, SellView<V> P, const BT* __restrict__ b,
+              const T* __restrict__ s, const T* __restrict__ r, const T* __restrict__ xc,
+              const T* __restrict__ xp, XT* __restrict__ x, T* __restrict__ e) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AQ.nslices;
        sl += nw) {
-    const double aq = sell_row<TPR, double>(AQ, sl, ln, [&](int J) { return __ldg(xc + J); });
-    const double px = sell_row<TPR, double>(P, sl, ln, [&](int J) { return __ldg(xc + J); });
+    const T aq = sell_row<TPR, T>(AQ, sl, ln, [&](int J) { return __ldg(xc + J); });
+    const T px = sell_row<TPR, T>(P, sl, ln, [&](int J) { return __ldg(xc + J); });
     const int64_t i = lane_row(AQ, sl, ln);
     if (i >= 0) {
-      const double si = s[i];
-      const double yi = (xp ? xp[i] : si * b[i]) + px;
-      const double ei = r[i] - aq;
-      x[i] = fma(si, ei, yi);
+      const T si = s[i];
+      const T yi = (xp ? xp[i] : si * to_f(b[i], T(0))) + px;
+      const T ei = r[i] - aq;
+      x[i] = to_f(fma(si, ei, yi), XT(0));
       if (e) e[i] = ei;
     }
+  }
+}
+
+// b_c = R r for a smoothed level (R = P^T, own slices); V-cycle vector types.
+template <int TPR, typename V, typename T>
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
+    k_restrict_sm(SellView<V> R, const T* __restrict__ r, T* __restrict__ bc) {
+  const Lanes<TPR> ln;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < R.nslices;
+       sl += nw) {
+    const T acc = sell_row<TPR, T>(R, sl, ln, [&](int j) { return __ldg(r + j); });
+    const int64_t I = lane_row(R, sl, ln);
+    if (I >= 0) bc[I] = acc;
   }
 }
 
@@ -419,12 +433,29 @@ static int launch_sweep(const amg_handle* H, const Level& L, const BT* b, const 
   }
 }
 
+// Values of a smoothed-level operator in the level's storage type.
+template <typename V>
+static const V* sm_vals(const Sell& M) {
+  if constexpr (sizeof(V) == 8) return M.v64;
+  else if constexpr (sizeof(V) == 4) return M.v32;
+  else return M.v16;
+}
+
 template <typename T>
 static int launch_restrict(const amg_handle* H, const Level& L, const T* r, T* bc,
                            cudaStream_t s) {
-  if constexpr (sizeof(T) == 8) {
-    if (H->opt.smooth_prolongator)  // b_c = R r, R = P^T
-      return sell_spmv64(L.R, 1.0, r, 0.0, bc, H->num_sms, s);
+  if (H->opt.smooth_prolongator) {  // b_c = R r, R = P^T
+    const int grid = sell_grid(L.R.nslices, H->num_sms);
+    auto go = [&](auto vtag) -> int {
+      using V = decltype(vtag);
+      const SellView<V> v = view<V>(L.R, sm_vals<V>(L.R));
+      AMG_DISPATCH_TPR(sell_code(L.R),
+                       (k_restrict_sm<TPR, V, T><<<grid, SELL_BLOCK, 0, s>>>(v, r, bc)));
+      AMG_LAUNCH_CHECK();
+      return AMG_OK;
+    };
+    if constexpr (sizeof(T) == 8) return go(double(0));
+    else return L.vstore == VAL_BF16 ? go(__nv_bfloat16()) : go(float(0));
   }
   k_restrict<T><<<grid_for(L.nc, 256, H->num_sms, 8), 256, 0, s>>>(L.nc, L.stride, L.members, r,
                                                                    bc);
@@ -441,26 +472,32 @@ static int pre_f32(const amg_handle* H, const Level& L, const BT* b, float* r, c
 }
 
 // Post-smoother of a smoothed-prolongator level (k_post_sm; no dot products).
-static int launch_post_sm(const amg_handle* H, const Level& L, const double* b, const double* xc,
-                          double* x, cudaStream_t s, const PostIn<double>& in) {
+template <typename T, typename BT, typename XT>
+static int launch_post_sm(const amg_handle* H, const Level& L, const BT* b, const T* xc, XT* x,
+                          cudaStream_t s, const PostIn<T>& in) {
   const int grid = sell_grid(L.AP.nslices, H->num_sms);
-  const SellView<double> q = view<double>(L.AP, L.AP.v64);
-  const SellView<double> p = view<double>(L.P, L.P.v64);
-  const double* r = in.r ? in.r : (const double*)L.r;
+  const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
+  const T* r = in.r ? in.r : (const T*)L.r;
   if (sell_code(L.AP) != sell_code(L.P)) return AMG_ERR_UNSUPPORTED;
-  AMG_DISPATCH_TPR(sell_code(L.AP), (k_post_sm<TPR><<<grid, SELL_BLOCK, 0, s>>>(
-                                        q, p, b, L.s64, r, xc, in.xp, x, in.e)));
-  AMG_LAUNCH_CHECK();
-  return AMG_OK;
+  auto go = [&](auto vtag) -> int {
+    using V = decltype(vtag);
+    const SellView<V> q = view<V>(L.AP, sm_vals<V>(L.AP));
+    const SellView<V> p = view<V>(L.P, sm_vals<V>(L.P));
+    AMG_DISPATCH_TPR(sell_code(L.AP), (k_post_sm<TPR, V, T, BT, XT><<<grid, SELL_BLOCK, 0, s>>>(
+                                          q, p, b, sc, r, xc, in.xp, x, in.e)));
+    AMG_LAUNCH_CHECK();
+    return AMG_OK;
+  };
+  if constexpr (sizeof(T) == 8) return go(double(0));
+  else return L.vstore == VAL_BF16 ? go(__nv_bfloat16()) : go(float(0));
 }
 
 template <typename T, typename BT, typename XT, int NDOT>
 static int post_any(const amg_handle* H, const Level& L, const BT* b, const T* xc, XT* x,
                     const double* q, cudaStream_t s, double* slice_part = nullptr,
                     const int* act = nullptr, const PostIn<T>& in = PostIn<T>()) {
-  if constexpr (sizeof(T) == 8 && sizeof(BT) == 8 && sizeof(XT) == 8 && NDOT == 0) {
-    if (H->opt.smooth_prolongator)
-      return launch_post_sm(H, L, (const double*)b, (const double*)xc, (double*)x, s, in);
+  if constexpr (NDOT == 0) {
+    if (H->opt.smooth_prolongator) return launch_post_sm<T, BT, XT>(H, L, b, xc, x, s, in);
   }
   if constexpr (sizeof(T) == 8) {
     return launch_post<double, T, BT, XT, NDOT>(H, L, L.AP.v64, b, xc, x, q, s, slice_part,

@@ -115,6 +115,31 @@ def test_smatch_configuration_solves(amg, orc):
     assert i2["iterations"] == info["iterations"] and torch.equal(x, x2)
 
 
+@pytest.mark.parametrize("agg,extra", [("matching", dict(sweeps=3)),
+                                       ("vbm", dict()),
+                                       ("matching", dict(sweeps=3, bf16_from_level=2))])
+def test_fp32_vcycle_solves(amg, orc, agg, extra):
+    """SMATCH / VBM with the V-cycle in FP32 (BF16 values below level 2 as an
+    option), FCG in FP64: same convergence as the FP64 oracle within 2
+    iterations, and the FP32 V-cycle within FP32 rounding of the oracle's."""
+    A = poisson3d(40)
+    n = 40 ** 3
+    H = amg.Hierarchy(*amg.csr_to_device(A), aggregation=agg, smooth_prolongator=1,
+                      smooth_sweeps=4, coarse_solver=1, precision="f32", **extra)
+    Ho = orc.Hierarchy(A, aggregation=agg, smoothed=True, smooth_sweeps=4, coarse="pcg",
+                       sweeps=extra.get("sweeps", 2))
+    b = np.ones(n)
+    x, info = H.pcg(torch.as_tensor(b, device="cuda"), tol=1e-6, beta_form="flexible")
+    _, io = orc.pcg(A, b, tol=1e-6, hier=Ho, beta_form=1)
+    assert info["status"] == 0 and info["true_relres"] <= 1.1e-6
+    assert abs(info["iterations"] - io["iterations"]) <= 2
+    if "bf16_from_level" not in extra:
+        r = uniform01(7, n) - 0.4
+        z = H.vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
+        zo = Ho.vcycle(r)
+        assert np.linalg.norm(z - zo) <= 1e-4 * np.linalg.norm(zo)
+
+
 def test_update_values_recomputes_the_prolongators(amg, orc):
     shape = (22, 20, 18)
     A1 = diffusion3d(np.exp(gaussian_field(shape, 1.0, 3.0, 31)))
@@ -145,8 +170,6 @@ def test_smoothed_layouts_and_limits(amg):
         H.vcycle_multi(torch.ones((n0, 2), dtype=torch.float64, device="cuda"))
     with pytest.raises(amg.AmgError):
         H.level_prolongator(H.levels - 1)
-    with pytest.raises(amg.AmgError):
-        amg.Hierarchy(*Ad, smooth_prolongator=1, precision="f32")
     with pytest.raises(amg.AmgError):
         amg.Hierarchy(*Ad, smooth_prolongator=1, autotune=1)
     with pytest.raises(amg.AmgError):
