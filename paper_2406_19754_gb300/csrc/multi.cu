@@ -102,6 +102,55 @@ __device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, i
   }
 }
 
+// Slices of at most SL_MAXW ELL columns (7-point rows, and their A P) are
+// staged in shared memory by the warp: column indices and values come in with
+// coalesced loads, then every row of the slice reads its entries from there
+// as broadcasts and issues all of its gathers at once, so a row costs one
+// gather latency instead of a chain of index load, gather, next group.
+// Entries are applied in the same order as row_mv (ELL column order, padding
+// included): the results are the same bits.  Wider slices take row_mv.
+// The V-cycle smoothers and the PCG product (FP32 and FP64) all walk slices
+// this way.
+constexpr int SL_MAXW = 8;
+constexpr int SL_CAP = SL_MAXW * 32;
+
+template <typename V, typename T>
+__device__ __forceinline__ bool stage_slice(const SellView<V>& A, int64_t sl, int C, int lane,
+                                            int32_t* scol, T* sval, int& w) {
+  const int64_t beg = __ldg(A.sliceptr + sl);
+  w = (int)((__ldg(A.sliceptr + sl + 1) - beg) / C);
+  if (w > SL_MAXW) return false;
+  for (int e = lane; e < w * C; e += 32) {
+    scol[e] = __ldg(A.col + beg + e);
+    sval[e] = to_f(__ldg(A.val + beg + e), T(0));
+  }
+  __syncwarp();
+  return true;
+}
+
+template <int KPL, typename T, typename G>
+__device__ __forceinline__ void staged_row(const int32_t* scol, const T* sval, int C, int w,
+                                           int r, int K, int lane, T (&acc)[KPL], G g) {
+  T gg[SL_MAXW][KPL];
+#pragma unroll
+  for (int u = 0; u < SL_MAXW; ++u)
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      gg[u][q] = (u < w && c < K) ? g(scol[u * C + r], c) : T(0);
+    }
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) acc[q] = T(0);
+#pragma unroll
+  for (int u = 0; u < SL_MAXW; ++u)
+    if (u < w) {
+      const T a = sval[u * C + r];
+#pragma unroll
+      for (int q = 0; q < KPL; ++q)
+        if (lane + 32 * q < K) acc[q] = fma(a, gg[u][q], acc[q]);
+    }
+}
+
 // Column sums over the grid: per-block sums in fixed warp order, then the
 // last block adds the blocks in order and calls epi(c, t) for every column.
 template <int KPL, int NV, typename Epi>
@@ -160,20 +209,37 @@ __device__ void cols_reduce(double (&v)[NV][KPL], int K, double* part, int maxb,
 
 // ------------------------------------------------------------------ V-cycle kernels
 
+// One warp per slice (staged slices, see stage_slice).
 template <int KPL, typename V, typename T, typename BT>
 __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     k_m_pre(SellView<V> Ah, int C, int K, const BT* __restrict__ B, T* __restrict__ R) {
+  __shared__ int32_t scol_all[MROWS_BLOCK / 32][SL_CAP];
+  __shared__ T sval_all[MROWS_BLOCK / 32][SL_CAP];
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < Ah.n; i += nw) {
-    T acc[KPL];
-    row_mv<KPL, T>(Ah, i, C, K, lane, acc,
-                   [&](int j, int c) { return to_f(__ldg(B + (int64_t)j * K + c), T(0)); });
+  int32_t* scol = scol_all[threadIdx.x >> 5];
+  T* sval = sval_all[threadIdx.x >> 5];
+  auto gather = [&](int j, int c) { return to_f(__ldg(B + (int64_t)j * K + c), T(0)); };
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
+       sl += nw) {
+    const int64_t i0 = sl * C;
+    const int rows = (int)(Ah.n - i0 < C ? Ah.n - i0 : C);
+    int w;
+    const bool staged = stage_slice(Ah, sl, C, lane, scol, sval, w);
+    for (int r = 0; r < rows; ++r) {
+      const int64_t i = i0 + r;
+      T acc[KPL];
+      if (staged)
+        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc, gather);
+      else
+        row_mv<KPL, T>(Ah, i, C, K, lane, acc, gather);
 #pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-      const int c = lane + 32 * q;
-      if (c < K) R[i * K + c] = to_f(B[i * K + c], T(0)) - acc[q];
+      for (int q = 0; q < KPL; ++q) {
+        const int c = lane + 32 * q;
+        if (c < K) R[i * K + c] = to_f(B[i * K + c], T(0)) - acc[q];
+      }
     }
+    __syncwarp();  // the next slice overwrites the staging
   }
 }
 
@@ -228,26 +294,42 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
   double d[2][KPL];
 #pragma unroll
   for (int q = 0; q < KPL; ++q) d[0][q] = d[1][q] = 0.0;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < AP.n; i += nw) {
-    T acc[KPL];
-    row_mv<KPL, T>(AP, i, C, K, lane, acc,
-                   [&](int J, int c) { return __ldg(Xc + (int64_t)J * K + c); });
-    const T si = s[i];
-    const int64_t ai = agg[i];
+  __shared__ int32_t scol_all[MROWS_BLOCK / 32][SL_CAP];
+  __shared__ T sval_all[MROWS_BLOCK / 32][SL_CAP];
+  int32_t* scol = scol_all[threadIdx.x >> 5];
+  T* sval = sval_all[threadIdx.x >> 5];
+  auto gather = [&](int J, int c) { return __ldg(Xc + (int64_t)J * K + c); };
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
+       sl += nw) {
+    const int64_t i0 = sl * C;
+    const int rows = (int)(AP.n - i0 < C ? AP.n - i0 : C);
+    int w;
+    const bool staged = stage_slice(AP, sl, C, lane, scol, sval, w);
+    for (int r = 0; r < rows; ++r) {
+      const int64_t i = i0 + r;
+      T acc[KPL];
+      if (staged)
+        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc, gather);
+      else
+        row_mv<KPL, T>(AP, i, C, K, lane, acc, gather);
+      const T si = s[i];
+      const int64_t ai = agg[i];
 #pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-      const int c = lane + 32 * q;
-      if (c < K) {
-        const T bi = to_f(B[i * K + c], T(0));
-        const T yi = si * bi + Xc[ai * K + c];
-        const XT zi = to_f(yi + si * (R[i * K + c] - acc[q]), XT(0));
-        Z[i * K + c] = zi;
-        if (DOTS) {
-          d[0][q] += (double)B[i * K + c] * (double)zi;
-          d[1][q] += (double)zi * Q[i * K + c];
+      for (int q = 0; q < KPL; ++q) {
+        const int c = lane + 32 * q;
+        if (c < K) {
+          const T bi = to_f(B[i * K + c], T(0));
+          const T yi = si * bi + Xc[ai * K + c];
+          const XT zi = to_f(yi + si * (R[i * K + c] - acc[q]), XT(0));
+          Z[i * K + c] = zi;
+          if (DOTS) {
+            d[0][q] += (double)B[i * K + c] * (double)zi;
+            d[1][q] += (double)zi * Q[i * K + c];
+          }
         }
       }
     }
+    __syncwarp();
   }
   if constexpr (DOTS) cols_reduce<KPL, 2>(d, K, part, maxb, ticket, epi);
 }
@@ -390,18 +472,34 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
   double d[1][KPL];
 #pragma unroll
   for (int q = 0; q < KPL; ++q) d[0][q] = 0.0;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n; i += nw) {
-    double acc[KPL];
-    row_mv<KPL, double>(A, i, C, K, lane, acc,
-                        [&](int j, int c) { return __ldg(P + (int64_t)j * K + c); });
+  __shared__ int32_t scol_all[MROWS_BLOCK / 32][SL_CAP];
+  __shared__ double sval_all[MROWS_BLOCK / 32][SL_CAP];
+  int32_t* scol = scol_all[threadIdx.x >> 5];
+  double* sval = sval_all[threadIdx.x >> 5];
+  auto gather = [&](int j, int c) { return __ldg(P + (int64_t)j * K + c); };
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+       sl += nw) {
+    const int64_t i0 = sl * C;
+    const int rows = (int)(A.n - i0 < C ? A.n - i0 : C);
+    int w;
+    const bool staged = stage_slice(A, sl, C, lane, scol, sval, w);
+    for (int r = 0; r < rows; ++r) {
+      const int64_t i = i0 + r;
+      double acc[KPL];
+      if (staged)
+        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc, gather);
+      else
+        row_mv<KPL, double>(A, i, C, K, lane, acc, gather);
 #pragma unroll
-    for (int q = 0; q < KPL; ++q) {
-      const int c = lane + 32 * q;
-      if (c < K) {
-        Q[i * K + c] = acc[q];
-        d[0][q] += P[i * K + c] * acc[q];
+      for (int q = 0; q < KPL; ++q) {
+        const int c = lane + 32 * q;
+        if (c < K) {
+          Q[i * K + c] = acc[q];
+          d[0][q] += P[i * K + c] * acc[q];
+        }
       }
     }
+    __syncwarp();
   }
   cols_reduce<KPL, 1>(d, K, part, maxb, ticket, epi);
 }
