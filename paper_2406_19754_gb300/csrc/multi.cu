@@ -151,6 +151,39 @@ __device__ __forceinline__ void staged_row(const int32_t* scol, const T* sval, i
     }
 }
 
+// Two rows of a staged slice at once (the second when two): all gathers of
+// both rows are in flight before either row's FMAs, so a warp waits one
+// gather latency per pair of rows.
+template <int KPL, typename T, typename G>
+__device__ __forceinline__ void staged_rows2(const int32_t* scol, const T* sval, int C, int w,
+                                             int r, bool two, int K, int lane, T (&acc0)[KPL],
+                                             T (&acc1)[KPL], G g) {
+  T g0[SL_MAXW][KPL], g1[SL_MAXW][KPL];
+#pragma unroll
+  for (int u = 0; u < SL_MAXW; ++u)
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+      const int c = lane + 32 * q;
+      const bool in = u < w && c < K;
+      g0[u][q] = in ? g(scol[u * C + r], c) : T(0);
+      g1[u][q] = in && two ? g(scol[u * C + r + 1], c) : T(0);
+    }
+#pragma unroll
+  for (int q = 0; q < KPL; ++q) acc0[q] = acc1[q] = T(0);
+#pragma unroll
+  for (int u = 0; u < SL_MAXW; ++u)
+    if (u < w) {
+      const T a0 = sval[u * C + r];
+      const T a1 = two ? sval[u * C + r + 1] : T(0);
+#pragma unroll
+      for (int q = 0; q < KPL; ++q)
+        if (lane + 32 * q < K) {
+          acc0[q] = fma(a0, g0[u][q], acc0[q]);
+          acc1[q] = fma(a1, g1[u][q], acc1[q]);
+        }
+    }
+}
+
 // Column sums over the grid: per-block sums in fixed warp order, then the
 // last block adds the blocks in order and calls epi(c, t) for every column.
 template <int KPL, int NV, typename Epi>
@@ -226,18 +259,28 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     const int rows = (int)(Ah.n - i0 < C ? Ah.n - i0 : C);
     int w;
     const bool staged = stage_slice(Ah, sl, C, lane, scol, sval, w);
-    for (int r = 0; r < rows; ++r) {
-      const int64_t i = i0 + r;
-      T acc[KPL];
-      if (staged)
-        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc, gather);
-      else
-        row_mv<KPL, T>(Ah, i, C, K, lane, acc, gather);
+    auto finish = [&](int64_t i, const T(&acc)[KPL]) {
 #pragma unroll
       for (int q = 0; q < KPL; ++q) {
         const int c = lane + 32 * q;
         if (c < K) R[i * K + c] = to_f(B[i * K + c], T(0)) - acc[q];
       }
+    };
+    // FP32 vectors: two rows in flight; FP64 ones (twice the registers): one
+    constexpr int RS = sizeof(T) == 4 ? 2 : 1;
+    for (int r = 0; r < rows; r += RS) {
+      const bool two = RS == 2 && r + 1 < rows;
+      T acc0[KPL], acc1[KPL];
+      if (staged && RS == 2) {
+        staged_rows2<KPL>(scol, sval, C, w, r, two, K, lane, acc0, acc1, gather);
+      } else if (staged) {
+        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc0, gather);
+      } else {
+        row_mv<KPL, T>(Ah, i0 + r, C, K, lane, acc0, gather);
+        if (two) row_mv<KPL, T>(Ah, i0 + r + 1, C, K, lane, acc1, gather);
+      }
+      finish(i0 + r, acc0);
+      if (two) finish(i0 + r + 1, acc1);
     }
     __syncwarp();  // the next slice overwrites the staging
   }
@@ -305,13 +348,7 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     const int rows = (int)(AP.n - i0 < C ? AP.n - i0 : C);
     int w;
     const bool staged = stage_slice(AP, sl, C, lane, scol, sval, w);
-    for (int r = 0; r < rows; ++r) {
-      const int64_t i = i0 + r;
-      T acc[KPL];
-      if (staged)
-        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc, gather);
-      else
-        row_mv<KPL, T>(AP, i, C, K, lane, acc, gather);
+    auto finish = [&](int64_t i, const T(&acc)[KPL]) {
       const T si = s[i];
       const int64_t ai = agg[i];
 #pragma unroll
@@ -328,6 +365,22 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
           }
         }
       }
+    };
+    // FP32 vectors: two rows in flight; FP64 ones (twice the registers): one
+    constexpr int RS = sizeof(T) == 4 ? 2 : 1;
+    for (int r = 0; r < rows; r += RS) {
+      const bool two = RS == 2 && r + 1 < rows;
+      T acc0[KPL], acc1[KPL];
+      if (staged && RS == 2) {
+        staged_rows2<KPL>(scol, sval, C, w, r, two, K, lane, acc0, acc1, gather);
+      } else if (staged) {
+        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc0, gather);
+      } else {
+        row_mv<KPL, T>(AP, i0 + r, C, K, lane, acc0, gather);
+        if (two) row_mv<KPL, T>(AP, i0 + r + 1, C, K, lane, acc1, gather);
+      }
+      finish(i0 + r, acc0);
+      if (two) finish(i0 + r + 1, acc1);
     }
     __syncwarp();
   }
