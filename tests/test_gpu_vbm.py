@@ -134,3 +134,26 @@ def test_vbm_options_checked(amg):
                 dict(aggregation="vbm", vbm_theta=-0.1)):
         with pytest.raises(amg.AmgError):
             amg.Hierarchy(*Ad, **bad)
+
+
+def test_update_values_on_a_vbm_hierarchy(amg, orc):
+    # new coefficients, the VBM aggregates kept: bit-identical to the oracle's rebuild
+    shape = (22, 20, 18)
+    A1 = diffusion3d(np.exp(gaussian_field(shape, 1.0, 3.0, 51)))
+    A2 = diffusion3d(np.exp(gaussian_field(shape, 2.0, 3.0, 52)))
+    for smoothed in (False, True):
+        H = amg.Hierarchy(*amg.csr_to_device(A1), aggregation="vbm", max_coarse=30,
+                          smooth_prolongator=int(smoothed))
+        Ho = orc.Hierarchy(A1, aggregation="vbm", max_coarse=30, smoothed=smoothed)
+        H.update_values(*amg.csr_to_device(A2))
+        R = Ho.reuse(A2)
+        assert R.status == 0 and H.levels == R.levels
+        for l in range(1, H.levels):
+            got = H.level_export(l)
+            rp, ci, v = R.level_csr(l)
+            assert np.array_equal(got["col"].cpu().numpy(), ci)
+            assert np.array_equal(got["val"].cpu().numpy(), v)
+        b = uniform01(8, len(A1[0]) - 1)
+        z = H.vcycle(torch.as_tensor(b, device="cuda")).cpu().numpy()
+        zo = R.vcycle(b)
+        assert np.linalg.norm(z - zo) <= 1e-11 * np.linalg.norm(zo)
