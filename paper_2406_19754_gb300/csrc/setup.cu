@@ -871,13 +871,20 @@ static int smoothed_galerkin(Arena& ar, Level& L, int64_t n, const int64_t* rp,
 
 // Threads per row when the options fix none: one (32 rows a slice) for
 // ordinary rows; rows of 64 entries or more (coarse levels of smoothed
-// hierarchies reach hundreds) get about one thread per 16 entries, a power of
-// two from 4 up to a whole warp.
-static int auto_tpr(int64_t rows, int64_t nnz) {
+// hierarchies reach hundreds) get a power of two from 4 up to a whole warp,
+// about one thread per 16 entries.  FP64 operators larger than the L2 get
+// one thread per 32: GB300's FP64 pipe bounds those kernels, and each
+// halving of the threads per row removes a level of the cross-lane FP64
+// reduction tree (at 16 threads a 140-entry row spent 64 additions on it);
+// smaller operators stay in L2, are latency bound, and want the threads.
+constexpr double L2_OPERATOR_BYTES = 126.0 * 1024 * 1024;
+
+static int auto_tpr(int64_t rows, int64_t nnz, bool f64) {
   const double m = (double)nnz / (double)std::max<int64_t>(rows, 1);
   if (m < 64.0) return 1;
+  const double per = f64 && 12.0 * (double)nnz > L2_OPERATOR_BYTES ? 32.0 : 16.0;
   int t = 4;
-  while (t < 32 && 16.0 * t < m) t <<= 1;
+  while (t < 32 && per * t < m) t <<= 1;
   return t;
 }
 
@@ -892,7 +899,8 @@ static int build_smoothed_ops(Arena& ar, Level& L, bool compress, cudaStream_t s
                         false));
   AMG_TRY(sell_from_csr(ar, L.n, L.nc, L.p_rp, L.p_ci, L.p_v, L.A.C, L.A.tpr, L.P, s, nullptr,
                         false));
-  const int rt = std::max(auto_tpr(L.nc, L.p_nnz), L.p_nnz >= 16 * L.nc ? 4 : 1);
+  const int rt = std::max(auto_tpr(L.nc, L.p_nnz, L.vstore == VAL_F64),
+                          L.p_nnz >= 16 * L.nc ? 4 : 1);
   AMG_TRY(sell_from_csr(ar, L.nc, L.n, L.t_rp, L.t_ci, L.t_v, 32 / rt, rt, L.R, s, nullptr,
                         compress));
   if (L.vstore != VAL_F64)
@@ -1242,7 +1250,8 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
       }
       return AMG_OK;
     };
-    int tpr = o.threads_per_row > 0 ? o.threads_per_row : auto_tpr(L.n, L.nnz);
+    int tpr = o.threads_per_row > 0 ? o.threads_per_row
+                                    : auto_tpr(L.n, L.nnz, L.vstore == VAL_F64);
     if (o.slice_height > 0) tpr = 32 / o.slice_height;
     if (like) {  // the assembled hierarchy's layout, tuned or not
       tpr = like->L[l].A.tpr;
