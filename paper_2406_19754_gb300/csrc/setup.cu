@@ -873,10 +873,11 @@ static int smoothed_galerkin(Arena& ar, Level& L, int64_t n, const int64_t* rp,
 // ordinary rows; rows of 64 entries or more (coarse levels of smoothed
 // hierarchies reach hundreds) get a power of two from 4 up to a whole warp,
 // about one thread per 16 entries.  FP64 operators larger than the L2 get
-// one thread per 32: GB300's FP64 pipe bounds those kernels, and each
-// halving of the threads per row removes a level of the cross-lane FP64
-// reduction tree (at 16 threads a 140-entry row spent 64 additions on it);
-// smaller operators stay in L2, are latency bound, and want the threads.
+// one thread per 32: each halving of the threads per row removes a level of
+// the cross-lane FP64 reduction (shuffle and add chain; at 16 threads a
+// 140-entry row spent 64 additions on it, with the FP64 pipe 76% busy) and
+// gives each lane more independent loads; smaller operators stay in L2, are
+// latency bound, and want the threads.
 constexpr double L2_OPERATOR_BYTES = 126.0 * 1024 * 1024;
 
 static int auto_tpr(int64_t rows, int64_t nnz, bool f64) {
