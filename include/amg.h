@@ -353,10 +353,12 @@ int amg_twogrid_loss(amg_handle* H, int nsamples, int ncycles, const double* e0,
 /* One V-cycle kernel launch timed by amg_vcycle_profile. */
 typedef struct amg_kernel_time {
   int level;     /* hierarchy level */
-  int kind;      /* 0 pre-smooth+residual, 1 restriction, 2 prolongation+post-smooth,
-                    3 coarsest-level solve, 4 the persistent launch of levels
-                    >= `level` (all their steps and the coarsest solve), 5 a
-                    further smoothing sweep (smooth_sweeps > 1) */
+  int kind;      /* 0 pre-smooth+residual, 1 restriction (sums over aggregates, or
+                    the product with P^T for smoothed prolongators),
+                    2 prolongation+post-smooth, 3 coarsest-level solve, 4 the
+                    persistent launch of levels >= `level` (all their steps and
+                    the coarsest solve), 5 a further smoothing sweep
+                    (smooth_sweeps > 1) */
   double bytes;  /* algorithmic bytes: each matrix entry (value + column index:
                     4 bytes, or 2 plus a share of the slice column's base when
                     compressed) and each vector entry read or written once */
