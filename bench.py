@@ -417,19 +417,23 @@ def run_ours(a):
 
     # our kernel launches per solve (see pcg.cu, batch.cu, vcycle.cu, tail.cu):
     # one per V-cycle profile record, plus the second phase of a coarse solve
-    # over a block larger than 1024 rows and the level-0 dot kernel of a
-    # one-level hierarchy
+    # over a block larger than 1024 rows, the level-0 dot kernel of a
+    # one-level hierarchy, and the separate dot kernel of V-cycles with
+    # several sweeps or smoothed prolongators
     V = len(recs)
     if any(r_["kind"] == "coarse" for r_ in recs) and H.level_info(nl - 1)[0] > 1024:
         V += 1
-    if nl == 1:
+    if nl == 1 or (not batch and (H.opts.smooth_sweeps > 1 or H.opts.smooth_prolongator)):
         V += 1
     if batch:
         launches = (2 + (V + 5) + (it - 1) * (V + 6) + 2) * a.steps
     elif multi:
         launches = None  # the blocked kernels (multi.cu) are not counted here
     else:
-        launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1) * a.steps
+        # initial residual, first iteration (V-cycle, SpMV, update), the others
+        # (+ p update), the owed x update, and the loop graph's stopping tests
+        ctl = it if a.graph == "loop" else 0
+        launches = (1 + (V + 2) + (it - 1) * (V + 3) + 1 + ctl) * a.steps
     nlaunch = {}  # launches per V-cycle of each (level, kind)
     for _ in range(reps):
         _, recs = H.vcycle_profile(b)

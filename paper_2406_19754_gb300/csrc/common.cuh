@@ -190,6 +190,8 @@ struct PcgScalars {
   double tol;
   int maxit;
   int iter;
+  // 1 while x += alpha p of the last update is still to be applied (pcg.cu)
+  int x_pending;
 };
 
 // Coarsest blocks up to this many rows are factored and solved by one CUDA
@@ -248,6 +250,7 @@ struct amg_handle {
   const double* graph_b = nullptr;
   double* graph_x = nullptr;
   int graph_beta = -2;
+  int graph_defer = -1;
   // the whole PCG loop as one graph (device-side stopping test in a
   // conditional while node); loop_state 0 untried, 1 built, -1 unavailable
   cudaGraphExec_t loop = nullptr;

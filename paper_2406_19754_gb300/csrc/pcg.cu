@@ -104,7 +104,9 @@ struct RrEpi {
 
 // x += alpha p; r -= alpha q; (r, r); r32 (if set) = (float) r for an FP32
 // V-cycle, so it gathers 4-byte values without converting each one.
-// Skipped after a breakdown.
+// Skipped after a breakdown.  x null: the x update is deferred to the next
+// p update (k_p_update_x) or to the end of the solve (k_x_pending), which
+// read p anyway; x_pending records that it is owed.
 __global__ void k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
                             const double* __restrict__ p, const double* __restrict__ q, Reduce red,
                             PcgScalars* sc, float* __restrict__ r32) {
@@ -113,12 +115,13 @@ __global__ void k_cg_update(int64_t n, double* __restrict__ x, double* __restric
   double d[1] = {0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = x[i] + alpha * p[i];
+    if (x) x[i] = x[i] + alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
     if (r32) r32[i] = (float)ri;
     d[0] += ri * ri;
   }
+  if (!x && blockIdx.x == 0 && threadIdx.x == 0) sc->x_pending = 1;
   grid_reduce<1>(d, red, RrEpi{sc});
 }
 
@@ -128,6 +131,31 @@ __global__ void k_p_update(int64_t n, double* __restrict__ p, const double* __re
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
+}
+
+// The owed x += alpha p of the previous update (the loop only goes on after a
+// complete one), then p = z + beta p: one pass over p for both.  The same
+// expressions as k_cg_update and k_p_update, so the same bits.
+__global__ void k_p_update_x(int64_t n, double* __restrict__ p, const double* __restrict__ z,
+                             double* __restrict__ x, PcgScalars* sc) {
+  const double alpha = sc->alpha, beta = sc->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double pi = p[i];
+    x[i] = x[i] + alpha * pi;
+    p[i] = z[i] + beta * pi;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->x_pending = 0;  // nobody else reads it here
+}
+
+// End of a solve: the x update still owed, if any.
+__global__ void k_x_pending(int64_t n, double* __restrict__ x, const double* __restrict__ p,
+                            const PcgScalars* sc) {
+  if (!sc->x_pending) return;
+  const double alpha = sc->alpha;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = x[i] + alpha * p[i];
 }
 
 // ------------------------------------------------------------------ driver
@@ -158,35 +186,44 @@ static int launch_spmv_dot(const amg_handle* H, cudaStream_t s) {
   return AMG_OK;
 }
 
-static int launch_update(const amg_handle* H, double* x, cudaStream_t s) {
+// defer: x += alpha p waits for the next p update (which reads p anyway),
+// saving one pass over p per iteration; the solve then ends with
+// k_x_pending.  Not with per-iteration histories of x.
+static int launch_update(const amg_handle* H, double* x, bool defer, cudaStream_t s) {
   const int64_t n = H->L[0].n;
-  k_cg_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, x, H->r, H->p, H->q, H->red,
-                                                              H->sc, H->r32);
+  k_cg_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(
+      n, defer ? nullptr : x, H->r, H->p, H->q, H->red, H->sc, H->r32);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
 
-// One iteration after the first: z = B r (+ dots, beta), p = z + beta p,
-// q = A p (+ alpha), x/r update (+ (r, r)).
-static int iteration_body(const amg_handle* H, double* x, int dots, cudaStream_t s) {
+// One iteration after the first: z = B r (+ dots, beta), p = z + beta p
+// (with the owed x update when deferring), q = A p (+ alpha), x/r update
+// (+ (r, r)).
+static int iteration_body(const amg_handle* H, double* x, int dots, bool defer, cudaStream_t s) {
   const int64_t n = H->L[0].n;
   AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s, nullptr, H->r32));
-  k_p_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, H->p, H->z, H->sc);
+  if (defer)
+    k_p_update_x<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, H->p, H->z, x, H->sc);
+  else
+    k_p_update<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, H->p, H->z, H->sc);
   AMG_LAUNCH_CHECK();
   AMG_TRY(launch_spmv_dot(H, s));
-  AMG_TRY(launch_update(H, x, s));
+  AMG_TRY(launch_update(H, x, defer, s));
   return AMG_OK;
 }
 
-static int ensure_graph(amg_handle* H, double* x, int dots, int beta_form) {
-  if (H->graph && H->graph_x == x && H->graph_beta == beta_form) return AMG_OK;
+static int ensure_graph(amg_handle* H, double* x, int dots, int beta_form, bool defer) {
+  if (H->graph && H->graph_x == x && H->graph_beta == beta_form &&
+      H->graph_defer == (int)defer)
+    return AMG_OK;
   if (H->graph) {
     cudaGraphExecDestroy(H->graph);
     H->graph = nullptr;
   }
   cudaGraph_t g = nullptr;
   AMG_CUDA_TRY(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = iteration_body(H, x, dots, H->cap_stream);
+  int rc = iteration_body(H, x, dots, defer, H->cap_stream);
   cudaError_t e = cudaStreamEndCapture(H->cap_stream, &g);
   if (rc < 0) {
     if (g) cudaGraphDestroy(g);
@@ -198,6 +235,7 @@ static int ensure_graph(amg_handle* H, double* x, int dots, int beta_form) {
   AMG_CUDA_TRY(e);
   H->graph_x = x;
   H->graph_beta = beta_form;
+  H->graph_defer = (int)defer;
   return AMG_OK;
 }
 
@@ -269,7 +307,7 @@ int build_while_graph(cudaStream_t cs, const std::function<int(cudaStream_t)>& b
 static int build_loop(amg_handle* H, double* x, int dots, cudaGraphExec_t* out) {
   PcgScalars* sc = H->sc;
   return build_while_graph(
-      H->cap_stream, [&](cudaStream_t cs) { return iteration_body(H, x, dots, cs); },
+      H->cap_stream, [&](cudaStream_t cs) { return iteration_body(H, x, dots, true, cs); },
       [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
         k_pcg_control<<<1, 1, 0, cs>>>(sc, h);
       },
@@ -314,7 +352,10 @@ int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg
     if (rc < 0 && rc != AMG_ERR_UNSUPPORTED) return rc;
     use_loop = rc == AMG_OK;
   }
-  if (o->use_graph && !use_loop) AMG_TRY(ensure_graph(H, x, dots, beta_form));
+  // x updates are deferred (one pass over p saved per iteration) unless x is
+  // recorded after every iteration
+  const bool defer = !o->x_history;
+  if (o->use_graph && !use_loop) AMG_TRY(ensure_graph(H, x, dots, beta_form, defer));
 
   PcgScalars init = {};
   init.beta_form = beta_form;
@@ -339,7 +380,7 @@ int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg
     AMG_TRY(vcycle_run(H, H->r, H->z, dots, H->q, s, nullptr, H->r32));
     AMG_CUDA_TRY(cudaMemcpyAsync(H->p, H->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     AMG_TRY(launch_spmv_dot(H, s));
-    AMG_TRY(launch_update(H, x, s));
+    AMG_TRY(launch_update(H, x, defer, s));
     if (use_loop) {
       AMG_CUDA_TRY(cudaGraphLaunch(H->loop, s));
       AMG_TRY(read_scalars(H, s));
@@ -376,8 +417,12 @@ int pcg_run(amg_handle* H, const double* b, double* x, const pcg_options* o, pcg
       if (o->use_graph) {
         AMG_CUDA_TRY(cudaGraphLaunch(H->graph, s));
       } else {
-        AMG_TRY(iteration_body(H, x, dots, s));
+        AMG_TRY(iteration_body(H, x, dots, defer, s));
       }
+    }
+    if (defer) {
+      k_x_pending<<<grid_for(n, 256, H->num_sms, 8), 256, 0, s>>>(n, x, H->p, H->sc);
+      AMG_LAUNCH_CHECK();
     }
   }
   AMG_CUDA_TRY(cudaEventRecord(H->ev1, s));
