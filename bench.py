@@ -114,6 +114,21 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """The largest `value` over all ranks (max-over-ranks timing of replicas):
+    an all-reduce of one number on the rank's device (NCCL) or on the host
+    (gloo); `value` itself with one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    dev = device if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -383,11 +398,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
-    if ws > 1:
-        t = torch.tensor([elapsed], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dev)
     per_solve = elapsed / a.steps
     it = iters[-1]
     assert info["status"] == 0, info
