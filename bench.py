@@ -88,6 +88,8 @@ def _args():
                     choices=["poisson", "diffusion", "batch", "paper", "smatch", "vbm", "multi"],
                     default="poisson")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--bf16-from-level", type=int, default=0,
+                    help="with --precision f32: BF16 operator values from this level down")
     ap.add_argument("--graph", choices=["loop", "iteration", "none"], default="loop",
                     help="PCG replay: the whole loop as one graph (default), one graph per "
                          "iteration (the host tests after each), or plain launches")
@@ -341,6 +343,8 @@ def run_ours(a):
         tail["compress_columns"] = 1
     if a.workload in PAPER_LIKE:
         tail.update(PAPER_LIKE[a.workload][1])
+    if a.bf16_from_level:
+        tail["bf16_from_level"] = a.bf16_from_level
     beta = "flexible" if a.workload in PAPER_LIKE else "auto"
 
     def make_hierarchy():
@@ -537,6 +541,7 @@ def run_ours(a):
                        "level_rows": [lv[0] for lv in levels],
                        "operator_complexity": round(oc, 4), "iterations": it,
                        "precision": a.precision, "autotune": bool(a.autotune),
+                       "bf16_from_level": a.bf16_from_level,
                        "tail_rows": int(H.opts.tail_rows),
                        "level0_layout": lay,
                        "pcg_graph": a.graph,
