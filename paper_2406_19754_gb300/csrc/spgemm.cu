@@ -27,13 +27,13 @@ namespace {
 // large table (coarse levels of a smoothed hierarchy reach a few hundred
 // columns per row).
 constexpr int SPG_SMALL = 512;   // slots of a small table
-constexpr int SPG_LARGE = 4096;  // slots of a large table
+constexpr int SPG_LARGE = 8192;  // slots of a large table (115 KB of shared memory)
 constexpr int SPG_WARPS = 4;     // warps (small tables) per block
 constexpr int32_t SPG_EMPTY = -1;
 
 template <int SLOTS>
 __device__ __forceinline__ int spg_hash(int32_t J) {
-  constexpr int LOG = SLOTS == 512 ? 9 : 12;
+  constexpr int LOG = SLOTS == 512 ? 9 : 13;
   static_assert((1 << LOG) == SLOTS, "table size");
   return (int)(((uint32_t)J * 2654435761u) >> (32 - LOG));
 }
