@@ -12,6 +12,11 @@ flush is needed between steps.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--side 256] [--precision f64|f32]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
+Other workloads (--workload): diffusion (256^3, k = exp(g), sigma 2), batch (48
+uneven diffusion systems), multi (64 right-hand sides on 128^3 Poisson), and the
+paper's own configurations on 200^3 Poisson with b = 1 to 1e-6: paper (VMATCH),
+smatch (smoothed prolongators), vbm (Vanek-Mandel-Brezina aggregation).
+
 With N > 1 (torchrun) every rank solves its own replica of the problem: the
 path has no exchange step on one node, so there is no collective in it.
 """
