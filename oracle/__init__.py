@@ -59,7 +59,7 @@ def _declare(L):
                                      _P]
     L.orc_setup_general.restype = _P
     L.orc_setup_general.argtypes = [_I64, _P, _P, _P, C.c_int, _I64, C.c_int, C.c_double, _I64,
-                                    C.c_int, C.c_int, C.c_double, _P]
+                                    C.c_int, C.c_int, C.c_double, C.c_double, _P]
     L.orc_vbm_aggregate.restype = _I64
     L.orc_vbm_aggregate.argtypes = [_I64, _P, _P, _P, C.c_double, _P]
     L.orc_level_prolongator.restype = _I64
@@ -258,7 +258,7 @@ class Hierarchy:
     def __init__(self, A, sweeps=2, max_coarse=200, max_levels=30, stall=0.9,
                  max_dense=8192, omega=None, systems=None, smooth_sweeps=1, variable=False,
                  coarse="cholesky", coarse_maxit=40, coarse_tol=1e-4, smoothed=False,
-                 aggregation="matching", theta=0.01):
+                 aggregation="matching", theta=0.01, pfilter=0.0):
         """systems: row offsets (nsys + 1) of independent systems stacked block
         diagonally in A; coarsening then stops when each has <= max_coarse rows.
         smooth_sweeps: l1-Jacobi sweeps nu_0 before and after the coarse
@@ -266,7 +266,8 @@ class Hierarchy:
         coarse: "cholesky" (dense) or "pcg" (PCG with l1-Jacobi, at most
         coarse_maxit iterations, stop at ||r|| <= coarse_tol ||b||).
         aggregation: "matching" (`sweeps` matching sweeps) or "vbm" (decoupled
-        Vanek-Mandel-Brezina with strength threshold theta)."""
+        Vanek-Mandel-Brezina with strength threshold theta).  pfilter > 0:
+        smoothed prolongators built from the filtered matrix A_F."""
         n, rp, ci, v = csr_args(A)
         self._keep = (rp, ci, v)
         st = C.c_int(0)
@@ -275,7 +276,7 @@ class Hierarchy:
             assert systems is None and omega is None
             self.h = lib().orc_setup_general(n, _p(rp), _p(ci), _p(v), sweeps, max_coarse,
                                              max_levels, stall, max_dense, 1 if smoothed else 0,
-                                             agg, theta, C.byref(st))
+                                             agg, theta, pfilter, C.byref(st))
         elif systems is not None:
             so = _i64(systems)
             self.h = lib().orc_setup_systems(n, _p(rp), _p(ci), _p(v), len(so) - 1, _p(so),

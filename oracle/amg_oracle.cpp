@@ -50,6 +50,13 @@
 //    each output entry sums its contributions in ascending order of the
 //    inner index, each as one product and one addition (no fused multiply-
 //    add).  The V-cycle restricts with P^T and prolongs with P.
+//  * Filtered prolongator smoothing (an option, off by default; the paper's
+//    formula uses A itself): with a threshold theta_f > 0 the smoothing uses
+//    A_F, which keeps the diagonal and the entries with |a_ij| >=
+//    theta_f * sqrt(a_ii * a_jj) (the entry of row i) and adds the dropped
+//    entries of each row, in stored order, to its diagonal (row sums kept):
+//    P = (I - w D_F^-1 A_F) P_hat with w = 1 / ||D_F^-1 A_F||_inf; the coarse
+//    matrix is still P^T (A P) with the unfiltered A.
 //  * Decoupled Vanek-Mandel-Brezina aggregation (Sec. 2.3, VBM), on one
 //    process, so "decoupled" changes nothing.  Strong neighbourhood
 //    N_i = {i} + {j != i : |a_ij| >= theta * sqrt(a_ii * a_jj)}, the value of
@@ -105,6 +112,7 @@ struct Hierarchy {
   int smooth_p = 0;  // 1: smoothed prolongators (Sec. 2.3)
   int aggregation = 0;  // 0: matching sweeps; 1: VBM with strength theta
   double theta = 0.01;
+  double pfilter = 0.0;  // > 0: smooth P with the filtered matrix A_F
   std::vector<Level> lev;
   std::vector<double> chol;  // dense lower factor of the coarsest matrix, row-major
   int64_t nco = 0;
@@ -537,6 +545,34 @@ Csr csr_copy(int64_t n, const int64_t* rp, const int32_t* ci, const double* v) {
   return A;
 }
 
+// A_F of the filtered prolongator smoothing (see the header).
+Csr filtered_matrix(const Csr& A, double theta) {
+  Csr F;
+  F.n = A.n;
+  F.rowptr.assign(A.n + 1, 0);
+  std::vector<double> d(A.n);
+  for (int64_t i = 0; i < A.n; ++i) d[i] = diag_of(A, i);
+  for (int64_t i = 0; i < A.n; ++i) {
+    double lump = 0.0;
+    int64_t dpos = -1;
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      const int64_t j = A.col[e];
+      const double v = A.val[e];
+      if (j == i) {
+        dpos = (int64_t)F.col.size();
+      } else if (!(std::fabs(v) >= theta * std::sqrt(d[i] * d[j]))) {
+        lump = lump + v;
+        continue;
+      }
+      F.col.push_back((int32_t)j);
+      F.val.push_back(v);
+    }
+    if (dpos >= 0) F.val[dpos] = F.val[dpos] + lump;
+    F.rowptr[i + 1] = (int64_t)F.col.size();
+  }
+  return F;
+}
+
 // The next level's matrix: P_hat^T A P_hat in canonical order, or with the
 // smoothed prolongator P^T (A P) (which also keeps P and P^T on the level).
 void coarse_matrix(const Hierarchy& H, Level& L, int stride, Csr& Ac) {
@@ -544,8 +580,10 @@ void coarse_matrix(const Hierarchy& H, Level& L, int stride, Csr& Ac) {
     galerkin(L.A, L.agg, L.nc, L.members, stride, Ac);
     return;
   }
-  L.wp = prolongator_damping(L.A);
-  smoothed_prolongator(L.A, L.agg, L.nc, L.wp, L.P);
+  const Csr AF = H.pfilter > 0.0 ? filtered_matrix(L.A, H.pfilter) : Csr();
+  const Csr& S = H.pfilter > 0.0 ? AF : L.A;
+  L.wp = prolongator_damping(S);
+  smoothed_prolongator(S, L.agg, L.nc, L.wp, L.P);
   L.Pt = transpose(L.P, L.nc);
   Csr Q;
   spgemm(L.A, L.P, Q);
@@ -572,11 +610,12 @@ int64_t largest_block(const std::vector<int64_t>& sys, int64_t n) {
 int build(Hierarchy& H, Csr A0, int sweeps, int64_t max_coarse, int max_levels,
           double stall, int64_t max_dense, const double* omega,
           std::vector<int64_t> sys = std::vector<int64_t>(), const Hierarchy* like = nullptr,
-          int smooth_p = 0, int aggregation = 0, double theta = 0.01) {
+          int smooth_p = 0, int aggregation = 0, double theta = 0.01, double pfilter = 0.0) {
   H.sweeps = sweeps;
   H.smooth_p = like ? like->smooth_p : smooth_p;
   H.aggregation = like ? like->aggregation : aggregation;
   H.theta = like ? like->theta : theta;
+  H.pfilter = like ? like->pfilter : pfilter;
   H.lev.clear();
   H.lev.emplace_back();
   H.lev[0].A = std::move(A0);
@@ -901,15 +940,17 @@ void* orc_setup_smoothed(int64_t n, const int64_t* rp, const int32_t* ci, const 
   return H;
 }
 
-// orc_setup with every hierarchy option: smoothed prolongators (smooth_p)
-// and the aggregation (0 matching sweeps, 1 VBM with strength theta).
+// orc_setup with every hierarchy option: smoothed prolongators (smooth_p,
+// smoothed with A_F when pfilter > 0) and the aggregation (0 matching sweeps,
+// 1 VBM with strength theta).
 void* orc_setup_general(int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
                         int sweeps, int64_t max_coarse, int max_levels, double stall,
                         int64_t max_dense, int smooth_p, int aggregation, double theta,
-                        int* status) {
+                        double pfilter, int* status) {
   Hierarchy* H = new Hierarchy();
   *status = build(*H, csr_copy(n, rp, ci, v), sweeps, max_coarse, max_levels, stall, max_dense,
-                  nullptr, std::vector<int64_t>(), nullptr, smooth_p, aggregation, theta);
+                  nullptr, std::vector<int64_t>(), nullptr, smooth_p, aggregation, theta,
+                  pfilter);
   return H;
 }
 

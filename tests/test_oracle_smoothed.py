@@ -106,3 +106,45 @@ def test_matching_takes_each_edge_from_its_upper_row(orc):
     upper = (rp, ci, np.where(ci > rows, v * (1.0 + 1e-3 * u), v))
     assert np.array_equal(orc.match(lower), orc.match((rp, ci, v)))
     assert not np.array_equal(orc.match(upper), orc.match((rp, ci, v)))
+
+
+def test_filtered_prolongator_smoothing_matches_dense(orc):
+    """With pfilter > 0 the prolongator is smoothed with A_F: entries with
+    |a_ij| < theta sqrt(a_ii a_jj) dropped and lumped into the diagonal (row
+    sums kept); the coarse matrix stays P^T A P with the unfiltered A."""
+    A = diffusion3d(np.exp(gaussian_field((9, 8, 7), 2.5, 2.0, 23)))
+    theta = 0.08
+    H = orc.Hierarchy(A, sweeps=2, max_coarse=12, smoothed=True, pfilter=theta)
+    assert H.status == 0 and H.levels >= 3
+    Ad = dense(A)
+    dropped_somewhere = False
+    for l in range(H.levels - 1):
+        d = np.diag(Ad)
+        weak = (np.abs(Ad) < theta * np.sqrt(np.outer(d, d))) & ~np.eye(len(d), dtype=bool)
+        dropped_somewhere |= bool(weak.any())
+        AF = np.where(weak, 0.0, Ad)
+        AF[np.diag_indices(len(d))] += np.where(weak, Ad, 0.0).sum(axis=1)
+        assert np.allclose(AF.sum(axis=1), Ad.sum(axis=1), rtol=1e-13, atol=1e-13)
+        DF = np.diag(AF)
+        (rp, ci, v), w = H.level_prolongator(l)
+        assert w == pytest.approx(1.0 / np.max(np.abs(AF).sum(axis=1) / DF), rel=1e-14)
+        Ph = prolongator(H.level_agg(l), H.level_n(l + 1))
+        P = Ph - w * (AF / DF[:, None]) @ Ph
+        assert np.abs(_rect((rp, ci, v), P.shape[1]) - P).max() <= 1e-14 * np.abs(P).max()
+        Ac = P.T @ Ad @ P
+        Ad = dense(H.level_csr(l + 1))
+        assert np.abs(Ad - Ac).max() <= 1e-13 * np.abs(Ac).max()
+    assert dropped_somewhere
+
+
+def test_filtered_smatch_is_sparser(orc):
+    # on Poisson every level-0 coupling is strong; the coarse levels lose their
+    # weak entries, so the hierarchy is sparser and converges as fast
+    A = poisson3d(24)
+    b = np.ones(24 ** 3)
+    Hu = orc.Hierarchy(A, sweeps=3, smoothed=True, smooth_sweeps=4, coarse="pcg")
+    Hf = orc.Hierarchy(A, sweeps=3, smoothed=True, smooth_sweeps=4, coarse="pcg", pfilter=0.01)
+    assert Hf.operator_complexity() < Hu.operator_complexity()
+    _, iu = orc.pcg(A, b, tol=1e-6, hier=Hu, beta_form=1)
+    _, i_f = orc.pcg(A, b, tol=1e-6, hier=Hf, beta_form=1)
+    assert i_f["iterations"] <= iu["iterations"] + 1
