@@ -95,6 +95,8 @@ def _args():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--bf16-from-level", type=int, default=0,
                     help="with --precision f32: BF16 operator values from this level down")
+    ap.add_argument("--prolongator-filter", type=float, default=0.0,
+                    help="smoothed prolongators: smooth with the filtered matrix (threshold)")
     ap.add_argument("--graph", choices=["loop", "iteration", "none"], default="loop",
                     help="PCG replay: the whole loop as one graph (default), one graph per "
                          "iteration (the host tests after each), or plain launches")
@@ -350,6 +352,8 @@ def run_ours(a):
         tail.update(PAPER_LIKE[a.workload][1])
     if a.bf16_from_level:
         tail["bf16_from_level"] = a.bf16_from_level
+    if a.prolongator_filter:
+        tail["prolongator_filter"] = a.prolongator_filter
     beta = "flexible" if a.workload in PAPER_LIKE else "auto"
 
     def make_hierarchy():
@@ -547,6 +551,7 @@ def run_ours(a):
                        "operator_complexity": round(oc, 4), "iterations": it,
                        "precision": a.precision, "autotune": bool(a.autotune),
                        "bf16_from_level": a.bf16_from_level,
+                       "prolongator_filter": a.prolongator_filter,
                        "tail_rows": int(H.opts.tail_rows),
                        "level0_layout": lay,
                        "pcg_graph": a.graph,

@@ -129,6 +129,12 @@ typedef struct amg_options {
   double vbm_theta;      /* VBM strength threshold theta in [0, 1): j is a strong
                             neighbour of i when |a_ij| >= theta sqrt(a_ii a_jj);
                             default 0.01 */
+  double prolongator_filter; /* with smooth_prolongator: > 0 smooths P with the
+                            filtered matrix A_F (entries with |a_ij| < this x
+                            sqrt(a_ii a_jj) dropped and added to the diagonal,
+                            row sums kept): P = P_hat - w D^-1 A_F P_hat, D and
+                            w from A; 0 (default): with A, the paper's formula.
+                            In [0, 1) */
 } amg_options;
 
 /* PCG controls (Sec. 3, psb_krylov arguments). */

@@ -55,8 +55,10 @@
 //    A_F, which keeps the diagonal and the entries with |a_ij| >=
 //    theta_f * sqrt(a_ii * a_jj) (the entry of row i) and adds the dropped
 //    entries of each row, in stored order, to its diagonal (row sums kept):
-//    P = (I - w D_F^-1 A_F) P_hat with w = 1 / ||D_F^-1 A_F||_inf; the coarse
-//    matrix is still P^T (A P) with the unfiltered A.
+//    P = P_hat - w D^-1 (A_F P_hat), with D = diag(A) and w = 1 / ||D^-1 A||_inf
+//    as the paper defines them (a row whose couplings are all weak then keeps
+//    its P_hat row instead of dividing by a vanishing filtered diagonal); the
+//    coarse matrix is still P^T (A P) with the unfiltered A.
 //  * Decoupled Vanek-Mandel-Brezina aggregation (Sec. 2.3, VBM), on one
 //    process, so "decoupled" changes nothing.  Strong neighbourhood
 //    N_i = {i} + {j != i : |a_ij| >= theta * sqrt(a_ii * a_jj)}, the value of
@@ -402,9 +404,10 @@ double prolongator_damping(const Csr& A) {
   return 1.0 / m;
 }
 
-// P = P_hat - w D^-1 (A P_hat), columns ascending.
-void smoothed_prolongator(const Csr& A, const std::vector<int32_t>& agg, int64_t nc, double w,
-                          Csr& P) {
+// P = P_hat - w D^-1 (S P_hat), columns ascending; D = diag(A), S = A or its
+// filtered form A_F.
+void smoothed_prolongator(const Csr& A, const Csr& S, const std::vector<int32_t>& agg,
+                          int64_t nc, double w, Csr& P) {
   P.n = A.n;
   P.rowptr.assign(A.n + 1, 0);
   P.col.clear();
@@ -413,16 +416,17 @@ void smoothed_prolongator(const Csr& A, const std::vector<int32_t>& agg, int64_t
   for (int64_t i = 0; i < A.n; ++i) {
     row.clear();
     double aii = 0.0;
-    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+    for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e)
       if (A.col[e] == i) aii = A.val[e];
-      const int32_t J = agg[A.col[e]];
+    for (int64_t e = S.rowptr[i]; e < S.rowptr[i + 1]; ++e) {
+      const int32_t J = agg[S.col[e]];
       bool found = false;
       for (auto& c : row)
         if (c.first == J) {
-          c.second = c.second + A.val[e];
+          c.second = c.second + S.val[e];
           found = true;
         }
-      if (!found) row.push_back({J, A.val[e]});
+      if (!found) row.push_back({J, S.val[e]});
     }
     std::sort(row.begin(), row.end(),
               [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
@@ -581,9 +585,8 @@ void coarse_matrix(const Hierarchy& H, Level& L, int stride, Csr& Ac) {
     return;
   }
   const Csr AF = H.pfilter > 0.0 ? filtered_matrix(L.A, H.pfilter) : Csr();
-  const Csr& S = H.pfilter > 0.0 ? AF : L.A;
-  L.wp = prolongator_damping(S);
-  smoothed_prolongator(S, L.agg, L.nc, L.wp, L.P);
+  L.wp = prolongator_damping(L.A);
+  smoothed_prolongator(L.A, H.pfilter > 0.0 ? AF : L.A, L.agg, L.nc, L.wp, L.P);
   L.Pt = transpose(L.P, L.nc);
   Csr Q;
   spgemm(L.A, L.P, Q);

@@ -42,7 +42,8 @@ class AmgOptions(C.Structure):
                 ("compress_columns", C.c_int),
                 ("smooth_prolongator", C.c_int),
                 ("aggregation", C.c_int),
-                ("vbm_theta", C.c_double)]
+                ("vbm_theta", C.c_double),
+                ("prolongator_filter", C.c_double)]
 
 
 class PcgOptions(C.Structure):

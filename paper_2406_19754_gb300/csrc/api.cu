@@ -33,6 +33,7 @@ int amg_default_options(amg_options* o) {
   o->smooth_prolongator = 0;
   o->aggregation = 0;
   o->vbm_theta = 0.01;
+  o->prolongator_filter = 0.0;
   return AMG_OK;
 }
 
@@ -73,6 +74,7 @@ static int check_options(const amg_options& o) {
   if (o.smooth_prolongator != 0 && o.smooth_prolongator != 1) return AMG_ERR_ARG;
   if (o.aggregation != 0 && o.aggregation != 1) return AMG_ERR_ARG;
   if (!(o.vbm_theta >= 0.0 && o.vbm_theta < 1.0)) return AMG_ERR_ARG;
+  if (!(o.prolongator_filter >= 0.0 && o.prolongator_filter < 1.0)) return AMG_ERR_ARG;
   if (o.smooth_sweeps < 1 || o.smooth_sweeps > 8) return AMG_ERR_ARG;
   if (o.variable_cycle != 0 && o.variable_cycle != 1) return AMG_ERR_ARG;
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return AMG_ERR_ARG;

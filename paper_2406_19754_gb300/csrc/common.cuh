@@ -507,6 +507,12 @@ int spgemm(Arena& ar, int64_t n, const int64_t* X_rp, const int32_t* X_ci, const
 int transpose_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rp, const int32_t* ci,
                   const double* v, int64_t nnz, int64_t** T_rp, int32_t** T_ci, double** T_v,
                   int num_sms, cudaStream_t s);
+// A_F of the filtered prolongator smoothing (option prolongator_filter):
+// entries with |a_ij| < theta sqrt(a_ii a_jj) dropped, each row's dropped
+// entries added to its diagonal; diag = a_ii.
+int filter_matrix(Arena& ar, int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+                  const double* diag, double theta, int64_t** F_rp, int32_t** F_ci,
+                  double** F_v, int num_sms, cudaStream_t s);
 int smoothed_prolongator(Arena& ar, int64_t n, const int64_t* A_rp, const int32_t* A_ci,
                          const double* A_v, const int32_t* agg, const int64_t* rp, int32_t* ci,
                          double* v, double* w_out, int num_sms, cudaStream_t s);

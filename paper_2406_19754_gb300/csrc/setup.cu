@@ -843,23 +843,47 @@ static int build_ap(Arena& ar, Level& L, const int64_t* rp, const int32_t* ci, c
 // ascending inner index.  P, R and Q stay on the level until setup has built
 // the V-cycle operators from them.
 static int smoothed_galerkin(Arena& ar, Level& L, int64_t n, const int64_t* rp,
-                             const int32_t* ci, const double* va, Level& next, int* dev_status,
-                             int num_sms, cudaStream_t s) {
+                             const int32_t* ci, const double* va, Level& next, double pfilter,
+                             int* dev_status, int num_sms, cudaStream_t s) {
+  // the matrix P is smoothed with: A, or A_F (option prolongator_filter)
+  int64_t* f_rp = nullptr;
+  int32_t* f_ci = nullptr;
+  double* f_va = nullptr;
+  const int64_t* srp = rp;
+  const int32_t* sci = ci;
+  const double* sva = va;
+  if (pfilter > 0.0) {
+    double* diag = nullptr;
+    AMG_TRY(ar.alloc_n(&diag, n));
+    k_l1_diag<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(n, rp, ci, va, nullptr, diag);
+    AMG_LAUNCH_CHECK();
+    AMG_TRY(filter_matrix(ar, n, rp, ci, va, diag, pfilter, &f_rp, &f_ci, &f_va, num_sms, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    ar.release(diag);
+    srp = f_rp;
+    sci = f_ci;
+    sva = f_va;
+  }
   int64_t* cnt = nullptr;
   AMG_TRY(ar.alloc_n(&cnt, n + 1));
   AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (n + 1), s));
   const int g = grid_for(n, 256, num_sms, 8);
-  k_ap_count<<<g, 256, 0, s>>>(n, rp, ci, L.agg, cnt);
+  k_ap_count<<<g, 256, 0, s>>>(n, srp, sci, L.agg, cnt);
   AMG_LAUNCH_CHECK();
   AMG_TRY(ar.alloc_n(&L.p_rp, n + 1));
   AMG_TRY(scan_exclusive_i64(ar, cnt, L.p_rp, n + 1, &L.p_nnz, s));
   ar.release(cnt);
   AMG_TRY(ar.alloc_n(&L.p_ci, L.p_nnz));
   AMG_TRY(ar.alloc_n(&L.p_v, L.p_nnz));
-  k_ap_fill<<<g, 256, 0, s>>>(n, rp, ci, va, L.agg, L.p_rp, L.p_ci, L.p_v);
+  k_ap_fill<<<g, 256, 0, s>>>(n, srp, sci, sva, L.agg, L.p_rp, L.p_ci, L.p_v);
   AMG_LAUNCH_CHECK();
+  // D and w come from A itself; only the product A_F P_hat is filtered
   AMG_TRY(smoothed_prolongator(ar, n, rp, ci, va, L.agg, L.p_rp, L.p_ci, L.p_v, &L.wp, num_sms,
                                s));
+  if (pfilter > 0.0) {
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    for (void* p : {(void*)f_rp, (void*)f_ci, (void*)f_va}) ar.release(p);
+  }
   AMG_TRY(transpose_csr(ar, n, L.nc, L.p_rp, L.p_ci, L.p_v, L.p_nnz, &L.t_rp, &L.t_ci, &L.t_v,
                         num_sms, s));
   AMG_TRY(spgemm(ar, n, rp, ci, va, L.p_rp, L.p_ci, L.p_v, &L.q_rp, &L.q_ci, &L.q_v, &L.q_nnz,
@@ -1043,7 +1067,8 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
       Level next;
       next.n = L.nc;
       if (o.smooth_prolongator)
-        AMG_TRY(smoothed_galerkin(ar, L, n, rp, ci, va, next, H->dev_status, sms, s));
+        AMG_TRY(smoothed_galerkin(ar, L, n, rp, ci, va, next, o.prolongator_filter,
+                                  H->dev_status, sms, s));
       else
         AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, L.stride, L.nc, &next.rowptr,
                          &next.col, &next.val, &next.nnz, H->dev_status, sms, s));
@@ -1147,7 +1172,8 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
       }
     }
     if (o.smooth_prolongator)
-      AMG_TRY(smoothed_galerkin(ar, L, n, rp, ci, va, next, H->dev_status, sms, s));
+      AMG_TRY(smoothed_galerkin(ar, L, n, rp, ci, va, next, o.prolongator_filter,
+                                  H->dev_status, sms, s));
     else
       AMG_TRY(galerkin(ar, n, rp, ci, va, L.agg, L.members, lstride, nc, &next.rowptr,
                        &next.col, &next.val, &next.nnz, H->dev_status, sms, s));

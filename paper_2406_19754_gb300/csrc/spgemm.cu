@@ -235,7 +235,68 @@ __global__ void k_smooth_p(int64_t n, const int64_t* __restrict__ A_rp,
   }
 }
 
+// A_F for the filtered prolongator smoothing: the diagonal and the entries
+// with |a_ij| >= theta sqrt(a_ii a_jj) kept, the dropped ones of each row
+// added (in stored order) to its diagonal.
+__device__ __forceinline__ bool filter_drop(int64_t i, int32_t j, double v,
+                                            const double* __restrict__ diag, double theta) {
+  return j != i && !(fabs(v) >= __dmul_rn(theta, __dsqrt_rn(__dmul_rn(diag[i], diag[j]))));
+}
+
+__global__ void k_filter_count(int64_t n, const int64_t* __restrict__ rp,
+                               const int32_t* __restrict__ ci, const double* __restrict__ va,
+                               const double* __restrict__ diag, double theta, int64_t* cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = 0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+      if (!filter_drop(i, ci[e], va[e], diag, theta)) ++c;
+    cnt[i] = c;
+  }
+}
+
+__global__ void k_filter_fill(int64_t n, const int64_t* __restrict__ rp,
+                              const int32_t* __restrict__ ci, const double* __restrict__ va,
+                              const double* __restrict__ diag, double theta,
+                              const int64_t* __restrict__ frp, int32_t* __restrict__ fci,
+                              double* __restrict__ fva) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double lump = 0.0;
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+      if (filter_drop(i, ci[e], va[e], diag, theta)) lump = __dadd_rn(lump, va[e]);
+    int64_t pos = frp[i];
+    for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+      const int32_t j = ci[e];
+      if (filter_drop(i, j, va[e], diag, theta)) continue;
+      fci[pos] = j;
+      fva[pos] = j == i ? __dadd_rn(va[e], lump) : va[e];
+      ++pos;
+    }
+  }
+}
+
 }  // namespace
+
+int filter_matrix(Arena& ar, int64_t n, const int64_t* rp, const int32_t* ci, const double* va,
+                  const double* diag, double theta, int64_t** F_rp, int32_t** F_ci,
+                  double** F_v, int num_sms, cudaStream_t s) {
+  int64_t* cnt = nullptr;
+  AMG_TRY(ar.alloc_n(&cnt, n + 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * (n + 1), s));
+  const int g = grid_for(n, 256, num_sms, 8);
+  k_filter_count<<<g, 256, 0, s>>>(n, rp, ci, va, diag, theta, cnt);
+  AMG_LAUNCH_CHECK();
+  AMG_TRY(ar.alloc_n(F_rp, n + 1));
+  int64_t total = 0;
+  AMG_TRY(scan_exclusive_i64(ar, cnt, *F_rp, n + 1, &total, s));
+  ar.release(cnt);
+  AMG_TRY(ar.alloc_n(F_ci, total > 0 ? total : 1));
+  AMG_TRY(ar.alloc_n(F_v, total > 0 ? total : 1));
+  k_filter_fill<<<g, 256, 0, s>>>(n, rp, ci, va, diag, theta, *F_rp, *F_ci, *F_v);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
 
 int spgemm(Arena& ar, int64_t n, const int64_t* X_rp, const int32_t* X_ci, const double* X_v,
            const int64_t* Y_rp, const int32_t* Y_ci, const double* Y_v, int64_t** C_rp,

@@ -15,12 +15,13 @@ from synthetic import diffusion3d, gaussian_field, poisson3d, uniform01
 pytestmark = pytest.mark.gpu
 
 
-def _pair(amg, orc, A, sweeps=2, max_coarse=40, nu0=1, coarse="cholesky", **extra):
+def _pair(amg, orc, A, sweeps=2, max_coarse=40, nu0=1, coarse="cholesky", pfilter=0.0,
+          **extra):
     H = amg.Hierarchy(*amg.csr_to_device(A), sweeps=sweeps, max_coarse=max_coarse,
                       smooth_sweeps=nu0, coarse_solver=1 if coarse == "pcg" else 0,
-                      smooth_prolongator=1, **extra)
+                      smooth_prolongator=1, prolongator_filter=pfilter, **extra)
     Ho = orc.Hierarchy(A, sweeps=sweeps, max_coarse=max_coarse, smooth_sweeps=nu0,
-                       coarse=coarse, smoothed=True)
+                       coarse=coarse, smoothed=True, pfilter=pfilter)
     return H, Ho
 
 
@@ -47,6 +48,30 @@ def test_prolongators_and_coarse_matrices_bitwise(amg, orc, sweeps):
     H, Ho = _pair(amg, orc, A, sweeps=sweeps)
     assert H.levels >= 3
     _same_levels(H, Ho)
+
+
+@pytest.mark.parametrize("pfilter", [0.02, 0.08])
+def test_filtered_smoothing_bitwise(amg, orc, pfilter):
+    # P smoothed with A_F (weak entries lumped into the diagonal)
+    A = diffusion3d(np.exp(gaussian_field((22, 20, 18), 2.5, 2.0, 43)))
+    H, Ho = _pair(amg, orc, A, sweeps=2, pfilter=pfilter)
+    assert H.levels >= 3
+    _same_levels(H, Ho)
+    r = uniform01(9, 22 * 20 * 18) - 0.5
+    z = H.vcycle(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    zo = Ho.vcycle(r)
+    assert np.linalg.norm(z - zo) <= 1e-11 * np.linalg.norm(zo)
+
+
+def test_filtered_smatch_solves(amg, orc):
+    A = poisson3d(40)
+    b = np.ones(40 ** 3)
+    H, Ho = _pair(amg, orc, A, sweeps=3, max_coarse=200, nu0=4, coarse="pcg", pfilter=0.01)
+    x, info = H.pcg(torch.as_tensor(b, device="cuda"), tol=1e-6, beta_form="flexible")
+    _, io = orc.pcg(A, b, tol=1e-6, hier=Ho, beta_form=1)
+    assert info["status"] == 0 and info["true_relres"] <= 1.1e-6
+    assert abs(info["iterations"] - io["iterations"]) <= 1
+    assert H.operator_complexity() == pytest.approx(Ho.operator_complexity(), rel=1e-15)
 
 
 def _bitwise_unsymmetric(side, seed):

@@ -111,8 +111,9 @@ def test_matching_takes_each_edge_from_its_upper_row(orc):
 def test_filtered_prolongator_smoothing_matches_dense(orc):
     """With pfilter > 0 the prolongator is smoothed with A_F: entries with
     |a_ij| < theta sqrt(a_ii a_jj) dropped and lumped into the diagonal (row
-    sums kept); the coarse matrix stays P^T A P with the unfiltered A."""
-    A = diffusion3d(np.exp(gaussian_field((9, 8, 7), 2.5, 2.0, 23)))
+    sums kept), P = P_hat - w D^-1 A_F P_hat with D and w from A; the coarse
+    matrix stays P^T A P with the unfiltered A."""
+    A = diffusion3d(np.exp(gaussian_field((12, 10, 9), 2.5, 2.0, 23)))
     theta = 0.08
     H = orc.Hierarchy(A, sweeps=2, max_coarse=12, smoothed=True, pfilter=theta)
     assert H.status == 0 and H.levels >= 3
@@ -125,11 +126,10 @@ def test_filtered_prolongator_smoothing_matches_dense(orc):
         AF = np.where(weak, 0.0, Ad)
         AF[np.diag_indices(len(d))] += np.where(weak, Ad, 0.0).sum(axis=1)
         assert np.allclose(AF.sum(axis=1), Ad.sum(axis=1), rtol=1e-13, atol=1e-13)
-        DF = np.diag(AF)
         (rp, ci, v), w = H.level_prolongator(l)
-        assert w == pytest.approx(1.0 / np.max(np.abs(AF).sum(axis=1) / DF), rel=1e-14)
+        assert w == pytest.approx(1.0 / np.max(np.abs(Ad).sum(axis=1) / d), rel=1e-14)
         Ph = prolongator(H.level_agg(l), H.level_n(l + 1))
-        P = Ph - w * (AF / DF[:, None]) @ Ph
+        P = Ph - w * (AF / d[:, None]) @ Ph
         assert np.abs(_rect((rp, ci, v), P.shape[1]) - P).max() <= 1e-14 * np.abs(P).max()
         Ac = P.T @ Ad @ P
         Ad = dense(H.level_csr(l + 1))
