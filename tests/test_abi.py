@@ -56,6 +56,16 @@ def test_options_roundtrip_without_gpu(libpath):
 
     o = amg.options(precision="f32", threads_per_row=2)
     assert o.sweeps == 2 and o.max_coarse == 200 and o.precision == 1 and o.threads_per_row == 2
+    # every default the library writes lands in the binding's field of that name:
+    # the ctypes layout matches include/amg.h to the last member
+    d = amg.options()
+    assert (d.max_levels, d.stall_ratio, d.max_dense, d.tail_rows) == (30, 0.9, 8192, 1024)
+    assert (d.smooth_sweeps, d.variable_cycle, d.coarse_solver) == (1, 0, 0)
+    assert (d.coarse_maxit, d.coarse_tol, d.compress_columns) == (40, 1e-4, 0)
+    assert (d.smooth_prolongator, d.aggregation) == (0, 0)
+    assert (d.vbm_theta, d.prolongator_filter) == (0.01, 0.0)
+    v = amg.options(aggregation="vbm", vbm_theta=0.2, prolongator_filter=0.05)
+    assert (v.aggregation, v.vbm_theta, v.prolongator_filter) == (1, 0.2, 0.05)
 
 
 def test_library_built_for_sm103a(libpath):
@@ -63,3 +73,27 @@ def test_library_built_for_sm103a(libpath):
     from paper_2406_19754_gb300 import build
 
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_struct_sizes_match_the_header(tmp_path):
+    """The ctypes mirrors of the option and result structs have the C sizes."""
+    import ctypes as C
+    import shutil
+    import subprocess
+
+    from paper_2406_19754_gb300 import _lib
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "sizes.c"
+    src.write_text('#include "amg.h"\n#include <stdio.h>\nint main(void) {\n'
+                   '  printf("%zu %zu %zu\\n", sizeof(amg_options), sizeof(pcg_options),\n'
+                   '         sizeof(pcg_stats));\n  return 0;\n}\n')
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = [int(t) for t in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == [C.sizeof(_lib.AmgOptions), C.sizeof(_lib.PcgOptions),
+                   C.sizeof(_lib.PcgStats)]
