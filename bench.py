@@ -105,6 +105,8 @@ def _args():
     ap.add_argument("--tail-rows", type=int, default=None,
                     help="levels with at most this many rows run as one persistent launch "
                          "(0 = one launch per step; default: the library's)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32 and FP32+BF16 forms timed beside the FP64 solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     a = ap.parse_args()
@@ -214,6 +216,19 @@ def _oracle_iterations(side):
         return None
 
 
+def _oracle_full_run(side):
+    """The oracle's one measured single-thread run of the full problem (setup
+    and solve seconds, host CPU), as recorded with its stored results."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_poisson%d.json" % side)
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    return {"setup_s": d.get("oracle_setup_s"), "solve_s": d.get("oracle_solve_s"),
+            "threads": d.get("oracle_threads"), "host": d.get("oracle_host")}
+
+
 def oracle_sample(min_seconds=10.0, repeats=None, tol=1e-8):
     """Times the CPU oracle's PCG-AMG solve on the SAMPLE_SIDE^3 problem."""
     import oracle
@@ -265,6 +280,8 @@ def run_reference(a):
             "config": {"workload": "poisson3d_%d^3_pcg_amg_v11_tol%g" % (a.side, a.tol),
                        "sample_side": SAMPLE_SIDE},
             "cpu_baseline": {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
+                             "extrapolated": True,
+                             "measured_full_run": _oracle_full_run(a.side),
                              "sample": sample},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -287,6 +304,52 @@ def _traffic_from_profiles(kernel_key, workload):
                         and p[2] == workload:
                     return float(p[3])
     return None
+
+
+def _oracle_fixture(a):
+    """The oracle's stored run of this exact problem, or None."""
+    if a.workload != "poisson":
+        return None
+    path = os.path.join(ROOT, "tests", "golden", "oracle_poisson%d.json" % a.side)
+    try:
+        with open(path) as f:
+            fx = json.load(f)
+    except Exception:
+        return None
+    return fx if fx.get("seed") == RHS_SEED and fx.get("tol") == a.tol else None
+
+
+def oracle_x_error(a, x):
+    """max |x - x_oracle| / max |x_oracle| over the oracle's sampled rows."""
+    import torch
+
+    fx = _oracle_fixture(a)
+    if fx is None or "x_rows" not in fx:
+        return None
+    rows = torch.as_tensor(fx["x_rows"], dtype=torch.int64, device=x.device)
+    xs = x[rows].double().cpu()
+    xo = torch.as_tensor(fx["x_values"], dtype=torch.float64)
+    return float((xs - xo).abs().max() / xo.abs().max())
+
+
+def full_size_parity(a, H, levels, oc, info, x):
+    """The FP64 GPU solve against the oracle's stored run of the same problem
+    (tests/golden/oracle_poisson<side>.json): levels, entries per level,
+    operator complexity, iterations (+-1) and sampled solution entries.
+    None when no stored run matches this workload (or another precision)."""
+    fx = _oracle_fixture(a)
+    if fx is None or a.precision != "f64" or any(
+            getattr(H.opts, k, d) != d for k, d in (("sweeps", 2), ("max_coarse", 200))):
+        return None
+    lv_ok = [tuple(lv) for lv in levels] == [(v["n"], v["nnz"]) for v in fx["levels"]]
+    it_ok = abs(info["iterations"] - fx["iterations"]) <= 1
+    oc_ok = abs(oc - fx["operator_complexity"]) <= 1e-12
+    xerr = oracle_x_error(a, x)
+    x_ok = xerr is None or xerr <= 1e-10
+    return {"oracle_iterations": fx["iterations"], "iterations": info["iterations"],
+            "levels_match": lv_ok, "operator_complexity_match": oc_ok,
+            "x_err_vs_oracle": xerr, "ok": bool(lv_ok and it_ok and oc_ok and x_ok),
+            "source": "tests/golden/oracle_poisson%d.json" % a.side}
 
 
 def run_ours(a):
@@ -364,20 +427,21 @@ def run_ours(a):
 
     multi = a.workload == "multi"
 
-    def solve(bv, xv):
+    def solve(bv, xv, hier=None):
+        H_ = hier if hier is not None else H
         if multi:
-            _, stats = H.pcg_multi(bv, xv, tol=a.tol)
+            _, stats = H_.pcg_multi(bv, xv, tol=a.tol)
             worst = min(s["status"] for s in stats) if any(s["status"] < 0 for s in stats) \
                 else max(s["status"] for s in stats)
             return dict(iterations=max(s["iterations"] for s in stats), status=worst,
                         per_rhs=[s["iterations"] for s in stats])
         if batch:
-            _, stats = H.pcg(bv, xv, tol=a.tol, use_graph=GRAPH_MODE[a.graph])
+            _, stats = H_.pcg(bv, xv, tol=a.tol, use_graph=GRAPH_MODE[a.graph])
             worst = min(s["status"] for s in stats) if any(s["status"] < 0 for s in stats) \
                 else max(s["status"] for s in stats)
             return dict(iterations=max(s["iterations"] for s in stats), status=worst,
                         per_system=[s["iterations"] for s in stats])
-        return H.pcg(bv, xv, tol=a.tol, beta_form=beta, use_graph=GRAPH_MODE[a.graph])[1]
+        return H_.pcg(bv, xv, tol=a.tol, beta_form=beta, use_graph=GRAPH_MODE[a.graph])[1]
 
     # warm the module on a small problem, then time the setup of the real one
     amg.Hierarchy(*amg.csr_to_device(poisson3d(16), dev), precision=a.precision).close()
@@ -415,6 +479,8 @@ def run_ours(a):
     per_solve = elapsed / a.steps
     it = iters[-1]
     assert info["status"] == 0, info
+    x_ref = x.clone() if not (batch or multi) else None
+    parity = full_size_parity(a, H, levels, oc, info, x_ref) if not (batch or multi) else None
 
     # the blocked V-cycle of all right-hand sides against one column at a time
     mvc = None
@@ -527,12 +593,51 @@ def run_ours(a):
                "d2h_bytes_per_step": 8 * bfull.numel()}
         assert np.allclose(xh[:8].numpy(), x[:8].cpu().numpy())
 
+    # the mixed-precision forms of the same solve (FP64 outer PCG): time to
+    # tolerance, iterations, true residual and distance to the FP64 solution
+    forms = None
+    if not a.no_forms and a.workload in ("poisson", "diffusion") and a.precision == "f64":
+        forms = {"f64": {"time_to_tol_s": per_solve, "iterations": it,
+                         "true_relres": info["true_relres"], "setup_s": setup_s}}
+        if parity and parity.get("x_err_vs_oracle") is not None:
+            forms["f64"]["x_err_vs_oracle"] = parity["x_err_vs_oracle"]
+        for name, kw in (("f32", {}), ("f32_bf16_from_level2", {"bf16_from_level": 2})):
+            opts = dict(tail)
+            opts.update(kw)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Hf = amg.Hierarchy(*Ad, precision="f32", autotune=int(a.autotune), **opts)
+            torch.cuda.synchronize()
+            fsetup = time.perf_counter() - t0
+            for _ in range(a.warmup):
+                x.zero_()
+                finfo = solve(b, x, Hf)
+            ev0.record(stream)
+            for _ in range(a.steps):
+                x.zero_()
+                finfo = solve(b, x, Hf)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            fper = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dev) / a.steps
+            assert finfo["status"] == 0, (name, finfo)
+            d = {"time_to_tol_s": fper, "iterations": finfo["iterations"],
+                 "true_relres": finfo["true_relres"], "setup_s": fsetup,
+                 "x_err_vs_f64": float(torch.linalg.vector_norm(x - x_ref)
+                                       / torch.linalg.vector_norm(x_ref)),
+                 "time_cut_vs_f64": 1.0 - fper / per_solve}
+            ox = oracle_x_error(a, x)
+            if ox is not None:
+                d["x_err_vs_oracle"] = ox
+            forms[name] = d
+            Hf.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu_baseline and a.workload == "poisson":
         times, its_s = oracle_sample(min_seconds=10.0, tol=a.tol)
         per = sum(times) / len(times)
         val, it_full = scale_to_full(per, its_s, side)
         cpu = {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
+               "extrapolated": True, "measured_full_run": _oracle_full_run(side),
                "sample": ("oracle FP64 PCG-AMG solve of %d^3 Poisson (same generator, RHS seed "
                           "%d) to %g, %d runs of %.3f s, %d iterations; scaled by unknowns x "
                           "iterations to %d^3 (%s iterations, the oracle's own count)"
@@ -563,6 +668,7 @@ def run_ours(a):
             "vcycle_ms": vc_ms, "spmv_gbs": spmv_gbs, "spmv_ms": spmv_ms,
             "ms_per_iteration": per_solve * 1e3 / max(it, 1),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "parity": parity, "precision_forms": forms,
             "clocks": clk,
             "vcycle_kernels": [{"level": k[0], "kind": k[1], "launches": nlaunch[k],
                                 "ms": round(v[0], 5),
@@ -611,6 +717,10 @@ def run_ours(a):
                                     "iterations": ref_it}
         print(json.dumps(line), flush=True)
     H.close()
+    if parity is not None and not parity["ok"]:
+        print("bench: the solve does not match the oracle's run of this problem: %s"
+              % json.dumps(parity), file=sys.stderr, flush=True)
+        sys.exit(1)
     if ws > 1:
         torch.distributed.destroy_process_group()
 

@@ -437,7 +437,9 @@ int amg_level_prolongator(const amg_handle* H, int level, int64_t* rowptr, int32
  * the first sweep of one coarsening step), as a standalone call.  A: device
  * CSR.  mate: device int32[n], receives the partner of each row or -1.
  * rounds: host, may be NULL, receives the number of pointer rounds.
- * Synchronous.
+ * Errors: AMG_ERR_ARG (NULL pointers, n <= 0, nnz < n), AMG_ERR_UNSUPPORTED
+ * (n beyond int32), AMG_ERR_DEVICE_CHECK (the rounds did not end),
+ * AMG_ERR_OOM / AMG_ERR_CUDA.  Synchronous.
  */
 int amg_pairwise_match(const amg_csr* A, int32_t* mate, int* rounds, amg_stream_t stream);
 
@@ -447,17 +449,20 @@ int amg_pairwise_match(const amg_csr* A, int32_t* mate, int* rounds, amg_stream_
 /*
  * amg_pairwise_match without any device allocation.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc, such as
- * code running while a CUDA graph is being captured, applications whose
- * device memory is owned by a pool or framework that forbids outside
- * allocations, and real-time loops that must not allocate after start-up.
+ * applications whose device memory is owned by a pool or framework that
+ * forbids outside allocations, and real-time loops that must not allocate
+ * after start-up.
  * Same arguments and result as amg_pairwise_match (bit-identical mate and
  * rounds).  Its scratch is one fixed device array of 24 bytes per row for
  * AMG_NOALLOC_MAX_ROWS rows (6 MiB), held by every GPU that loads the library
  * until the process exits; larger matrices return AMG_ERR_UNSUPPORTED.  The
- * first call on a device looks up that array's address (a one-time set-up);
- * make that first call before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU (other streams or host threads)
- * race and must be serialised by the caller.  Synchronous.
+ * first call on a device looks up that array's address (a one-time set-up,
+ * kept until the process exits; a device reset invalidates it, so do not call
+ * this on a device reset by cudaDeviceReset); make that first call before any
+ * stream capture.  All calls share the array, so calls that overlap on the
+ * GPU (other streams or host threads) race and must be serialised by the
+ * caller.  Errors: as amg_pairwise_match (never AMG_ERR_OOM), and
+ * AMG_ERR_UNSUPPORTED for more than AMG_NOALLOC_MAX_ROWS rows.  Synchronous.
  */
 int amg_pairwise_match_noalloc(const amg_csr* A, int32_t* mate, int* rounds,
                                amg_stream_t stream);

@@ -8,6 +8,16 @@
 
 using namespace amg;
 
+namespace amg {
+
+int check_csr(const amg_csr* A) {
+  if (!A || A->n <= 0 || A->nnz < A->n || !A->rowptr || !A->col || !A->val) return AMG_ERR_ARG;
+  if (A->n > (int64_t)0x7fffffff) return AMG_ERR_UNSUPPORTED;
+  return AMG_OK;
+}
+
+}  // namespace amg
+
 extern "C" {
 
 int amg_default_options(amg_options* o) {
@@ -84,12 +94,6 @@ static int check_options(const amg_options& o) {
   if (C != 0 && C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
   if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return AMG_ERR_ARG;
   if (C && t && C * t != 32) return AMG_ERR_ARG;
-  return AMG_OK;
-}
-
-static int check_csr(const amg_csr* A) {
-  if (!A || A->n <= 0 || A->nnz < A->n || !A->rowptr || !A->col || !A->val) return AMG_ERR_ARG;
-  if (A->n > (int64_t)0x7fffffff) return AMG_ERR_UNSUPPORTED;
   return AMG_OK;
 }
 

@@ -468,6 +468,13 @@ __global__ void k_match_final(int64_t n, int32_t* mate);
 // same structure) instead of matching.
 int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s,
                     const amg_handle* like = nullptr);
+int match_round_loop(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                     const double* diag, int32_t* mate, int32_t* cand, int32_t* flag,
+                     int32_t* wl, int64_t wl_stride, int* cnt, int* rounds_out, int num_sms,
+                     cudaStream_t s);
+// Arguments of a caller's CSR matrix: AMG_ERR_ARG for null pointers or
+// sizes that cannot describe one, AMG_ERR_UNSUPPORTED beyond int32 rows.
+int check_csr(const amg_csr* A);
 int match_pairwise(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
                    const double* val, int32_t* mate, int* rounds, cudaStream_t s);
 int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s);

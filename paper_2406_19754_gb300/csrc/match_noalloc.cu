@@ -1,19 +1,22 @@
 // Allocation-free pairwise matching: amg_pairwise_match_noalloc.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, applications whose device memory belongs to a pool or
-// framework that forbids outside allocations, and real-time loops that must
-// not allocate (or risk an allocator stall) after start-up.  For them this
-// entry point runs the same matching kernels as amg_pairwise_match, with all
-// of its scratch (diagonal, pointers, frontier flags and lists, counters) in
-// one file-scope __device__ array of fixed size instead of cudaMalloc'ed
-// buffers.  The caller still passes the matrix and the output array.
+// Some callers cannot call cudaMalloc: applications whose device memory
+// belongs to a pool or framework that forbids outside allocations, and
+// real-time loops that must not allocate (or risk an allocator stall) after
+// start-up.  For them this entry point runs the same matching kernels as
+// amg_pairwise_match, with all of its scratch (diagonal, pointers, frontier
+// flags and lists, counters) in one file-scope __device__ array of fixed size
+// instead of cudaMalloc'ed buffers.  The caller still passes the matrix and
+// the output array.
 //
 // The array is sized for AMG_NOALLOC_MAX_ROWS rows (24 bytes a row, 6 MiB);
 // every GPU that loads this library holds it until the process exits.  Its
 // device address is looked up once per device (cudaGetSymbolAddress) by the
-// first call made with that device current.  All calls share the array, so
-// calls that overlap on the GPU (different streams or host threads) race.
+// first call made with that device current, and kept: after cudaDeviceReset
+// the kept address belongs to a context that no longer exists, so the entry
+// point must not be called on a device that was reset in this process.  All
+// calls share the array, so calls that overlap on the GPU (different streams
+// or host threads) race.
 #include <mutex>
 
 #include "common.cuh"
@@ -48,15 +51,6 @@ static int scratch_base(unsigned char** base) {
   return AMG_OK;
 }
 
-__global__ void k_noalloc_counts(int* cnt, int n) {
-  if (threadIdx.x == 0) {
-    cnt[0] = n;  // the first frontier holds every row
-    cnt[1] = 0;
-    cnt[2] = 0;  // rounds with a non-empty frontier
-    cnt[3] = 0;
-  }
-}
-
 static int match_noalloc(const amg_csr* A, int32_t* mate, int* rounds_out, cudaStream_t s) {
   unsigned char* base = nullptr;
   AMG_TRY(scratch_base(&base));
@@ -69,59 +63,22 @@ static int match_noalloc(const amg_csr* A, int32_t* mate, int* rounds_out, cudaS
   int dev = 0, sms = 0;
   AMG_CUDA_TRY(cudaGetDevice(&dev));
   AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int grid = grid_for(n, 256, sms, 8);
-  k_l1_diag<<<grid, 256, 0, s>>>(n, A->rowptr, A->col, A->val, nullptr, diag);
+  k_l1_diag<<<grid_for(n, 256, sms, 8), 256, 0, s>>>(n, A->rowptr, A->col, A->val, nullptr,
+                                                    diag);
   AMG_LAUNCH_CHECK();
-  // the array keeps the previous call's contents: reset what must start at zero
-  AMG_CUDA_TRY(cudaMemsetAsync(mate, 0xFF, sizeof(int32_t) * n, s));
-  AMG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t) * n, s));
-  k_noalloc_counts<<<1, 32, 0, s>>>(cnt, (int)n);
-  AMG_LAUNCH_CHECK();
-  k_iota<<<grid, 256, 0, s>>>(n, wl);
-  AMG_LAUNCH_CHECK();
-  int cur = 0;
-  int rc = AMG_OK;
-  int64_t launched = 0;
-  for (;;) {
-    for (int r = 0; r < 8; ++r) {
-      int32_t* w = wl + (int64_t)cur * NA_ROWS;
-      int32_t* wn = wl + (int64_t)(1 - cur) * NA_ROWS;
-      k_match_cand<<<grid, 256, 0, s>>>(w, cnt + cur, A->rowptr, A->col, A->val, diag, mate,
-                                        cand, flag, cnt + 2);
-      AMG_LAUNCH_CHECK();
-      k_match_commit<<<grid, 256, 0, s>>>(w, cnt + cur, cand, mate);
-      AMG_LAUNCH_CHECK();
-      AMG_CUDA_TRY(cudaMemsetAsync(cnt + 1 - cur, 0, sizeof(int), s));
-      k_match_expand<<<grid, 256, 0, s>>>(w, cnt + cur, A->rowptr, A->col, mate, flag, wn,
-                                          cnt + 1 - cur);
-      AMG_LAUNCH_CHECK();
-      cur = 1 - cur;
-    }
-    launched += 8;
-    int h[4];
-    AMG_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s));
-    AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    if (h[cur] == 0) {
-      if (rounds_out) *rounds_out = h[2];
-      break;
-    }
-    if (launched > 4 * n + 64) {  // each round matches at least the heaviest edge
-      rc = AMG_ERR_DEVICE_CHECK;
-      break;
-    }
-  }
-  k_match_final<<<grid, 256, 0, s>>>(n, mate);
-  AMG_LAUNCH_CHECK();
-  AMG_CUDA_TRY(cudaStreamSynchronize(s));
-  return rc;
+  // the same round loop as amg_pairwise_match, on the static scratch (its
+  // two frontiers NA_ROWS entries apart); it clears what must start at zero
+  return match_round_loop(n, A->rowptr, A->col, A->val, diag, mate, cand, flag, wl, NA_ROWS,
+                          cnt, rounds_out, sms, s);
 }
 
 }  // namespace amg
 
 extern "C" int amg_pairwise_match_noalloc(const amg_csr* A, int32_t* mate, int* rounds,
                                           amg_stream_t stream) {
-  if (!A || A->n <= 0 || A->nnz < A->n || !A->rowptr || !A->col || !A->val || !mate)
-    return AMG_ERR_ARG;
+  const int rc = amg::check_csr(A);
+  if (rc < 0) return rc;
+  if (!mate) return AMG_ERR_ARG;
   if (A->n > AMG_NOALLOC_MAX_ROWS) return AMG_ERR_UNSUPPORTED;
   return amg::match_noalloc(A, mate, rounds, (cudaStream_t)stream);
 }

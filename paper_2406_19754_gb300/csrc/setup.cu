@@ -157,20 +157,29 @@ __global__ void k_match_final(int64_t n, int32_t* mate) {
     if (mate[i] < 0) mate[i] = -1;
 }
 
-static int match_rounds(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
-                        const double* val, const double* diag, int32_t* mate, int* rounds_out,
-                        int num_sms, cudaStream_t s) {
-  int32_t *cand = nullptr, *flag = nullptr, *wl = nullptr;
-  int* cnt = nullptr;  // [0], [1]: frontier sizes; [2]: rounds with a non-empty frontier
-  AMG_TRY(ar.alloc_n(&cand, n));
-  AMG_TRY(ar.alloc_n(&flag, n));
-  AMG_TRY(ar.alloc_n(&wl, 2 * n));
-  AMG_TRY(ar.alloc_n(&cnt, 4));
+__global__ void k_match_counts(int* cnt, int n) {
+  if (threadIdx.x == 0) {
+    cnt[0] = n;  // the first frontier holds every row
+    cnt[1] = 0;
+    cnt[2] = 0;  // rounds with a non-empty frontier
+    cnt[3] = 0;
+  }
+}
+
+// The rounds of locally-dominant matching on caller-provided scratch: cand
+// and flag hold n entries, wl two frontiers of n entries at wl and
+// wl + wl_stride, cnt 4 ints.  Every entry point that matches runs this loop,
+// so they launch the same kernels in the same order.
+int match_round_loop(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                     const double* diag, int32_t* mate, int32_t* cand, int32_t* flag,
+                     int32_t* wl, int64_t wl_stride, int* cnt, int* rounds_out, int num_sms,
+                     cudaStream_t s) {
+  // scratch may hold an earlier call's contents: reset what must start at zero
   AMG_CUDA_TRY(cudaMemsetAsync(mate, 0xFF, sizeof(int32_t) * n, s));
   AMG_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int32_t) * n, s));
-  const int hcnt[4] = {(int)n, 0, 0, 0};
-  AMG_CUDA_TRY(cudaMemcpyAsync(cnt, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, s));
   const int grid = grid_for(n, 256, num_sms, 8);
+  k_match_counts<<<1, 32, 0, s>>>(cnt, (int)n);
+  AMG_LAUNCH_CHECK();
   k_iota<<<grid, 256, 0, s>>>(n, wl);
   AMG_LAUNCH_CHECK();
   int cur = 0;
@@ -179,8 +188,8 @@ static int match_rounds(Arena& ar, int64_t n, const int64_t* rowptr, const int32
   for (;;) {
     // a batch of rounds between host checks; empty rounds exit immediately
     for (int r = 0; r < 8; ++r) {
-      int32_t* w = wl + (int64_t)cur * n;
-      int32_t* wn = wl + (int64_t)(1 - cur) * n;
+      int32_t* w = wl + (int64_t)cur * wl_stride;
+      int32_t* wn = wl + (int64_t)(1 - cur) * wl_stride;
       k_match_cand<<<grid, 256, 0, s>>>(w, cnt + cur, rowptr, col, val, diag, mate, cand, flag,
                                         cnt + 2);
       AMG_LAUNCH_CHECK();
@@ -208,6 +217,20 @@ static int match_rounds(Arena& ar, int64_t n, const int64_t* rowptr, const int32
   k_match_final<<<grid, 256, 0, s>>>(n, mate);
   AMG_LAUNCH_CHECK();
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
+  return rc;
+}
+
+static int match_rounds(Arena& ar, int64_t n, const int64_t* rowptr, const int32_t* col,
+                        const double* val, const double* diag, int32_t* mate, int* rounds_out,
+                        int num_sms, cudaStream_t s) {
+  int32_t *cand = nullptr, *flag = nullptr, *wl = nullptr;
+  int* cnt = nullptr;  // [0], [1]: frontier sizes; [2]: rounds with a non-empty frontier
+  AMG_TRY(ar.alloc_n(&cand, n));
+  AMG_TRY(ar.alloc_n(&flag, n));
+  AMG_TRY(ar.alloc_n(&wl, 2 * n));
+  AMG_TRY(ar.alloc_n(&cnt, 4));
+  const int rc = match_round_loop(n, rowptr, col, val, diag, mate, cand, flag, wl, n, cnt,
+                                  rounds_out, num_sms, s);
   ar.release(cand);
   ar.release(flag);
   ar.release(wl);

@@ -1,8 +1,10 @@
 """amg_pairwise_match_noalloc: the matching entry point for callers that
-cannot allocate device memory (graph capture, framework-owned memory pools,
-real-time loops).  It must return exactly what amg_pairwise_match returns,
-call after call, although its scratch array keeps the previous call's
-contents.  This file is collected last on purpose."""
+cannot allocate device memory (framework-owned memory pools, real-time loops
+that must not allocate after start-up).  It must return exactly what
+amg_pairwise_match returns, and the oracle's matching, call after call,
+although its scratch array keeps the previous call's contents; and it must
+not allocate: the library's allocation-failure hook stays armed while it
+runs.  This file is collected last on purpose."""
 
 import ctypes as C
 
@@ -28,7 +30,7 @@ def _match(lib, fn, Ad):
     return rc, mate.cpu().numpy(), rounds.value
 
 
-def test_noalloc_matches_allocating_entry_point_twice(amg):
+def test_noalloc_matches_allocating_entry_point_twice(amg, orc):
     lib = amg._lib.load()
     cases = [poisson3d(48, 40, 36),  # 69,120 rows
              diffusion3d(np.exp(gaussian_field((30, 30, 30), 2.0, 4.0, 11))),
@@ -41,8 +43,15 @@ def test_noalloc_matches_allocating_entry_point_twice(amg):
         Ad = amg.csr_to_device(A)
         rc0, want, r0 = _match(lib, "amg_pairwise_match", Ad)
         assert rc0 == 0
+        # the oracle's sorted greedy matching (the same matching, Sec. 2.3)
+        assert np.array_equal(want, orc.match(A))
         for _ in range(2):  # two calls in a row share the same scratch array
-            rc, got, r = _match(lib, "amg_pairwise_match_noalloc", Ad)
+            # any device allocation by the library would now fail (AMG_ERR_OOM)
+            lib.amg_debug_fail_alloc_after(0)
+            try:
+                rc, got, r = _match(lib, "amg_pairwise_match_noalloc", Ad)
+            finally:
+                lib.amg_debug_fail_alloc_after(-1)
             assert rc == 0
             assert np.array_equal(got, want)
             assert r == r0
