@@ -100,6 +100,10 @@ def _args():
     ap.add_argument("--graph", choices=["loop", "iteration", "none"], default="loop",
                     help="PCG replay: the whole loop as one graph (default), one graph per "
                          "iteration (the host tests after each), or plain launches")
+    ap.add_argument("--no-ring", action="store_true",
+                    help="per-lane loads instead of the shared-memory ring (stream_ring=0)")
+    ap.add_argument("--ring-stages", type=int, default=0,
+                    help="stages per warp of the shared-memory ring (2..4; 0: the library's)")
     ap.add_argument("--compress", action="store_true",
                     help="2-byte column offsets in the kernels (compress_columns=1)")
     ap.add_argument("--tail-rows", type=int, default=None,
@@ -352,6 +356,29 @@ def full_size_parity(a, H, levels, oc, info, x):
             "source": "tests/golden/oracle_poisson%d.json" % a.side}
 
 
+# GB300's FP64 pipe: 1.25 TFLOP/s nominal = 2 FP64 FMA instructions per SM
+# per clock (152 SMs at 2.07 GHz); every FP64 add, multiply or FMA takes one
+FP64_OPS_PER_SM_CLOCK = 2.0
+SM_COUNT, SM_MAX_GHZ = 152, 2.07
+
+
+def fp64_pipe(H, level, kind, ms, a):
+    """FP64 instructions of one pre- or post-smoother launch of an FP64
+    hierarchy (one per stored entry, plus per row: 1 for r = b - acc, 3 for
+    y, e and z) against the FP64 pipe's peak: those kernels are co-limited by
+    HBM and by GB300's reduced-rate FP64 arithmetic."""
+    if a.precision != "f64" or kind not in ("pre", "post"):
+        return None
+    n = H.level_info(level)[0]
+    slots = H.level_layout(level, ap=(kind == "post"))["slots"]
+    ops = slots + (1 if kind == "pre" else 3) * n
+    peak = FP64_OPS_PER_SM_CLOCK * SM_COUNT * SM_MAX_GHZ * 1e9
+    rate = ops / (ms * 1e-3)
+    return {"ops_per_launch": ops, "ops_per_s": rate, "peak_ops_per_s": peak,
+            "frac": rate / peak,
+            "peak_source": "nominal 1.25 TFLOP/s FP64 = 2 FMA per SM per clock at 2.07 GHz"}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -411,6 +438,10 @@ def run_ours(a):
     tail = {} if a.tail_rows is None else {"tail_rows": a.tail_rows}
     if a.compress:
         tail["compress_columns"] = 1
+    if a.no_ring:
+        tail["stream_ring"] = 0
+    elif a.ring_stages:
+        tail["stream_ring"] = a.ring_stages
     if a.workload in PAPER_LIKE:
         tail.update(PAPER_LIKE[a.workload][1])
     if a.bf16_from_level:
@@ -556,6 +587,9 @@ def run_ours(a):
                          "(%.0f MB) per launch" % (L2_BYTES / 1e6)}
     if multi:
         roof["scope"] = "the single-column V-cycle of the same hierarchy"
+    fp64 = fp64_pipe(H, dl, dk, dms, a)
+    if fp64:
+        roof["fp64_pipe"] = fp64
 
     # SpMV (PCG operator) timed alone
     y = torch.empty_like(b)
@@ -660,6 +694,7 @@ def run_ours(a):
                        "tail_rows": int(H.opts.tail_rows),
                        "level0_layout": lay,
                        "pcg_graph": a.graph,
+                       "stream_ring": int(H.opts.stream_ring),
                        "level0_ap_layout": H.level_layout(0, ap=True) if nl > 1 else None,
                        "rhs": "uniform[0,1) seed %d" % RHS_SEED,
                        "l2": "inputs larger than L2 (matrix %.2f GB)" % (12.0 * nnz / 1e9),

@@ -43,7 +43,8 @@ class AmgOptions(C.Structure):
                 ("smooth_prolongator", C.c_int),
                 ("aggregation", C.c_int),
                 ("vbm_theta", C.c_double),
-                ("prolongator_filter", C.c_double)]
+                ("prolongator_filter", C.c_double),
+                ("stream_ring", C.c_int)]
 
 
 class PcgOptions(C.Structure):

@@ -44,6 +44,7 @@ int amg_default_options(amg_options* o) {
   o->aggregation = 0;
   o->vbm_theta = 0.01;
   o->prolongator_filter = 0.0;
+  o->stream_ring = 1;
   return AMG_OK;
 }
 
@@ -85,6 +86,7 @@ static int check_options(const amg_options& o) {
   if (o.aggregation != 0 && o.aggregation != 1) return AMG_ERR_ARG;
   if (!(o.vbm_theta >= 0.0 && o.vbm_theta < 1.0)) return AMG_ERR_ARG;
   if (!(o.prolongator_filter >= 0.0 && o.prolongator_filter < 1.0)) return AMG_ERR_ARG;
+  if (o.stream_ring < 0 || o.stream_ring > 4) return AMG_ERR_ARG;
   if (o.smooth_sweeps < 1 || o.smooth_sweeps > 8) return AMG_ERR_ARG;
   if (o.variable_cycle != 0 && o.variable_cycle != 1) return AMG_ERR_ARG;
   if (o.coarse_solver != 0 && o.coarse_solver != 1) return AMG_ERR_ARG;
@@ -181,6 +183,8 @@ static int create(const amg_csr* A, const amg_options* opt, cudaStream_t s, amg_
   Arena& ar = H->arena;
   AMG_TRY(ar.alloc_n(&H->dev_status, 1));
   AMG_CUDA_TRY(cudaMemsetAsync(H->dev_status, 0, sizeof(int), s));
+  AMG_TRY(ar.alloc_n(&H->wait_fail, 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(H->wait_fail, 0, sizeof(int), s));
   H->red.max_blocks = H->num_sms * 16;
   AMG_TRY(ar.alloc_n(&H->red.partials, (int64_t)H->red.max_blocks * 4));
   AMG_TRY(ar.alloc_n(&H->red.ticket, 1));

@@ -64,6 +64,7 @@ struct Arena {
 struct Sell {
   int64_t n = 0, nslices = 0, nnz_pad = 0;
   int C = 32, tpr = 1;
+  int wmax = 0;  // widest slice (ELL columns)
   int64_t* sliceptr = nullptr;
   int32_t* col = nullptr;
   double* v64 = nullptr;
@@ -280,12 +281,21 @@ struct amg_handle {
   // failure flag, and the largest co-resident grid (0: not available)
   unsigned* tail_bar = nullptr;
   int* tail_fail = nullptr;
+  // sticky flag of the streaming kernels (ring.cuh): set when a bounded wait
+  // for a bulk copy gave up; later launches return at once until it is read
+  int* wait_fail = nullptr;
   int tail_grid = 0;
   int tail_debug = 0;  // amg_debug_tail_timeout
   unsigned long long pattern = 0;  // fingerprint of the level-0 sparsity (value updates)
 };
 
 namespace amg {
+
+// Stages per warp of the shared-memory ring streams (option stream_ring:
+// 0 off, 1 the default count, 2..4 that many); 0 means the default.
+inline int ring_stages(const amg_handle* H) {
+  return H->opt.stream_ring >= 2 ? H->opt.stream_ring : 0;
+}
 
 // ------------------------------------------------------------------ device helpers
 
@@ -500,7 +510,8 @@ template <typename T>
 int tail_launch(const amg_handle* H, int lt, cudaStream_t s, const int* act = nullptr);
 int tail_reset(amg_handle* H, cudaStream_t s);
 // Synchronous: AMG_ERR_DEVICE_CHECK (and a reset) if a persistent launch gave
-// up waiting at a barrier since the last check, else AMG_OK.
+// up waiting at a barrier, or a streaming kernel gave up waiting for a bulk
+// copy, since the last check, else AMG_OK.
 int tail_check(amg_handle* H, cudaStream_t s);
 
 // Sparse products for smoothed prolongators (spgemm.cu).  C = X Y with the

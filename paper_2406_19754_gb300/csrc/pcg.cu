@@ -15,6 +15,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "ring.cuh"
 #include "sellk.cuh"
 
 namespace amg {
@@ -90,6 +91,36 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
       q[i] = acc;
       d[0] += p[i] * acc;
     }
+  }
+  grid_reduce<1>(d, red, PqEpi{sc});
+}
+
+// k_spmv_dot on the shared-memory ring of ring.cuh (one system, one thread
+// per row): the same row sums; (p, q) per thread over the warp's slices.
+__global__ void __launch_bounds__(RING_THREADS, 4)
+    k_spmv_dot_ring(SellView<double> A, const double* __restrict__ p, double* __restrict__ q,
+                    Reduce red, PcgScalars* sc, RingGeom g, RingRows rows, int* fail) {
+  extern __shared__ unsigned char ring_smem[];
+  if (*(volatile int*)fail) return;  // the host resets the reduction ticket
+  double d[1] = {0.0};
+  RingWarp<double> ring(A, g, rows, ring_smem);
+  ring.start();
+  for (int64_t sl = ring.first; sl < A.nslices; sl += ring.nwt) {
+    const int64_t i = sl * 32 + ring.lane;
+    const bool has = i < A.n;
+    const double pi = has ? __ldg(p + i) : 0.0;  // overlaps the wait
+    if (!ring.wait()) {
+      if (ring.lane == 0) ring_fail(fail, &sc->status);
+      ring.drain();
+      break;
+    }
+    const double acc =
+        ring_row_sum<double>(ring, ring.width(), [&](int j) { return __ldg(p + j); });
+    if (has) {
+      q[i] = acc;
+      d[0] += pi * acc;
+    }
+    ring.release();
   }
   grid_reduce<1>(d, red, PqEpi{sc});
 }
@@ -180,6 +211,16 @@ static int launch_spmv_dot(const amg_handle* H, cudaStream_t s) {
   const Level& L = H->L[0];
   const int grid = sell_grid(L.A.nslices, H->num_sms);
   const SellView<double> v = view<double>(L.A, L.A.v64);
+  if (H->opt.stream_ring && !H->batched) {
+    RingGeom g = ring_plan(L.A, 8, ring_stages(H), RingRows());
+    if (g.D) {
+      AMG_TRY(ring_prepare((const void*)k_spmv_dot_ring, g, L.A.nslices, H->num_sms));
+      k_spmv_dot_ring<<<g.grid, RING_THREADS, g.smem, s>>>(v, H->p, H->q, H->red, H->sc, g,
+                                                           RingRows(), H->wait_fail);
+      AMG_LAUNCH_CHECK();
+      return AMG_OK;
+    }
+  }
   AMG_DISPATCH_TPR(sell_code(L.A),
                    (k_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(v, H->p, H->q, H->red, H->sc)));
   AMG_LAUNCH_CHECK();

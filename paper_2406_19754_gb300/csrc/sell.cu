@@ -57,7 +57,7 @@ __device__ int slice_offsets(int64_t rb, int64_t re, const int64_t* rowptr, cons
 // Slice lengths (width * C) and the aligned flag of every slice.
 __global__ void k_sell_widths(int64_t n, int64_t nslices, int C, const int64_t* row0,
                               const int64_t* rowptr, const int32_t* col, int64_t* slen,
-                              uint8_t* aligned) {
+                              uint8_t* aligned, int* wmax) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nslices) return;
   int64_t rb, re, w = 0;
@@ -68,6 +68,7 @@ __global__ void k_sell_widths(int64_t n, int64_t nslices, int C, const int64_t* 
   }
   aligned[s] = w > 0 && slice_offsets(rb, re, rowptr, col, (int)w, nullptr) >= 0;
   slen[s] = w * C;
+  atomicMax(wmax, (int)(w < 0x7fffffff ? w : 0x7fffffff));
 }
 
 // Offsets of the aligned slices, stored per ELL column at sliceptr[s]/C + k.
@@ -203,17 +204,25 @@ int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, co
   }
   int64_t* slen = nullptr;
   uint8_t* aligned = nullptr;
+  int* wmax = nullptr;
   AMG_TRY(ar.alloc_n(&slen, out.nslices));
   AMG_TRY(ar.alloc_n(&aligned, out.nslices));
+  AMG_TRY(ar.alloc_n(&wmax, 1));
   AMG_TRY(ar.alloc_n(&out.sliceptr, out.nslices + 1));
+  AMG_CUDA_TRY(cudaMemsetAsync(wmax, 0, sizeof(int), s));
   const unsigned gs = (unsigned)((out.nslices + 127) / 128);
-  k_sell_widths<<<gs, 128, 0, s>>>(n, out.nslices, C, out.row0, rowptr, col, slen, aligned);
+  k_sell_widths<<<gs, 128, 0, s>>>(n, out.nslices, C, out.row0, rowptr, col, slen, aligned,
+                                   wmax);
   AMG_LAUNCH_CHECK();
+  int wmax_h = 0;
+  AMG_CUDA_TRY(cudaMemcpyAsync(&wmax_h, wmax, sizeof(int), cudaMemcpyDeviceToHost, s));
   int64_t total = 0;
   AMG_TRY(scan_exclusive_i64(ar, slen, out.sliceptr, out.nslices, &total, s));
   AMG_CUDA_TRY(cudaMemcpyAsync(out.sliceptr + out.nslices, &total, sizeof(int64_t),
                                cudaMemcpyHostToDevice, s));
   ar.release(slen);
+  ar.release(wmax);  // scan_exclusive_i64 synchronised: wmax_h is set
+  out.wmax = wmax_h;
   out.nnz_pad = total;
   AMG_TRY(ar.alloc_n(&out.col, total));
   AMG_TRY(ar.alloc_n(&out.v64, total));

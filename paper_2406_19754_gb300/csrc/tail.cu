@@ -439,12 +439,20 @@ int tail_reset(amg_handle* H, cudaStream_t s) {
 }
 
 int tail_check(amg_handle* H, cudaStream_t s) {
-  if (!H->tail_fail) return AMG_OK;
-  int f = 0;
-  AMG_CUDA_TRY(cudaMemcpyAsync(&f, H->tail_fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+  int f[2] = {0, 0};
+  if (H->tail_fail)
+    AMG_CUDA_TRY(cudaMemcpyAsync(&f[0], H->tail_fail, sizeof(int), cudaMemcpyDeviceToHost, s));
+  // the streaming kernels' flag (ring.cuh): a bounded wait for a bulk copy gave up
+  if (H->wait_fail)
+    AMG_CUDA_TRY(cudaMemcpyAsync(&f[1], H->wait_fail, sizeof(int), cudaMemcpyDeviceToHost, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
-  if (!f) return AMG_OK;
-  AMG_TRY(tail_reset(H, s));
+  if (!f[0] && !f[1]) return AMG_OK;
+  if (f[0]) AMG_TRY(tail_reset(H, s));
+  if (f[1]) {
+    // launches that returned early skipped their grid reductions
+    AMG_CUDA_TRY(cudaMemsetAsync(H->wait_fail, 0, sizeof(int), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(H->red.ticket, 0, sizeof(unsigned), s));
+  }
   return AMG_ERR_DEVICE_CHECK;
 }
 

@@ -16,6 +16,7 @@
 // and (z, q) for the PCG step.
 #include <algorithm>
 
+#include "ring.cuh"
 #include "smooth.cuh"
 
 namespace amg {
@@ -114,6 +115,89 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     for (int k = 0; k < NDOT; ++k) d[k] = dacc[k][threadIdx.x];
     grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
   }
+}
+
+// k_pre and k_post (one sweep, one system, one thread per row, FP64
+// operator values) on the shared-memory ring of ring.cuh: the same row
+// arithmetic in the same order, so the same bits as the per-lane-load
+// kernels; the dot products of the level-0 post-smoother are summed per
+// thread over the warp's slices, then per block and over blocks, as there
+// (with this launch's grid).  k_pre loads its row's b before waiting for the
+// slice; k_post's row operands s, r, b, agg (and q for the second dot
+// product) come with the slice (per-row vectors of the ring).
+template <typename V, typename T, typename BT>
+__global__ void __launch_bounds__(RING_THREADS, 4)
+    k_pre_ring(SellView<V> Ah, const BT* __restrict__ b, T* __restrict__ r, RingGeom g,
+               RingRows rows, int* fail) {
+  extern __shared__ unsigned char ring_smem[];
+  if (*(volatile int*)fail) return;
+  RingWarp<V> ring(Ah, g, rows, ring_smem);
+  ring.start();
+  for (int64_t sl = ring.first; sl < Ah.nslices; sl += ring.nwt) {
+    const int64_t i = sl * 32 + ring.lane;
+    const bool has = i < Ah.n;
+    const T bi = has ? to_f(__ldg(b + i), T(0)) : T(0);  // overlaps the wait
+    if (!ring.wait()) {
+      if (ring.lane == 0) ring_fail(fail, nullptr);
+      ring.drain();
+      return;
+    }
+    const T acc =
+        ring_row_sum<T>(ring, ring.width(), [&](int j) { return to_f(__ldg(b + j), T(0)); });
+    if (has) r[i] = bi - acc;
+    ring.release();
+  }
+}
+
+template <typename V, typename T, typename BT, typename XT, int NDOT>
+__global__ void __launch_bounds__(RING_THREADS, 4)
+    k_post_ring(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,
+                const T* __restrict__ r, const int32_t* __restrict__ agg,
+                const T* __restrict__ xc, XT* __restrict__ x, const double* __restrict__ q,
+                Reduce red, PcgScalars* sc, RingGeom g, RingRows rows, int* fail) {
+  extern __shared__ unsigned char ring_smem[];
+  if (*(volatile int*)fail) return;  // the host resets the reduction ticket
+  constexpr int ND = NDOT > 0 ? NDOT : 1;
+  double d[ND];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) d[k] = 0.0;
+  RingWarp<V> ring(AP, g, rows, ring_smem);
+  ring.start();
+  for (int64_t sl = ring.first; sl < AP.nslices; sl += ring.nwt) {
+    if (!ring.wait()) {
+      if (ring.lane == 0) ring_fail(fail, NDOT > 0 ? &sc->status : nullptr);
+      ring.drain();
+      break;
+    }
+    const bool f = ring.full(sl);
+    const int64_t i = sl * 32 + ring.lane;
+    const bool has = i < AP.n;
+    T si = T(0), ri = T(0);
+    BT bi = BT(0);
+    int32_t ai = 0;
+    double qi = 0.0;
+    if (has) {  // the row's operands, which came with the slice
+      si = ring.template row<T>(0, f, i);
+      ri = ring.template row<T>(1, f, i);
+      bi = ring.template row<BT>(2, f, i);
+      ai = ring.template row<int32_t>(3, f, i);
+      if constexpr (NDOT > 1) qi = ring.template row<double>(4, f, i);
+    }
+    // x_c of the row's own aggregate: gathered with the row's entries
+    const T xci = has ? __ldg(xc + ai) : T(0);
+    const T acc = ring_row_sum<T>(ring, ring.width(), [&](int J) { return __ldg(xc + J); });
+    if (has) {
+      // post_slice's expressions, in its order
+      const T yi = fma(si, to_f(bi, T(0)), xci);
+      const T ei = ri - acc;
+      const XT zi = to_f(fma(si, ei, yi), XT(0));
+      x[i] = zi;
+      if constexpr (NDOT > 0) d[0] += (double)bi * (double)zi;
+      if constexpr (NDOT > 1) d[NDOT > 1 ? 1 : 0] += (double)zi * qi;
+    }
+    ring.release();
+  }
+  if constexpr (NDOT > 0) grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
 }
 
 // Post-smoother of a level with a smoothed prolongator P (Sec. 2.3; A P in
@@ -350,6 +434,20 @@ static int launch_pre(const amg_handle* H, const Level& L, const V* ah, const BT
   const int grid = sell_grid(L.A.nslices, H->num_sms);
   SellView<V> v = view<V>(L.A, ah);
   v.act = act;
+  // FP64 operators (the ring's gain is where GB300's FP64 pipe co-limits the
+  // stream; FP32 values stream faster from the per-lane kernels)
+  if constexpr (sizeof(V) == 8) {
+    if (!act && H->opt.stream_ring) {
+      RingGeom g = ring_plan(L.A, (int)sizeof(V), ring_stages(H), RingRows());
+      if (g.D) {
+        AMG_TRY(ring_prepare((const void*)k_pre_ring<V, T, BT>, g, L.A.nslices, H->num_sms));
+        k_pre_ring<V, T, BT><<<g.grid, RING_THREADS, g.smem, s>>>(v, b, r, g, RingRows(),
+                                                                 H->wait_fail);
+        AMG_LAUNCH_CHECK();
+        return AMG_OK;
+      }
+    }
+  }
   AMG_DISPATCH_TPR(sell_code(L.A),
                    (k_pre<TPR, V, T, BT><<<grid, SELL_BLOCK, 0, s>>>(v, b, r)));
   AMG_LAUNCH_CHECK();
@@ -386,6 +484,25 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
     }
   }
   if (in.xp) return AMG_ERR_ARG;  // several sweeps: the dot products follow separately
+  if constexpr (sizeof(V) == 8) {  // FP64 operators, as for k_pre
+    if (!act && !slice_part && H->opt.stream_ring) {
+      RingRows rows;  // indices 0..4 as read by k_post_ring
+      rows.add(sc, (int)sizeof(T));
+      rows.add(r, (int)sizeof(T));
+      rows.add(b, (int)sizeof(BT));
+      rows.add(L.agg, (int)sizeof(int32_t));
+      if (NDOT > 1) rows.add(q, (int)sizeof(double));
+      RingGeom g = ring_plan(L.AP, (int)sizeof(V), ring_stages(H), rows);
+      if (g.D) {
+        AMG_TRY(ring_prepare((const void*)k_post_ring<V, T, BT, XT, NDOT>, g, L.AP.nslices,
+                             H->num_sms));
+        k_post_ring<V, T, BT, XT, NDOT><<<g.grid, RING_THREADS, g.smem, s>>>(
+            v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, g, rows, H->wait_fail);
+        AMG_LAUNCH_CHECK();
+        return AMG_OK;
+      }
+    }
+  }
   if constexpr (NDOT > 0) {
     if (slice_part) {
       AMG_DISPATCH_TPR(sell_code(L.AP),

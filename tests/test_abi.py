@@ -63,7 +63,7 @@ def test_options_roundtrip_without_gpu(libpath):
     assert (d.smooth_sweeps, d.variable_cycle, d.coarse_solver) == (1, 0, 0)
     assert (d.coarse_maxit, d.coarse_tol, d.compress_columns) == (40, 1e-4, 0)
     assert (d.smooth_prolongator, d.aggregation) == (0, 0)
-    assert (d.vbm_theta, d.prolongator_filter) == (0.01, 0.0)
+    assert (d.vbm_theta, d.prolongator_filter, d.stream_ring) == (0.01, 0.0, 1)
     v = amg.options(aggregation="vbm", vbm_theta=0.2, prolongator_filter=0.05)
     assert (v.aggregation, v.vbm_theta, v.prolongator_filter) == (1, 0.2, 0.05)
 
