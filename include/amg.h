@@ -210,8 +210,9 @@ int amg_update_values(amg_handle* H, const amg_csr* A, amg_stream_t stream);
 /*
  * Replaces the level-0 smoother damping weights: s_i = omega_i * (1 / d_i)
  * with d_i the l1 row sum (Sec. 2.3, l1-Jacobi).  omega: device float32[n0],
- * each in (0, 1], or NULL to restore omega == 1.  Levels >= 1 keep plain
- * l1-Jacobi.  Asynchronous.
+ * each in (0, 2) (every such omega keeps the smoother A-convergent and the
+ * V-cycle SPD; see mlp_set_omega_max), or NULL to restore omega == 1.
+ * Levels >= 1 keep plain l1-Jacobi.  Asynchronous.
  */
 int amg_set_smoother_weights(amg_handle* H, const float* omega, amg_stream_t stream);
 
@@ -297,11 +298,11 @@ int pcg_solve_batch(amg_handle* H, const double* b, double* x, const pcg_options
 
 /* ----------------------------------------------------------- learned smoother weights */
 /*
- * A 9 -> 32 -> 32 -> 1 MLP (GELU hidden layers, sigmoid output clamped to
- * [1e-3, 1)) maps each row's stencil features to the l1-Jacobi damping weight
- * omega_i, so s_i = omega_i / d_i stays an A-convergent smoother and the
- * V-cycle stays SPD (Sec. 2.3, l1-Jacobi; the network itself is not in the
- * paper).  Weights are FP32 on the device; 1409 parameters laid out as
+ * A 9 -> 32 -> 32 -> 1 MLP (GELU hidden layers, output
+ * omega = max(omega_max * sigmoid(z), 1e-3), omega_max = 1 unless set) maps
+ * each row's stencil features to the l1-Jacobi damping weight omega_i, so
+ * s_i = omega_i / d_i stays an A-convergent smoother and the V-cycle stays
+ * SPD (Sec. 2.3, l1-Jacobi; the network itself is not in the paper).  Weights are FP32 on the device; 1409 parameters laid out as
  * W1[32][9], b1[32], W2[32][32], b2[32], W3[32], b3.
  */
 typedef struct mlp_handle mlp_handle;
@@ -318,6 +319,16 @@ int mlp_destroy(mlp_handle* M);
  * state and the accumulated gradient).  Synchronous. */
 int mlp_get_params(const mlp_handle* M, float* host);
 int mlp_set_params(mlp_handle* M, const float* host);
+
+/*
+ * Output cap omega_max in [1, 2) (default 1: omega in (0, 1], the plain
+ * smoother's step at most).  Above 1 the network may over-relax; any
+ * omega_i < 2 keeps 2 diag(d / omega) - A = (2/omega - 1) diag(d) +
+ * (diag(d) - A) positive definite (diag(d) - A is diagonally dominant for the
+ * l1 row sums d), so the smoother stays A-convergent and the V-cycle SPD.
+ * Not in the paper.  Errors: AMG_ERR_ARG (M NULL, omega_max outside [1, 2)).
+ */
+int mlp_set_omega_max(mlp_handle* M, double omega_max);
 
 /* Accumulated gradient (host double[1409]).  Synchronous. */
 int mlp_get_grad(const mlp_handle* M, double* host);

@@ -87,8 +87,8 @@ def _declare(L):
 def _declare_mlp(L):
     L.mlp_orc_nparam.restype = C.c_int
     L.mlp_orc_features.argtypes = [_I64, _I64, _I64, _P, _P, _P, _P]
-    L.mlp_orc_forward.argtypes = [_I64, _P, _P, _P, _P]
-    L.mlp_orc_backward.argtypes = [_I64, _P, _P, _P, _P]
+    L.mlp_orc_forward.argtypes = [_I64, _P, _P, C.c_double, _P, _P]
+    L.mlp_orc_backward.argtypes = [_I64, _P, _P, C.c_double, _P, _P]
     L.mlp_orc_adam.argtypes = [C.c_int, _P, _P, _P, _P, C.c_int, C.c_double, C.c_double,
                                C.c_double, C.c_double]
     L.tg_orc_loss.restype = C.c_int
@@ -111,18 +111,19 @@ def mlp_features(A, shape):
     return f
 
 
-def mlp_forward(params, feat):
+def mlp_forward(params, feat, omega_max=1.0):
+    """omega = max(omega_max * sigmoid(z), 1e-3) per row, and z."""
     p, f = _f64(params), _f64(feat)
     n = f.shape[0]
     om, z = np.empty(n), np.empty(n)
-    lib().mlp_orc_forward(n, _p(p), _p(f), _p(om), _p(z))
+    lib().mlp_orc_forward(n, _p(p), _p(f), omega_max, _p(om), _p(z))
     return om, z
 
 
-def mlp_backward(params, feat, domega):
+def mlp_backward(params, feat, domega, omega_max=1.0):
     p, f, d = _f64(params), _f64(feat), _f64(domega)
     g = np.empty(mlp_nparam())
-    lib().mlp_orc_backward(f.shape[0], _p(p), _p(f), _p(d), _p(g))
+    lib().mlp_orc_backward(f.shape[0], _p(p), _p(f), omega_max, _p(d), _p(g))
     return g
 
 

@@ -1,7 +1,8 @@
 // CPU ORACLE (test infrastructure only) for the learned smoother weights.
 //
 // A small MLP maps nine per-row stencil features to a damping weight
-// omega_i in (0, 1] for the l1-Jacobi smoother, s_i = omega_i / d_i
+// omega_i in (0, omega_max] (omega_max 1 by default, at most below 2) for the
+// l1-Jacobi smoother, s_i = omega_i / d_i
 // (Sec. 2.3, l1-Jacobi; the network itself is not in the paper).  Plain FP64
 // statements of: the features, the forward pass, its gradient by the chain
 // rule, an Adam step, and the two-grid loss
@@ -13,7 +14,7 @@
 // coefficients a_ij / a_ii in the order -x, +x, -y, +y, -z, +z of a
 // lexicographic grid (0 where absent), the l1 ratio sum_{j!=i}|a_ij| / a_ii,
 // log(max|a_ij| / min|a_ij|) over present neighbours and the neighbour count
-// / 6; GELU is the exact erf form; omega = max(sigmoid(z), 1e-3).
+// / 6; GELU is the exact erf form; omega = max(omega_max sigmoid(z), 1e-3).
 // Parameter layout (1409 values): W1[32][9], b1[32], W2[32][32], b2[32],
 // W3[32], b3.
 
@@ -42,7 +43,12 @@ struct Act {
   double u1[NH], h1[NH], u2[NH], h2[NH], z, sg, omega;
 };
 
-void forward_row(const double* p, const double* f, Act& a) {
+// omega = max(omega_max * sigmoid(z), OMEGA_MIN): omega_max = 1 is the
+// configuration's clamp to (0, 1]; omega_max in (1, 2) lets the network
+// over-relax while 2 diag(d / omega) - A stays positive definite (d the l1
+// row sums, so diag(d) - A is diagonally dominant): the smoother stays
+// A-convergent and the V-cycle SPD.
+void forward_row(const double* p, const double* f, Act& a, double omega_max) {
   for (int o = 0; o < NH; ++o) {
     double s = p[OFF_B1 + o];
     for (int i = 0; i < NF; ++i) s += p[OFF_W1 + o * NF + i] * f[i];
@@ -59,12 +65,15 @@ void forward_row(const double* p, const double* f, Act& a) {
   for (int i = 0; i < NH; ++i) z += p[OFF_W3 + i] * a.h2[i];
   a.z = z;
   a.sg = sigmoid(z);
-  a.omega = std::max(a.sg, OMEGA_MIN);
+  a.omega = std::max(omega_max * a.sg, OMEGA_MIN);
 }
 
-// Adds d(omega)/d(params) * g to grad.
-void backward_row(const double* p, const double* f, const Act& a, double g, double* grad) {
-  const double dz = a.sg > OMEGA_MIN ? g * a.sg * (1.0 - a.sg) : 0.0;
+// Adds d(omega)/d(params) * g to grad (d omega / dz = omega_max s (1 - s)
+// above the floor, 0 on it).
+void backward_row(const double* p, const double* f, const Act& a, double g, double* grad,
+                  double omega_max) {
+  const double ws = omega_max * a.sg;
+  const double dz = ws > OMEGA_MIN ? g * ws * (1.0 - a.sg) : 0.0;
   grad[OFF_B3] += dz;
   double du2[NH];
   for (int i = 0; i < NH; ++i) {
@@ -185,24 +194,24 @@ void mlp_orc_features(int64_t nx, int64_t ny, int64_t nz, const int64_t* rp, con
   }
 }
 
-void mlp_orc_forward(int64_t n, const double* params, const double* feat, double* omega,
-                     double* z) {
+void mlp_orc_forward(int64_t n, const double* params, const double* feat, double omega_max,
+                     double* omega, double* z) {
   Act a;
   for (int64_t i = 0; i < n; ++i) {
-    forward_row(params, feat + i * NF, a);
+    forward_row(params, feat + i * NF, a, omega_max);
     omega[i] = a.omega;
     if (z) z[i] = a.z;
   }
 }
 
 // grad = sum_i domega_i * d omega_i / d params.
-void mlp_orc_backward(int64_t n, const double* params, const double* feat, const double* domega,
-                      double* grad) {
+void mlp_orc_backward(int64_t n, const double* params, const double* feat, double omega_max,
+                      const double* domega, double* grad) {
   std::fill(grad, grad + NPARAM, 0.0);
   Act a;
   for (int64_t i = 0; i < n; ++i) {
-    forward_row(params, feat + i * NF, a);
-    backward_row(params, feat + i * NF, a, domega[i], grad);
+    forward_row(params, feat + i * NF, a, omega_max);
+    backward_row(params, feat + i * NF, a, domega[i], grad, omega_max);
   }
 }
 

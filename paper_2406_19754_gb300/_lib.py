@@ -94,6 +94,7 @@ SIGNATURES = {
     "mlp_get_params": (C.c_int, [_P, _P]),
     "mlp_set_params": (C.c_int, [_P, _P]),
     "mlp_get_grad": (C.c_int, [_P, _P]),
+    "mlp_set_omega_max": (C.c_int, [_P, C.c_double]),
     "mlp_features": (C.c_int, [C.POINTER(AmgCsr), C.c_int64, C.c_int64, C.c_int64, _P, _P]),
     "mlp_forward": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "mlp_backward": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int, _P]),

@@ -1,5 +1,6 @@
-// Learned smoother weights: a 9 -> 32 -> 32 -> 1 MLP (GELU, sigmoid output
-// clamped to [1e-3, 1)) maps per-row stencil features to the l1-Jacobi
+// Learned smoother weights: a 9 -> 32 -> 32 -> 1 MLP (GELU hidden layers,
+// output omega = max(omega_max sigmoid(z), 1e-3) with omega_max 1 by default
+// or in (1, 2) by mlp_set_omega_max) maps per-row stencil features to the l1-Jacobi
 // damping weight omega_i (s_i = omega_i / d_i, Sec. 2.3 l1-Jacobi; the network
 // is not in the paper).  FP32 weights and activations; gradients are summed
 // in FP64 with a fixed order (per-block partials, then blocks in order), so
@@ -26,6 +27,7 @@ constexpr int BW_BLOCKS_MAX = 1024;
 }  // namespace amg
 
 struct mlp_handle {
+  float omega_max = 1.0f;  // output cap: omega = max(omega_max * sigmoid(z), OMEGA_MIN)
   float* params = nullptr;
   double* grad = nullptr;   // accumulated gradient (FP64)
   double* gpart = nullptr;  // per-block partial gradients
@@ -129,7 +131,8 @@ constexpr int FW_HLD = 36;  // padded activation row (float4-aligned, fewer conf
 
 __global__ void __launch_bounds__(FW_WARPS * 32)
     k_mlp_forward_tiled(int64_t n, const float* __restrict__ params,
-                        const float* __restrict__ feat, float* __restrict__ omega) {
+                        const float* __restrict__ feat, float omega_max,
+                        float* __restrict__ omega) {
   __shared__ __align__(16) float fs[FW_WARPS][32 * FW_FLD];
   __shared__ __align__(16) float hs[FW_WARPS][32 * FW_HLD];
   __shared__ float zs[FW_WARPS][32 * 33];
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32)
 #pragma unroll 8
       for (int i = 0; i < NH; ++i) z = fmaf(w3s[i], zr[lane * 33 + i], z);
       const float sg = 1.0f / (1.0f + expf(-z));
-      omega[r0 + lane] = fmaxf(sg, OMEGA_MIN);
+      omega[r0 + lane] = fmaxf(omega_max * sg, OMEGA_MIN);
     }
     __syncwarp();
   }
@@ -201,7 +204,8 @@ __global__ void __launch_bounds__(FW_WARPS * 32)
 // gpart[block][param].
 __global__ void __launch_bounds__(BW_ROWS)
     k_mlp_backward(int64_t n, const float* __restrict__ params, const float* __restrict__ feat,
-                   const float* __restrict__ domega, double* __restrict__ gpart) {
+                   float omega_max, const float* __restrict__ domega,
+                   double* __restrict__ gpart) {
   __shared__ float p[NPARAM];
   __shared__ float sf[BW_ROWS][NF], sh1[BW_ROWS][NH], sh2[BW_ROWS][NH], sdu1[BW_ROWS][NH],
       sdu2[BW_ROWS][NH], sdz[BW_ROWS];
@@ -221,7 +225,8 @@ __global__ void __launch_bounds__(BW_ROWS)
       for (int k = 0; k < NF; ++k) f[k] = sf[r][k] = feat[i * NF + k];
       RowAct a;
       mlp_row(p, f, a);
-      const float dz = a.sg > OMEGA_MIN ? domega[i] * a.sg * (1.0f - a.sg) : 0.0f;
+      const float ws = omega_max * a.sg;  // d omega / dz = omega_max s (1 - s) above the floor
+      const float dz = ws > OMEGA_MIN ? domega[i] * ws * (1.0f - a.sg) : 0.0f;
       sdz[r] = dz;
       float dh1[NH];
 #pragma unroll
@@ -378,6 +383,12 @@ int mlp_set_params(mlp_handle* M, const float* host) {
   return AMG_OK;
 }
 
+int mlp_set_omega_max(mlp_handle* M, double omega_max) {
+  if (!M || !(omega_max >= 1.0 && omega_max < 2.0)) return AMG_ERR_ARG;
+  M->omega_max = (float)omega_max;
+  return AMG_OK;
+}
+
 int mlp_get_grad(const mlp_handle* M, double* host) {
   if (!M || !host) return AMG_ERR_ARG;
   AMG_CUDA_TRY(cudaMemcpy(host, M->grad, sizeof(double) * NPARAM, cudaMemcpyDeviceToHost));
@@ -402,7 +413,7 @@ int mlp_forward(const mlp_handle* M, int64_t n, const float* feat, float* omega,
   if (n == 0) return AMG_OK;
   // 5 blocks fit an SM (41.6 KB of shared memory each): one wave
   k_mlp_forward_tiled<<<grid_for((n + 31) / 32, FW_WARPS, M->num_sms, 5), FW_WARPS * 32, 0,
-                        (cudaStream_t)stream>>>(n, M->params, feat, omega);
+                        (cudaStream_t)stream>>>(n, M->params, feat, M->omega_max, omega);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -413,7 +424,7 @@ int mlp_backward(mlp_handle* M, int64_t n, const float* feat, const float* domeg
   const int64_t chunks = (n + BW_ROWS - 1) / BW_ROWS;
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, BW_BLOCKS_MAX));
   cudaStream_t s = (cudaStream_t)stream;
-  k_mlp_backward<<<nb, BW_ROWS, 0, s>>>(n, M->params, feat, domega, M->gpart);
+  k_mlp_backward<<<nb, BW_ROWS, 0, s>>>(n, M->params, feat, M->omega_max, domega, M->gpart);
   AMG_LAUNCH_CHECK();
   k_mlp_grad_reduce<<<(NPARAM + 255) / 256, 256, 0, s>>>(nb, M->gpart, M->grad, accumulate);
   AMG_LAUNCH_CHECK();

@@ -1,13 +1,15 @@
 """Learned l1-Jacobi damping weights: binding, training loop and evaluation.
 
 The network (include/amg.h, mlp_*) maps nine stencil features of each row to
-omega_i in (0, 1]; the smoother scale becomes s_i = omega_i / d_i.  Training
+omega_i in (0, omega_max] (omega_max 1 by default, or up to below 2, which
+still keeps the smoother A-convergent); the smoother scale becomes
+s_i = omega_i / d_i.  Training
 minimises the two-grid error-reduction loss (amg_twogrid_loss) over
 generated variable-coefficient diffusion problems with Adam.  Every numeric
 step runs in the library's kernels; this module only sequences the calls.
 
-  python -m paper_2406_19754_gb300.learned train --problems 4000 --out FILE
-  python -m paper_2406_19754_gb300.learned evaluate --weights FILE
+  python -m paper_2406_19754_gb300.learned train --problems 4000 [--omega-max 1.9]
+  python -m paper_2406_19754_gb300.learned evaluate [--omega-max 1.9] [--weights FILE]
 """
 
 from __future__ import annotations
@@ -29,15 +31,33 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "omega_mlp_diffusion48.f32")
 
 
-class Mlp:
-    """The 9 -> 32 -> 32 -> 1 network on the current CUDA device."""
+def weights_path(omega_max: float = 1.0) -> str:
+    """The committed network trained with this output cap (1: DEFAULT_WEIGHTS)."""
+    if omega_max == 1.0:
+        return DEFAULT_WEIGHTS
+    return os.path.join(HERE, "weights", "omega_mlp_diffusion48_wmax%g.f32" % omega_max)
 
-    def __init__(self, seed: int = 0):
+
+class Mlp:
+    """The 9 -> 32 -> 32 -> 1 network on the current CUDA device; its output is
+    omega = max(omega_max * sigmoid(z), 1e-3) with omega_max in [1, 2)."""
+
+    def __init__(self, seed: int = 0, omega_max: float = 1.0):
         self._lib = _lib.load()
         self.nparam = self._lib.mlp_num_params()
         h = C.c_void_p()
         _check(self._lib.mlp_create(C.c_uint64(seed), C.byref(h)), "mlp_create")
         self.h = h
+        self.omega_max = float(omega_max)
+        _check(self._lib.mlp_set_omega_max(self.h, self.omega_max), "mlp_set_omega_max")
+
+    def start_at_plain_smoother(self) -> None:
+        """Output bias so that a zero hidden signal gives omega = 1 (plain
+        l1-Jacobi) under the cap omega_max > 1: sigmoid(b3) = 1 / omega_max."""
+        if self.omega_max > 1.0:
+            p = self.params()
+            p[-1] = np.float32(-np.log(self.omega_max - 1.0))
+            self.set_params(p)
 
     def __del__(self):
         try:
@@ -164,8 +184,11 @@ def train(mlp: Mlp, problems: int, batch: int = 8, lr: float = 1e-3, side: int =
 
 
 def evaluate(weights: str | None, side: int = 256, sigma: float = 2.5, seed: int = 5,
-             precision: str = "f64", tol: float = 1e-8, repeats: int = 3):
-    """Iterations and seconds to tol on side^3 diffusion: omega == 1 vs the network."""
+             precision: str = "f64", tol: float = 1e-8, repeats: int = 3,
+             omega_max: float = 1.0):
+    """Iterations and seconds to tol on side^3 diffusion: omega == 1 (plain
+    l1-Jacobi), the network, and the constant omega equal to the network's
+    mean (does the per-row choice matter, or only the overall step?)."""
     from synthetic import diffusion_problem, uniform01
 
     dev = torch.device("cuda")
@@ -184,7 +207,7 @@ def evaluate(weights: str | None, side: int = 256, sigma: float = 2.5, seed: int
 
     out = {"side": side, "sigma": sigma, "seed": seed, "precision": precision, "tol": tol}
     out["plain"] = dict(zip(("iterations", "seconds", "true_relres"), timed()))
-    mlp = Mlp(0)
+    mlp = Mlp(0, omega_max)
     if weights:
         mlp.load(weights)
     feat = mlp.features(Ad, (side, side, side))
@@ -210,6 +233,10 @@ def evaluate(weights: str | None, side: int = 256, sigma: float = 2.5, seed: int
     out["learned"] = dict(zip(("iterations", "seconds", "true_relres"), timed()))
     out["omega_mean"] = float(om.mean())
     out["omega_min"] = float(om.min())
+    out["omega_max"] = float(om.max())
+    out["omega_cap"] = omega_max
+    H.set_smoother_weights(torch.full_like(om, float(om.mean())))
+    out["constant_mean_omega"] = dict(zip(("iterations", "seconds", "true_relres"), timed()))
     H.close()
     return out
 
@@ -224,15 +251,20 @@ def main(argv=None):
     t.add_argument("--side", type=int, default=TRAIN_SIDE)
     t.add_argument("--seed", type=int, default=0)
     t.add_argument("--workers", type=int, default=8)
-    t.add_argument("--out", default=DEFAULT_WEIGHTS)
+    t.add_argument("--omega-max", type=float, default=1.0,
+                   help="output cap in [1, 2): omega = max(cap * sigmoid(z), 1e-3)")
+    t.add_argument("--out", default=None)
     e = sub.add_parser("evaluate")
-    e.add_argument("--weights", default=DEFAULT_WEIGHTS)
+    e.add_argument("--weights", default=None)
+    e.add_argument("--omega-max", type=float, default=1.0)
     e.add_argument("--side", type=int, default=256)
     e.add_argument("--sigma", type=float, default=2.5)
     e.add_argument("--precision", default="f64")
     a = ap.parse_args(argv)
     if a.cmd == "train":
-        mlp = Mlp(a.seed)
+        a.out = a.out or weights_path(a.omega_max)
+        mlp = Mlp(a.seed, a.omega_max)
+        mlp.start_at_plain_smoother()
         hist = train(mlp, a.problems, a.batch, a.lr, a.side, a.workers,
                      log=lambda s: print(s, flush=True))
         mlp.save(a.out)
@@ -241,8 +273,8 @@ def main(argv=None):
         print(json.dumps({"problems": a.problems, "loss_first100": first,
                           "loss_last100": last, "weights": a.out}), flush=True)
     else:
-        print(json.dumps(evaluate(a.weights, a.side, a.sigma, precision=a.precision)),
-              flush=True)
+        print(json.dumps(evaluate(a.weights or weights_path(a.omega_max), a.side, a.sigma,
+                                  precision=a.precision, omega_max=a.omega_max)), flush=True)
 
 
 if __name__ == "__main__":

@@ -49,6 +49,36 @@ def test_forward_backward_match_oracle(amg, orc, lm):
     np.testing.assert_allclose(m.grad(), 2 * g, rtol=1e-12)
 
 
+@pytest.mark.parametrize("omega_max", [1.5, 1.9])
+def test_forward_backward_with_omega_cap(amg, orc, lm, omega_max):
+    # omega = max(omega_max sigmoid(z), 1e-3): the over-relaxing form of the network
+    A, shape = _problem(), (10, 9, 8)
+    n = 720
+    m = lm.Mlp(4, omega_max)
+    p = (0.5 * standard_normal(22, m.nparam)).astype(np.float32)
+    p[-1] = 3.0  # output bias: most rows above omega = 1
+    m.set_params(p)
+    feat = m.features(amg.csr_to_device(A), shape)
+    om = m.forward(feat).cpu().numpy()
+    f64 = feat.cpu().numpy().astype(np.float64)
+    om_o, _ = orc.mlp_forward(p.astype(np.float64), f64, omega_max)
+    np.testing.assert_allclose(om, om_o, rtol=2e-5, atol=1e-6)
+    assert om.max() > 1.0 and om.max() < omega_max
+    g_out = (uniform01(6, n) - 0.5).astype(np.float32)
+    m.backward(feat, torch.as_tensor(g_out, device="cuda"), accumulate=False)
+    g_o = orc.mlp_backward(p.astype(np.float64), f64, g_out.astype(np.float64), omega_max)
+    assert np.linalg.norm(m.grad() - g_o) <= 1e-5 * np.linalg.norm(g_o)
+
+
+def test_omega_cap_checked(amg, lm):
+    from paper_2406_19754_gb300 import _lib
+
+    m = lm.Mlp(0)
+    for bad in (0.5, 2.0, float("nan")):
+        assert m._lib.mlp_set_omega_max(m.h, bad) == _lib.AMG_ERR_ARG
+    assert m._lib.mlp_set_omega_max(m.h, 1.9) == 0
+
+
 def test_adam_matches_oracle(amg, orc, lm):
     m = lm.Mlp(2)
     p0 = m.params().astype(np.float64)
@@ -135,3 +165,39 @@ def test_trained_network_against_plain_smoother(amg, lm):
                                               il["iterations"], float(om.mean())))
         assert loss_l <= loss_p + 1e-3 * abs(loss_p)
         assert il["iterations"] <= ip["iterations"] + 1
+
+
+def test_over_relaxing_network_against_plain_smoother(amg, lm):
+    """The network trained with the output cap omega_max = 1.9 (the same 4000
+    problems; omega may exceed 1) on held-out problems: two-grid loss and PCG
+    iterations against plain l1-Jacobi and against the constant omega equal
+    to the network's mean.  The two-grid loss the network was trained on must
+    improve clearly; PCG iterations must not get worse; all numbers are
+    printed."""
+    from synthetic import diffusion_problem
+
+    m = lm.Mlp(0, 1.9)
+    m.load(lm.weights_path(1.9))
+    side = 40
+    n = side ** 3
+    for sigma, seed in ((2.5, 5), (1.0, 77), (0.0, 78)):
+        Ad = amg.csr_to_device(diffusion_problem(side, sigma, 8.0, seed))
+        H = amg.Hierarchy(*Ad)
+        e0 = torch.as_tensor(standard_normal(seed + 7919, 4 * n).reshape(4, n), device="cuda")
+        b = torch.as_tensor(uniform01(seed + 1, n), device="cuda")
+        loss_p, _ = lm.twogrid_loss(H, e0, 2, gradient=False)
+        _, ip = H.pcg(b, tol=1e-8)
+        om = m.forward(m.features(Ad, (side, side, side)))
+        assert float(om.min()) > 0.0 and float(om.max()) < 1.9
+        H.set_smoother_weights(om)
+        loss_l, _ = lm.twogrid_loss(H, e0, 2, gradient=False)
+        _, il = H.pcg(b, tol=1e-8)
+        H.set_smoother_weights(torch.full_like(om, float(om.mean())))
+        loss_c, _ = lm.twogrid_loss(H, e0, 2, gradient=False)
+        _, ic = H.pcg(b, tol=1e-8)
+        print("cap 1.9, sigma %.1f: two-grid loss plain %.5f learned %.5f constant %.5f; PCG "
+              "iterations plain %d learned %d constant %d; omega mean %.4f min %.4f max %.4f"
+              % (sigma, loss_p, loss_l, loss_c, ip["iterations"], il["iterations"],
+                 ic["iterations"], float(om.mean()), float(om.min()), float(om.max())))
+        assert loss_l < loss_p - 0.05 * abs(loss_p)
+        assert il["iterations"] <= ip["iterations"]

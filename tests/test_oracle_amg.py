@@ -263,7 +263,9 @@ def _vcycle_dense(orc, H, n):
 def test_vcycle_symmetric_positive_definite(orc, side, max_coarse):
     A = poisson3d(side)
     n = side ** 3
-    for omega in (None, 0.05 + 0.95 * uniform01(side, n)):
+    # plain l1-Jacobi, random under-relaxation, and random over-relaxation below 2
+    # (2 diag(d/omega) - A > 0 keeps the smoother A-convergent, so B stays SPD)
+    for omega in (None, 0.05 + 0.95 * uniform01(side, n), 1.0 + 0.95 * uniform01(side + 1, n)):
         H = orc.Hierarchy(A, max_coarse=max_coarse, omega=omega)
         assert H.levels >= 2
         B = _vcycle_dense(orc, H, n)

@@ -32,13 +32,13 @@ def _torch_mlp(p):
     return W1, b1, W2, b2, W3, b3
 
 
-def _torch_forward(params, feat):
+def _torch_forward(params, feat, omega_max=1.0):
     W1, b1, W2, b2, W3, b3 = _torch_mlp(params)
     f = torch.as_tensor(feat, dtype=torch.float64)
     h1 = torch.nn.functional.gelu(f @ W1.T + b1)
     h2 = torch.nn.functional.gelu(h1 @ W2.T + b2)
     z = h2 @ W3 + b3
-    return torch.clamp(torch.sigmoid(z), min=1e-3)
+    return torch.clamp(omega_max * torch.sigmoid(z), min=1e-3)
 
 
 def test_features_poisson_closed_form(orc):
@@ -75,6 +75,25 @@ def test_forward_matches_torch(orc):
     assert np.all(om >= 1e-3) and np.all(om < 1.0)
     om0, z0 = orc.mlp_forward(np.zeros(1409), feat)  # zero network: sigmoid(0)
     assert np.all(om0 == 0.5) and np.all(z0 == 0.0)
+
+
+@pytest.mark.parametrize("omega_max", [1.5, 1.9])
+def test_forward_backward_with_omega_cap(orc, omega_max):
+    # omega = max(omega_max sigmoid(z), 1e-3): over-relaxation up to omega_max < 2
+    feat = orc.mlp_features(diffusion3d(np.exp(gaussian_field((5, 6, 4), 2.0, 2.0, 9))),
+                            (5, 6, 4))
+    p = _params(14)
+    om, _ = orc.mlp_forward(p, feat, omega_max)
+    want = _torch_forward(p, feat, omega_max).numpy()
+    np.testing.assert_allclose(om, want, rtol=1e-13, atol=1e-15)
+    assert np.all(om >= 1e-3) and np.all(om < omega_max) and om.max() > 1.0
+    om0, _ = orc.mlp_forward(np.zeros(1409), feat, omega_max)
+    assert np.all(om0 == 0.5 * omega_max)  # zero network: omega_max sigmoid(0)
+    g_out = uniform01(15, len(om)) - 0.5
+    grad = orc.mlp_backward(p, feat, g_out, omega_max)
+    pt = torch.as_tensor(p, dtype=torch.float64).requires_grad_(True)
+    (_torch_forward(pt, feat, omega_max) * torch.as_tensor(g_out)).sum().backward()
+    np.testing.assert_allclose(grad, pt.grad.numpy(), rtol=1e-10, atol=1e-14)
 
 
 def test_backward_matches_autograd_and_differences(orc):
@@ -131,6 +150,21 @@ def test_two_grid_loss_matches_dense(orc):
         want += math.log(math.sqrt(eK @ M @ eK) / math.sqrt(e @ M @ e)) / 2
     assert math.isclose(loss, want / 2, rel_tol=1e-11)
     assert loss < 0.0  # omega in (0, 1]: each cycle contracts the A-norm
+
+
+def test_two_grid_loss_over_relaxed_contracts(orc):
+    # omega in (1, 2): 2 diag(d / omega) - A = (2/omega - 1) diag(d) + (diag(d) - A) > 0
+    # keeps S = I - diag(omega / d) A an A-norm contraction, so the loss stays negative
+    A, agg, Ac = _two_grid_setup(orc)
+    n = len(agg)
+    om = 1.0 + 0.95 * uniform01(9, n)
+    M = dense(A)
+    d = np.abs(M).sum(axis=1)
+    ev = np.linalg.eigvals((om / d)[:, None] * M).real  # eig(diag(s) A) in (0, 2)
+    assert ev.min() > 0.0 and ev.max() < 2.0
+    e0 = standard_normal(10, 2 * n).reshape(2, n)
+    loss, _ = orc.twogrid_loss(A, agg, Ac, om, e0, K=2)
+    assert loss < 0.0
 
 
 def test_two_grid_gradient_central_differences(orc):
