@@ -365,13 +365,16 @@ SM_COUNT, SM_MAX_GHZ = 152, 2.07
 def fp64_pipe(H, level, kind, ms, a):
     """FP64 instructions of one pre- or post-smoother launch of an FP64
     hierarchy (one per stored entry, plus per row: 1 for r = b - acc, 3 for
-    y, e and z) against the FP64 pipe's peak: those kernels are co-limited by
-    HBM and by GB300's reduced-rate FP64 arithmetic."""
+    y, e and z, and on level 0 one more for (r, z)) against the FP64 pipe's
+    peak: those kernels are co-limited by HBM and by GB300's reduced-rate FP64
+    arithmetic."""
     if a.precision != "f64" or kind not in ("pre", "post"):
         return None
     n = H.level_info(level)[0]
     slots = H.level_layout(level, ap=(kind == "post"))["slots"]
-    ops = slots + (1 if kind == "pre" else 3) * n
+    # level 0's post-smoother also forms (r, z) for PCG's beta (one FMA a row)
+    per_row = 1 if kind == "pre" else (4 if level == 0 else 3)
+    ops = slots + per_row * n
     peak = FP64_OPS_PER_SM_CLOCK * SM_COUNT * SM_MAX_GHZ * 1e9
     rate = ops / (ms * 1e-3)
     return {"ops_per_launch": ops, "ops_per_s": rate, "peak_ops_per_s": peak,
@@ -693,6 +696,9 @@ def run_ours(a):
                        "prolongator_filter": a.prolongator_filter,
                        "tail_rows": int(H.opts.tail_rows),
                        "level0_layout": lay,
+                       "level_layouts": [[H.level_layout(l)["slice_height"],
+                                          H.level_layout(l)["threads_per_row"]]
+                                         for l in range(nl)],
                        "pcg_graph": a.graph,
                        "stream_ring": int(H.opts.stream_ring),
                        "level0_ap_layout": H.level_layout(0, ap=True) if nl > 1 else None,

@@ -83,13 +83,22 @@ typedef struct amg_options {
                             default 8192, at most 16384 */
   int precision;         /* AMG_PREC_F64 (default) or AMG_PREC_F32 */
   int bf16_from_level;   /* with F32: levels >= this keep BF16 values; 0 = off */
-  int slice_height;      /* sliced-ELL rows per slice 1/2/4/8/16/32 (slice height
-                            x threads per row = 32); 0 = default */
-  int threads_per_row;   /* 1/2/4/8/16/32 threads per row; 0 = default: 1 (32
-                            rows a slice), more on levels whose rows average
-                            64 entries or more (about one thread per 16) */
-  int autotune;          /* 1: choose slice height / threads per row per level by
-                            timing the kernels at setup */
+  int slice_height;      /* sliced-ELL rows per slice 1/2/4/8/16/32/64; 0 =
+                            default: 32 / threads_per_row (one slice per warp).
+                            Any other height decouples the slices from the
+                            warps (a warp covers 32 / threads_per_row rows of
+                            one or several slices); not for batched systems,
+                            which always use 32 / threads_per_row */
+  int threads_per_row;   /* 1/2/4/8/16/32 threads per row; 0 = default: 32 /
+                            slice_height if that is set, else 1, more on levels
+                            whose rows average 64 entries or more (about one
+                            thread per 16) */
+  int autotune;          /* 1: choose slice height and threads per row per level
+                            by timing the level's kernels at setup: threads per
+                            row 1/2/4/8 (16, 32 on wide rows) x slice heights
+                            8/16/32/64 and 32 / threads per row (batched systems:
+                            the latter only); choices are kept for the process,
+                            keyed by rows, entries per row and value type */
   int64_t tail_rows;     /* levels (other than level 0) with at most this many
                             rows, and the coarsest solve, run as one persistent
                             launch instead of one launch per step: one CTA when

@@ -93,9 +93,9 @@ static int check_options(const amg_options& o) {
   if (o.coarse_maxit < 0 || o.coarse_maxit > 100000 || !(o.coarse_tol >= 0.0))
     return AMG_ERR_ARG;
   const int C = o.slice_height, t = o.threads_per_row;
-  if (C != 0 && C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32) return AMG_ERR_ARG;
+  if (C != 0 && C != 1 && C != 2 && C != 4 && C != 8 && C != 16 && C != 32 && C != 64)
+    return AMG_ERR_ARG;
   if (t != 0 && t != 1 && t != 2 && t != 4 && t != 8 && t != 16 && t != 32) return AMG_ERR_ARG;
-  if (C && t && C * t != 32) return AMG_ERR_ARG;
   return AMG_OK;
 }
 

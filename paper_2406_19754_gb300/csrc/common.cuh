@@ -83,6 +83,11 @@ struct Sell {
 template <typename V>
 struct SellView {
   int64_t n, nslices;
+  // Warp row-groups of the one-warp-per-group kernels (sellk.cuh): 32/tpr
+  // consecutive rows each; the slices themselves when the slice height C is
+  // 32/tpr, more or fewer groups than slices otherwise (C in {4, ..., 64}).
+  int64_t ngroups;
+  int C;
   const int64_t* sliceptr;
   const int32_t* col;
   const V* val;

@@ -102,8 +102,9 @@ __device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, i
   }
 }
 
-// Slices of at most SL_MAXW ELL columns (7-point rows, and their A P) are
-// staged in shared memory by the warp: column indices and values come in with
+// Slices of at most SL_MAXW ELL columns and SL_CAP entries (7-point rows, and
+// their A P, in slices of up to 32 rows) are staged in shared memory by the
+// warp: column indices and values come in with
 // coalesced loads, then every row of the slice reads its entries from there
 // as broadcasts and issues all of its gathers at once, so a row costs one
 // gather latency instead of a chain of index load, gather, next group.
@@ -119,7 +120,7 @@ __device__ __forceinline__ bool stage_slice(const SellView<V>& A, int64_t sl, in
                                             int32_t* scol, T* sval, int& w) {
   const int64_t beg = __ldg(A.sliceptr + sl);
   w = (int)((__ldg(A.sliceptr + sl + 1) - beg) / C);
-  if (w > SL_MAXW) return false;
+  if (w > SL_MAXW || w * C > SL_CAP) return false;  // slices of 64 rows fit fewer columns
   for (int e = lane; e < w * C; e += 32) {
     scol[e] = __ldg(A.col + beg + e);
     sval[e] = to_f(__ldg(A.val + beg + e), T(0));

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double d[2] = {0.0, 0.0};
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.ngroups;
        sl += nw) {
     const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(x + j); });
     const int64_t i = lane_row(A, sl, ln);
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double d[1] = {0.0};
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.ngroups;
        sl += nw) {
     const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(p + j); });
     const int64_t i = lane_row(A, sl, ln);
@@ -194,7 +194,7 @@ __global__ void k_x_pending(int64_t n, double* __restrict__ x, const double* __r
 static int launch_residual(const amg_handle* H, int mode, const double* b, const double* x,
                            double* r, cudaStream_t s) {
   const Level& L = H->L[0];
-  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const int grid = sell_grid(sell_groups(L.A), H->num_sms);
   const SellView<double> v = view<double>(L.A, L.A.v64);
   if (mode == 0) {
     AMG_DISPATCH_TPR(sell_code(L.A), (k_residual<TPR, 0><<<grid, SELL_BLOCK, 0, s>>>(
@@ -209,7 +209,7 @@ static int launch_residual(const amg_handle* H, int mode, const double* b, const
 
 static int launch_spmv_dot(const amg_handle* H, cudaStream_t s) {
   const Level& L = H->L[0];
-  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const int grid = sell_grid(sell_groups(L.A), H->num_sms);
   const SellView<double> v = view<double>(L.A, L.A.v64);
   if (H->opt.stream_ring && !H->batched) {
     RingGeom g = ring_plan(L.A, 8, ring_stages(H), RingRows());

@@ -30,7 +30,7 @@ __device__ __forceinline__ void slice_rows(int64_t s, int C, int64_t n, const in
 // (if non-null) and returns their count, or -1 once it exceeds `cap`.
 __device__ int slice_offsets(int64_t rb, int64_t re, const int64_t* rowptr, const int32_t* col,
                              int cap, int32_t* u) {
-  int pos[32];
+  int pos[64];  // rows of the slice: at most the largest slice height
   const int m = (int)(re - rb);
   for (int r = 0; r < m; ++r) pos[r] = 0;
   int cnt = 0;
@@ -178,7 +178,11 @@ int sell_from_csr(Arena& ar, int64_t n, int64_t ncols, const int64_t* rowptr, co
                   const double* val, int C, int tpr, Sell& out, cudaStream_t s,
                   const std::vector<int64_t>* sys_off, bool compress) {
   if (n <= 0 || ncols <= 0) return AMG_ERR_ARG;
-  if (C * tpr != 32) return AMG_ERR_ARG;
+  // heights 1..64 and 1..32 threads per row, powers of two; batched systems
+  // keep one slice per warp (slice height x threads per row = 32)
+  if (C < 1 || C > 64 || (C & (C - 1)) || tpr < 1 || tpr > 32 || (tpr & (tpr - 1)))
+    return AMG_ERR_ARG;
+  if (sys_off && sys_off->size() >= 2 && C * tpr != 32) return AMG_ERR_ARG;
   out.n = n;
   out.C = C;
   out.tpr = tpr;
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
              double* __restrict__ y) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < A.nslices;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < A.ngroups;
        s += nw) {
     double acc = sell_row<TPR, double>(A, s, ln, [&](int j) { return __ldg(x + j); });
     const int64_t i = lane_row(A, s, ln);
@@ -296,7 +300,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
 
 int sell_spmv64(const Sell& A, double alpha, const double* x, double beta, double* y,
                 int num_sms, cudaStream_t s) {
-  const int grid = sell_grid(A.nslices, num_sms);
+  const int grid = sell_grid(sell_groups(A), num_sms);
   SellView<double> v = view(A, (const double*)A.v64);
   AMG_DISPATCH_TPR(sell_code(A),
                    (k_spmv64<TPR><<<grid, SELL_BLOCK, 0, s>>>(v, alpha, x, beta, y)));

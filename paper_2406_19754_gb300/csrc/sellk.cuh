@@ -1,9 +1,11 @@
 // Sliced-ELL row traversal shared by the SpMV, smoother and PCG kernels.
 //
-// Mapping: one warp per slice, C * TPR == 32.  Lane = t * C + r handles row r
-// of the slice and the entries k = t, t + TPR, ... of that row, so every load
-// instruction of a warp touches C * TPR consecutive entries of the
-// column-major slice (fully coalesced).  The TPR partial sums of a row are
+// Mapping: one warp per group of R = 32 / TPR consecutive rows (a slice, when
+// the slice height C is R).  Lane = t * R + r handles row r of the group and
+// the entries k = t, t + TPR, ... of that row, so with C == R every load
+// instruction of a warp touches 32 consecutive entries of the column-major
+// slice (fully coalesced); with C != R (the autotuner's decoupled layouts) the
+// lanes of a row group read C-row runs of one or several slices.  The TPR partial sums of a row are
 // combined with xor-shuffles (fixed order).  Matrix values and column indices
 // are streamed with evict-first loads; the gathered vectors stay in L2.
 #pragma once
@@ -35,17 +37,53 @@ struct Lanes {
   }
 };
 
-// sum_k a_{row,k} * g(col_{row,k}) over the row's entries, accumulated in AccT.
-// Compressed columns (SELL_D16 in the layout code; A.d16 set) give the same j
-// for every slot, so the sum is the same bits either way.
+// sum_k a_{row,k} * g(col_{row,k}) over the entries of this lane's row in
+// warp row-group s (32/TPR rows), accumulated in AccT.  When the slice height
+// is 32/TPR (one slice per group, every layout but the autotuner's decoupled
+// ones, and every batched one) the group is the slice; otherwise each lane
+// finds its row's own slice (row i: slice i / C, slot k at
+// sliceptr + k C + i mod C), and the row's entries are visited in the same
+// order.  Compressed columns (SELL_D16 in the layout code; A.d16 set) give
+// the same j for every slot, so the sum is the same bits either way.
 template <int TPR, typename AccT, typename V, typename G>
 __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const Lanes<TPR>& ln,
                                          G g) {
   constexpr int C = Lanes<TPR>::C, W = Lanes<TPR>::W;
+  AccT acc = AccT(0);
+  if (!A.row0 && A.C != C) {
+    const int64_t i = s * C + ln.r;
+    if (i < A.n) {
+      const int64_t sl = i / A.C;
+      const int64_t b0 = __ldg(A.sliceptr + sl);
+      const int w = (int)((__ldg(A.sliceptr + sl + 1) - b0) / A.C);
+      const int64_t beg = b0 + (i - sl * A.C);
+      const V* vp = A.val + beg;
+      if constexpr (Lanes<TPR>::D16) {
+        const uint16_t* dp = A.d16 + beg;
+        const int32_t* bp = A.kbase + b0 / A.C;
+#pragma unroll 4
+        for (int k = ln.t; k < w; k += W) {
+          const int j = __ldg(bp + k) + (int)ld_stream(dp + (int64_t)k * A.C);
+          const AccT a = to_f(ld_stream(vp + (int64_t)k * A.C), AccT(0));
+          acc = fma(a, g(j), acc);
+        }
+      } else {
+        const int32_t* cp = A.col + beg;
+#pragma unroll 4
+        for (int k = ln.t; k < w; k += W) {
+          const int j = ld_stream(cp + (int64_t)k * A.C);
+          const AccT a = to_f(ld_stream(vp + (int64_t)k * A.C), AccT(0));
+          acc = fma(a, g(j), acc);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = C; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+  }
   const int64_t beg = __ldg(A.sliceptr + s);
   const int w = (int)((__ldg(A.sliceptr + s + 1) - beg) / C);
   const V* vp = A.val + beg + ln.r;
-  AccT acc = AccT(0);
   if constexpr (Lanes<TPR>::D16) {
     const uint16_t* dp = A.d16 + beg + ln.r;
     const int32_t* bp = A.kbase + beg / C;
@@ -94,11 +132,21 @@ __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const 
 
 inline int sell_code(const Sell& A) { return A.tpr | (A.d16 ? SELL_D16 : 0); }
 
+// Warp row-groups of 32/tpr rows that the one-warp-per-group kernels iterate
+// over A (see SellView::ngroups).
+inline int64_t sell_groups(const Sell& A) {
+  const int R = 32 / A.tpr;
+  if (A.row0 || A.C == R) return A.nslices;
+  return (A.n + R - 1) / R;
+}
+
 template <typename V>
 inline SellView<V> view(const Sell& A, const V* val) {
   SellView<V> v;
   v.n = A.n;
   v.nslices = A.nslices;
+  v.ngroups = sell_groups(A);
+  v.C = A.C;
   v.sliceptr = A.sliceptr;
   v.col = A.col;
   v.val = val;
@@ -110,7 +158,8 @@ inline SellView<V> view(const Sell& A, const V* val) {
   return v;
 }
 
-// Row handled by this lane in slice sl, or -1 (padding lane / sub-row lane).
+// Row handled by this lane in warp row-group sl, or -1 (padding lane /
+// sub-row lane).
 template <int TPR, typename V>
 __device__ __forceinline__ int64_t lane_row(const SellView<V>& A, int64_t sl,
                                             const Lanes<TPR>& ln) {
@@ -119,10 +168,10 @@ __device__ __forceinline__ int64_t lane_row(const SellView<V>& A, int64_t sl,
   return (ln.t == 0 && i < A.rend(sl, C)) ? i : -1;
 }
 
-// Grid for one-warp-per-slice kernels: enough blocks to fill the GPU, capped
-// by the slice count (grid-stride loop inside).
-inline int sell_grid(int64_t nslices, int num_sms, int blocks_per_sm = 8) {
-  return grid_for(nslices * 32, SELL_BLOCK, num_sms, blocks_per_sm);
+// Grid for one-warp-per-group kernels: enough blocks to fill the GPU, capped
+// by the group count (grid-stride loop inside).
+inline int sell_grid(int64_t ngroups, int num_sms, int blocks_per_sm = 8) {
+  return grid_for(ngroups * 32, SELL_BLOCK, num_sms, blocks_per_sm);
 }
 
 }  // namespace amg

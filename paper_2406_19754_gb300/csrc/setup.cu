@@ -964,9 +964,10 @@ static int build_smoothed_ops(Arena& ar, Level& L, bool compress, cudaStream_t s
 }
 
 // ------------------------------------------------------------------ autotuner
-// Threads per row (and so slice height 32/tpr) per level, chosen by timing the
-// level's smoother kernels in every layout; choices are remembered for the
-// process, keyed by (rows, 10 x entries per row, value type, batched).
+// Slice height C and threads per row per level, chosen by timing the level's
+// smoother kernels (and the level-0 SpMV) in every candidate layout; choices
+// are remembered for the process, keyed by (rows, 10 x entries per row, value
+// type, batched, compressed columns).
 
 struct TuneKey {
   int64_t n;
@@ -983,20 +984,38 @@ struct TuneKey {
   }
 };
 
-static std::mutex g_tune_mu;
-static std::map<TuneKey, int> g_tune;
+struct Layout {
+  int C, tpr;
+};
 
-static bool tune_lookup(const TuneKey& k, int* tpr) {
+static std::mutex g_tune_mu;
+static std::map<TuneKey, Layout> g_tune;
+
+static bool tune_lookup(const TuneKey& k, Layout* lay) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find(k);
   if (it == g_tune.end()) return false;
-  *tpr = it->second;
+  *lay = it->second;
   return true;
 }
 
-static void tune_store(const TuneKey& k, int tpr) {
+static void tune_store(const TuneKey& k, Layout lay) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tune[k] = tpr;
+  g_tune[k] = lay;
+}
+
+// Candidate layouts of a level: threads per row 1, 2, 4, 8 (and 16, 32 when
+// rows average 64 entries or more) with slice height 32 / tpr, and, unless
+// the slices must follow the warps (batched systems), heights 8, 16, 32, 64.
+static std::vector<Layout> tune_candidates(bool wide, bool batched) {
+  std::vector<Layout> c;
+  for (int tpr = 1; tpr <= (wide ? 32 : 8); tpr <<= 1) {
+    c.push_back({32 / tpr, tpr});
+    if (batched) continue;
+    for (int C : {8, 16, 32, 64})
+      if (C != 32 / tpr) c.push_back({C, tpr});
+  }
+  return c;
 }
 
 static void release_sell(Arena& ar, Sell& A) {
@@ -1287,9 +1306,9 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
     const int32_t* ci = l == 0 ? A->col : L.col;
     const double* va = l == 0 ? A->val : L.val;
     const bool smooth = l + 1 < H->L.size();  // a level with a coarser one
-    auto build = [&](int tpr) -> int {
+    auto build = [&](Layout lay) -> int {
       const bool cmp = o.compress_columns != 0;
-      AMG_TRY(sell_from_csr(ar, L.n, L.n, rp, ci, va, 32 / tpr, tpr, L.A, s,
+      AMG_TRY(sell_from_csr(ar, L.n, L.n, rp, ci, va, lay.C, lay.tpr, L.A, s,
                             H->batched ? &L.sys_off : nullptr, cmp));
       if (smooth) {
         AMG_TRY(build_ah(ar, L, sms, s));
@@ -1300,32 +1319,45 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
       }
       return AMG_OK;
     };
-    int tpr = o.threads_per_row > 0 ? o.threads_per_row
+    // threads per row: the option, else 32 / slice height, else by row length;
+    // slice height: the option, else 32 / threads per row (always that for
+    // batched systems, whose slices restart at every system)
+    Layout lay;
+    lay.tpr = o.threads_per_row > 0 ? o.threads_per_row
+              : o.slice_height > 0  ? std::max(1, 32 / o.slice_height)
                                     : auto_tpr(L.n, L.nnz, L.vstore == VAL_F64);
-    if (o.slice_height > 0) tpr = 32 / o.slice_height;
+    lay.C = o.slice_height > 0 && !H->batched ? o.slice_height : 32 / lay.tpr;
     if (like) {  // the assembled hierarchy's layout, tuned or not
-      tpr = like->L[l].A.tpr;
-    } else if (o.autotune && smooth) {
+      lay = {like->L[l].A.C, like->L[l].A.tpr};
+    } else if (o.autotune && smooth && (l == 0 || L.n > o.tail_rows)) {
+      // (levels that the persistent small-level launch runs are not tuned:
+      // their per-level kernels never run in a V-cycle)
       const TuneKey key{L.n, (int)(10 * L.nnz / L.n), L.vstore, H->batched,
                         o.compress_columns != 0};
-      if (!tune_lookup(key, &tpr)) {
-        float best = 1e30f;
-        const int ncand = L.nnz >= 64 * L.n ? 6 : 4;  // 16 and 32 for wide rows
-        for (int k = 0; k < ncand; ++k) {
-          const int cand = 1 << k;
+      if (!tune_lookup(key, &lay)) {
+        const Layout def = lay;
+        float best = 1e30f, def_ms = 1e30f;
+        for (const Layout cand : tune_candidates(L.nnz >= 64 * L.n, H->batched)) {
           AMG_TRY(build(cand));
+          // enough repetitions for about 2 ms of kernel time (small levels
+          // take microseconds a launch), at least 3, at most 200
           float ms = 0.f;
           AMG_TRY(time_level(H, (int)l, 3, tb, tz, &ms, s));
+          const int reps = (int)std::min(200.0f, std::max(3.0f, 2.0f / std::max(ms, 1e-4f)));
+          if (reps > 3) AMG_TRY(time_level(H, (int)l, reps, tb, tz, &ms, s));
+          if (cand.C == def.C && cand.tpr == def.tpr) def_ms = ms;
           if (ms < best) {
             best = ms;
-            tpr = cand;
+            lay = cand;
           }
           release_level_ops(ar, L);
         }
-        tune_store(key, tpr);
+        // the default layout unless another is clearly faster (3%)
+        if (def_ms < 1e30f && best > 0.97f * def_ms) lay = def;
+        tune_store(key, lay);
       }
     }
-    AMG_TRY(build(tpr));
+    AMG_TRY(build(lay));
   }
   ar.release(tb);
   ar.release(tz);

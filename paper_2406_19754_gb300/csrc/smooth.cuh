@@ -230,7 +230,7 @@ __device__ void coarse_pcg_cta(const SellView<double>& A, const double* sinv, co
     const Lanes<TPR> ln;
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int k = 0; k < maxit; ++k) {
-      for (int64_t sl = warp; sl < A.nslices; sl += nwarps) {
+      for (int64_t sl = warp; sl < A.ngroups; sl += nwarps) {
         const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return p[j]; });
         const int64_t i = lane_row(A, sl, ln);
         if (i >= 0) q[i] = acc;

@@ -41,7 +41,8 @@ constexpr unsigned long long TAIL_WAIT_NS = 1000000000ull;        // 1 s
 constexpr unsigned long long TAIL_DEBUG_WAIT_NS = 10000000ull;    // 10 ms (test hook)
 
 struct SellDesc {
-  int64_t n, nslices;
+  int64_t n, nslices, ngroups;
+  int C;
   const int64_t* sliceptr;
   const int32_t* col;
   const void* val;
@@ -105,6 +106,8 @@ __device__ __forceinline__ SellView<V> dview(const SellDesc& d) {
   SellView<V> v;
   v.n = d.n;
   v.nslices = d.nslices;
+  v.ngroups = d.ngroups;
+  v.C = d.C;
   v.sliceptr = d.sliceptr;
   v.col = d.col;
   v.val = (const V*)d.val;
@@ -186,7 +189,7 @@ template <int TPR, typename Ld, typename T, typename V>
 __device__ __forceinline__ void pre_rows(const TailLevel& L, int64_t gw, int64_t nw) {
   const Lanes<TPR> ln;
   const SellView<V> Ah = dview<V>(L.A);
-  for (int64_t sl = gw; sl < Ah.nslices; sl += nw)
+  for (int64_t sl = gw; sl < Ah.ngroups; sl += nw)
     if (Ah.live(sl)) pre_slice<TPR, Ld>(Ah, (const T*)L.b, (T*)L.r, sl, ln);
 }
 
@@ -195,7 +198,7 @@ __device__ __forceinline__ void post_rows(const TailLevel& L, const T* r, const 
                                           int64_t gw, int64_t nw) {
   const Lanes<TPR> ln;
   const SellView<V> AP = dview<V>(L.AP);
-  for (int64_t sl = gw; sl < AP.nslices; sl += nw) {
+  for (int64_t sl = gw; sl < AP.ngroups; sl += nw) {
     if (!AP.live(sl)) continue;
     T z;
     post_slice<TPR, Ld>(AP, (const T*)L.b, (const T*)L.s, r, L.agg, (const T*)L.xc, (T*)L.x,
@@ -210,7 +213,7 @@ __device__ __forceinline__ void sweep_rows(const TailLevel& L, const T* r, T* r_
   const Lanes<TPR> ln;
   const SellView<V> Ah = dview<V>(L.A);
   const T* s = (const T*)L.s;
-  for (int64_t sl = gw; sl < Ah.nslices; sl += nw) {
+  for (int64_t sl = gw; sl < Ah.ngroups; sl += nw) {
     if (!Ah.live(sl)) continue;
     T ri = T(0), rn = T(0);
     int64_t i;
@@ -377,6 +380,8 @@ static SellDesc desc(const Sell& A, const void* val, const int* act) {
   SellDesc d;
   d.n = A.n;
   d.nslices = A.nslices;
+  d.ngroups = sell_groups(A);
+  d.C = A.C;
   d.sliceptr = A.sliceptr;
   d.col = A.col;
   d.val = val;
@@ -489,7 +494,7 @@ int tail_launch(const amg_handle* H, int lt, cudaStream_t s, const int* act) {
     d.nu = L.nu;
     d.r2 = L.r2;
     d.xp = L.xp;
-    warps = std::max({warps, L.A.nslices, L.AP.nslices, (L.nc + 31) / 32});
+    warps = std::max({warps, sell_groups(L.A), sell_groups(L.AP), (L.nc + 31) / 32});
   }
   const Level& Lc = H->L[nl - 1];
   const int64_t m = largest_coarse_block(H);

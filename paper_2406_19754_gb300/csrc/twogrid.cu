@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
                 double* __restrict__ out, double* __restrict__ Ax) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.ngroups;
        sl += nw) {
     const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(x + j); });
     const int64_t i = lane_row(A, sl, ln);
@@ -161,7 +161,7 @@ int twogrid_loss(amg_handle* H, int nsamples, int K, const double* e0, double* l
   const Level& L0 = H->L[0];
   const int64_t n = w.n;
   const SellView<double> A = view<double>(L0.A, L0.A.v64);
-  const int gs = sell_grid(L0.A.nslices, H->num_sms);
+  const int gs = sell_grid(sell_groups(L0.A), H->num_sms);
   const int gv = grid_for(n, 256, H->num_sms, 8);
   const double* sv = L0.s64;
   pcg_options po;

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_pre(SellView<V> Ah, const BT* __restrict__ b, T* __restrict__ r) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.ngroups;
        sl += nw)
     if (Ah.live(sl)) pre_slice<TPR, LdRO>(Ah, b, r, sl, ln);
 }
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
 #pragma unroll
     for (int k = 0; k < NDOT; ++k) dacc[k][threadIdx.x] = 0.0;
   }
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.ngroups;
        sl += nw) {
     if (!AP.live(sl)) continue;  // warp-uniform
     XT zi;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
               const T* __restrict__ xp, XT* __restrict__ x, T* __restrict__ e) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AQ.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AQ.ngroups;
        sl += nw) {
     const T aq = sell_row<TPR, T>(AQ, sl, ln, [&](int J) { return __ldg(xc + J); });
     const T px = sell_row<TPR, T>(P, sl, ln, [&](int J) { return __ldg(xc + J); });
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_restrict_sm(SellView<V> R, const T* __restrict__ r, T* __restrict__ bc) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < R.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < R.ngroups;
        sl += nw) {
     const T acc = sell_row<TPR, T>(R, sl, ln, [&](int j) { return __ldg(r + j); });
     const int64_t I = lane_row(R, sl, ln);
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
                 const T* __restrict__ r, T* __restrict__ r_out, T* __restrict__ x, int first) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.ngroups;
        sl += nw) {
     if (!Ah.live(sl)) continue;
     T ri = T(0), rn = T(0);
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
                  T* __restrict__ r_out, YT* __restrict__ y) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.ngroups;
        sl += nw) {
     if (!Ah.live(sl)) continue;
     T ri = T(0), rn = T(0);
@@ -310,7 +310,7 @@ __global__ void k_slice_dots(SellView<double> A, const double* r, const double* 
                              const double* q, double* slice_part) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.ngroups;
        sl += nw) {
     const int64_t b0 = A.rbeg(sl, 32), b1 = A.rend(sl, 32);
     double d0 = 0.0, d1 = 0.0;
@@ -333,7 +333,7 @@ static int slice_dots(const amg_handle* H, const double* r, const double* z, con
   const Level& L = H->L[0];
   if (!L.A.row0) return AMG_ERR_ARG;
   const SellView<double> v = view<double>(L.A, L.A.v64);
-  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const int grid = sell_grid(sell_groups(L.A), H->num_sms);
   if (dots == 1)
     k_slice_dots<1><<<grid, SELL_BLOCK, 0, s>>>(v, r, z, q, slice_part);
   else
@@ -431,7 +431,7 @@ static int coarse_solve(const amg_handle* H, const BT* b, XT* x, cudaStream_t s,
 template <typename V, typename T, typename BT>
 static int launch_pre(const amg_handle* H, const Level& L, const V* ah, const BT* b, T* r,
                       cudaStream_t s, const int* act = nullptr) {
-  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const int grid = sell_grid(sell_groups(L.A), H->num_sms);
   SellView<V> v = view<V>(L.A, ah);
   v.act = act;
   // FP64 operators (the ring's gain is where GB300's FP64 pipe co-limits the
@@ -468,7 +468,7 @@ template <typename V, typename T, typename BT, typename XT, int NDOT>
 static int launch_post(const amg_handle* H, const Level& L, const V* ap, const BT* b,
                        const T* xc, XT* x, const double* q, cudaStream_t s,
                        double* slice_part, const int* act, const PostIn<T>& in) {
-  const int grid = sell_grid(L.AP.nslices, H->num_sms);
+  const int grid = sell_grid(sell_groups(L.AP), H->num_sms);
   SellView<V> v = view<V>(L.AP, ap);
   v.act = act;
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
@@ -526,7 +526,7 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
 template <bool PRE, typename T, typename BT, typename YT>
 static int launch_sweep(const amg_handle* H, const Level& L, const BT* b, const T* r, T* r_out,
                         YT* x, int first, cudaStream_t s, const int* act) {
-  const int grid = sell_grid(L.A.nslices, H->num_sms);
+  const int grid = sell_grid(sell_groups(L.A), H->num_sms);
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
   auto go = [&](auto vtag, const auto* ah) -> int {
     using V = decltype(vtag);
@@ -562,7 +562,7 @@ template <typename T>
 static int launch_restrict(const amg_handle* H, const Level& L, const T* r, T* bc,
                            cudaStream_t s) {
   if (H->opt.smooth_prolongator) {  // b_c = R r, R = P^T
-    const int grid = sell_grid(L.R.nslices, H->num_sms);
+    const int grid = sell_grid(sell_groups(L.R), H->num_sms);
     auto go = [&](auto vtag) -> int {
       using V = decltype(vtag);
       const SellView<V> v = view<V>(L.R, sm_vals<V>(L.R));
@@ -592,7 +592,7 @@ static int pre_f32(const amg_handle* H, const Level& L, const BT* b, float* r, c
 template <typename T, typename BT, typename XT>
 static int launch_post_sm(const amg_handle* H, const Level& L, const BT* b, const T* xc, XT* x,
                           cudaStream_t s, const PostIn<T>& in) {
-  const int grid = sell_grid(L.AP.nslices, H->num_sms);
+  const int grid = sell_grid(sell_groups(L.AP), H->num_sms);
   const T* sc = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
   const T* r = in.r ? in.r : (const T*)L.r;
   if (sell_code(L.AP) != sell_code(L.P)) return AMG_ERR_UNSUPPORTED;

@@ -220,7 +220,11 @@ def test_bad_arguments_rejected(amg):
         m.Hierarchy(*A, sweeps=5)
     assert e.value.status == m._lib.AMG_ERR_ARG
     with pytest.raises(m.AmgError):
-        m.Hierarchy(*A, slice_height=16, threads_per_row=4)
+        m.Hierarchy(*A, slice_height=128, threads_per_row=1)  # heights 1..64
+    with pytest.raises(m.AmgError):
+        m.Hierarchy(*A, slice_height=12, threads_per_row=4)  # powers of two only
+    with pytest.raises(m.AmgError):
+        m.Hierarchy(*A, threads_per_row=3)
     H = m.Hierarchy(*A)
     with pytest.raises(m.AmgError):
         H.spmv(torch.zeros(64, dtype=torch.float64, device="cuda"), level=7)
