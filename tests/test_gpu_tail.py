@@ -1,7 +1,10 @@
 """The persistent launch of the small levels (levels with at most `tail_rows`
-rows and the coarsest solve between grid barriers) against one launch per
-step: the same per-row code runs in both, so every result must agree bit for
-bit, in every precision and layout and for batched systems."""
+rows and the coarsest solve between barriers) against one launch per step:
+the same per-row code runs in both, so every result must agree bit for bit,
+in every precision and layout and for batched systems.  The launch is one CTA
+when its largest level has at most 16384 rows (__syncthreads between phases)
+and a cooperative grid with the bounded grid barrier beyond; both are
+covered below."""
 
 import numpy as np
 import pytest
@@ -24,6 +27,7 @@ def _kinds(H, r):
 
 SMALL = (40, 36, 30)   # 43200 rows: the default tail runs in one CTA
 LARGE = (64, 64, 64)   # level 1 has 65536 rows: a tail from it spans the grid
+HUGE = (96, 96, 96)    # level 1 has 221184 rows: a wider grid
 
 
 @pytest.mark.parametrize("shape,opts", [
@@ -45,6 +49,8 @@ LARGE = (64, 64, 64)   # level 1 has 65536 rows: a tail from it spans the grid
     (SMALL, dict(precision="f64", coarse_solver=1, coarse_tol=0.0, coarse_maxit=9,
                  tail_rows=16384)),
     (LARGE, dict(precision="f64", smooth_sweeps=2, variable_cycle=1, tail_rows=70000)),
+    (HUGE, dict(precision="f64", tail_rows=300000)),
+    (HUGE, dict(precision="f32", smooth_sweeps=2, tail_rows=300000)),
 ])
 def test_tail_vcycle_bitwise(amg, shape, opts):
     A = diffusion3d(np.exp(gaussian_field(shape, 1.5, 4.0, 21)))
