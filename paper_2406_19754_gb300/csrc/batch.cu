@@ -6,10 +6,11 @@
 // V-cycle (one launch per stage for all systems).  Every level is sliced so
 // that no slice straddles two systems: the slices form a work list of
 // (system, slice) tiles.  The PCG kernels below walk the level-0 tiles, write
-// one partial sum per tile, and a segmented reduction turns those into the
+// partial sums, and a segmented reduction turns those into the
 // per-system scalars (alpha, beta, residual norm) and convergence flags on the
-// device.  Converged systems are frozen: their tiles are skipped in the SpMV
-// and vector updates.  One iteration for all systems replays as one CUDA
+// device.  Partial sums are per chunk of up to BATCH_CHUNK slices of one
+// system (a warp walks a chunk and reduces once at its end).  Converged
+// systems are frozen: their tiles are skipped in the SpMV and vector updates.  One iteration for all systems replays as one CUDA
 // graph; the host reads only the number of systems still iterating.
 #include <math.h>
 
@@ -21,70 +22,80 @@ namespace amg {
 
 enum { SEG_INIT = 0, SEG_RZ_FIRST = 1, SEG_PQ = 2, SEG_RR = 3, SEG_RZ = 4, SEG_TRUE = 5 };
 
-// r = b - A x with per-tile (r, r) and (b, b).
+// The kernels below walk the level-0 chunks (Batch): warp w takes chunks
+// w, w + W, ...; a chunk is consecutive slices of one system.
+#define AMG_BATCH_CHUNKS(c, s0, s1)                                                     \
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;  \
+       c += ((int64_t)gridDim.x * blockDim.x) >> 5)                                     \
+    for (int64_t s0 = chunk_off[c], s1 = chunk_off[c + 1], once_ = 1; once_; once_ = 0)
+
+// r = b - A x with per-chunk (r, r) and (b, b).
 template <int TPR>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
-    k_b_residual(SellView<double> A, const double* __restrict__ b, const double* __restrict__ x,
+    k_b_residual(SellView<double> A, int64_t nchunks, const int64_t* __restrict__ chunk_off,
+                 const double* __restrict__ b, const double* __restrict__ x,
                  double* __restrict__ r, double* __restrict__ part, float* __restrict__ r32) {
   const Lanes<TPR> ln;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
-       sl += nw) {
-    const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(x + j); });
-    const int64_t i = lane_row(A, sl, ln);
+  AMG_BATCH_CHUNKS(c, s0, s1) {
     double d0 = 0.0, d1 = 0.0;
-    if (i >= 0) {
-      const double ri = b[i] - acc;
-      r[i] = ri;
-      if (r32) r32[i] = (float)ri;
-      d0 = ri * ri;
-      d1 = b[i] * b[i];
+    for (int64_t sl = s0; sl < s1; ++sl) {
+      const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(x + j); });
+      const int64_t i = lane_row(A, sl, ln);
+      if (i >= 0) {
+        const double ri = b[i] - acc;
+        r[i] = ri;
+        if (r32) r32[i] = (float)ri;
+        d0 += ri * ri;
+        d1 += b[i] * b[i];
+      }
     }
     d0 = warp_sum(d0);
     d1 = warp_sum(d1);
     if ((threadIdx.x & 31) == 0) {
-      part[2 * sl] = d0;
-      part[2 * sl + 1] = d1;
+      part[2 * c] = d0;
+      part[2 * c + 1] = d1;
     }
   }
 }
 
-// q = A p with per-tile (p, q); tiles of converged systems are skipped.
+// q = A p with per-chunk (p, q); chunks of converged systems are skipped.
 template <int TPR>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
-    k_b_spmv_dot(SellView<double> A, const double* __restrict__ p, double* __restrict__ q,
+    k_b_spmv_dot(SellView<double> A, int64_t nchunks, const int64_t* __restrict__ chunk_off,
+                 const double* __restrict__ p, double* __restrict__ q,
                  double* __restrict__ part, const Scal* __restrict__ sc) {
   const Lanes<TPR> ln;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
-       sl += nw) {
-    if (!sc[A.sys[sl]].active) continue;  // warp-uniform
-    const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(p + j); });
-    const int64_t i = lane_row(A, sl, ln);
+  AMG_BATCH_CHUNKS(c, s0, s1) {
+    if (!sc[A.sys[s0]].active) continue;  // warp-uniform: one system per chunk
     double d = 0.0;
-    if (i >= 0) {
-      q[i] = acc;
-      d = p[i] * acc;
+    for (int64_t sl = s0; sl < s1; ++sl) {
+      const double acc = sell_row<TPR, double>(A, sl, ln, [&](int j) { return __ldg(p + j); });
+      const int64_t i = lane_row(A, sl, ln);
+      if (i >= 0) {
+        q[i] = acc;
+        d += p[i] * acc;
+      }
     }
     d = warp_sum(d);
-    if ((threadIdx.x & 31) == 0) part[2 * sl] = d;
+    if ((threadIdx.x & 31) == 0) part[2 * c] = d;
   }
 }
 
-// x += alpha_k p; r -= alpha_k q; per-tile (r, r); r32 (if set) = (float) r.
-__global__ void k_b_update(SellView<double> A, double* __restrict__ x, double* __restrict__ r,
-                           const double* __restrict__ p, const double* __restrict__ q,
-                           double* __restrict__ part, const Scal* __restrict__ sc,
-                           float* __restrict__ r32) {
+// x += alpha_k p; r -= alpha_k q; per-chunk (r, r); r32 (if set) = (float) r.
+__global__ void k_b_update(SellView<double> A, int64_t nchunks,
+                           const int64_t* __restrict__ chunk_off, double* __restrict__ x,
+                           double* __restrict__ r, const double* __restrict__ p,
+                           const double* __restrict__ q, double* __restrict__ part,
+                           const Scal* __restrict__ sc, float* __restrict__ r32) {
   const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
-       sl += nw) {
-    const Scal& S = sc[A.sys[sl]];
+  AMG_BATCH_CHUNKS(c, s0, s1) {
+    const Scal& S = sc[A.sys[s0]];
     if (!S.active) continue;
     const double alpha = S.alpha;
     double d = 0.0;
-    for (int64_t i = A.rbeg(sl, 32) + lane; i < A.rend(sl, 32); i += 32) {
+    // the chunk's rows are contiguous: first row of its first slice to one past
+    // the last row of its last
+    for (int64_t i = A.rbeg(s0, 32) + lane; i < A.rend(s1 - 1, 32); i += 32) {
       x[i] = x[i] + alpha * p[i];
       const double ri = r[i] - alpha * q[i];
       r[i] = ri;
@@ -92,7 +103,7 @@ __global__ void k_b_update(SellView<double> A, double* __restrict__ x, double* _
       d += ri * ri;
     }
     d = warp_sum(d);
-    if (lane == 0) part[2 * sl] = d;
+    if (lane == 0) part[2 * c] = d;
   }
 }
 
@@ -110,18 +121,18 @@ __global__ void k_b_p_update(SellView<double> A, double* __restrict__ p,
   }
 }
 
-// One CUDA block per system: each thread sums a fixed stride of its tiles'
+// One CUDA block per system: each thread sums a fixed stride of its chunks'
 // partials, the block adds them by a fixed tree, and thread 0 updates that
 // system's scalars (deterministic run to run).
 template <int MODE>
-__global__ void k_b_seg(int nsys, const int64_t* __restrict__ slice_off,
+__global__ void k_b_seg(int nsys, const int64_t* __restrict__ sys_chunk,
                         const double* __restrict__ part, Scal* sc, double tol, int maxit,
                         int beta_form, int* nactive, int* active) {
   for (int k = blockIdx.x; k < nsys; k += gridDim.x) {
     double t[2] = {0.0, 0.0};
-    for (int64_t sl = slice_off[k] + threadIdx.x; sl < slice_off[k + 1]; sl += blockDim.x) {
-      t[0] += part[2 * sl];
-      t[1] += part[2 * sl + 1];
+    for (int64_t c = sys_chunk[k] + threadIdx.x; c < sys_chunk[k + 1]; c += blockDim.x) {
+      t[0] += part[2 * c];
+      t[1] += part[2 * c + 1];
     }
     block_sum<2>(t);
     const double t0 = t[0], t1 = t[1];
@@ -193,7 +204,7 @@ template <int MODE>
 static int seg(const BatchRun& R, cudaStream_t s) {
   const Batch& B = R.H->batch;
   const int grid = std::max(1, std::min(B.nsys, R.H->num_sms * 8));
-  k_b_seg<MODE><<<grid, 256, 0, s>>>(B.nsys, B.slice_off, B.part, B.sc, R.tol, R.maxit,
+  k_b_seg<MODE><<<grid, 256, 0, s>>>(B.nsys, B.sys_chunk, B.part, B.sc, R.tol, R.maxit,
                                      R.beta_form, B.nactive, B.active);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -201,12 +212,32 @@ static int seg(const BatchRun& R, cudaStream_t s) {
 
 static SellView<double> a0(const amg_handle* H) { return view<double>(H->L[0].A, H->L[0].A.v64); }
 
+// Grid of the chunk kernels: one warp per chunk, at most one full wave.
+static int chunk_grid(const amg_handle* H) { return sell_grid(H->batch.nchunks, H->num_sms); }
+
 static int b_residual(const BatchRun& R, const double* b, const double* x, double* r,
                       float* r32, cudaStream_t s) {
   const Level& L = R.H->L[0];
-  const int grid = sell_grid(L.A.nslices, R.H->num_sms);
-  AMG_DISPATCH_TPR(sell_code(L.A), (k_b_residual<TPR><<<grid, SELL_BLOCK, 0, s>>>(
-                                a0(R.H), b, x, r, R.H->batch.part, r32)));
+  const Batch& B = R.H->batch;
+  AMG_DISPATCH_TPR(sell_code(L.A), (k_b_residual<TPR><<<chunk_grid(R.H), SELL_BLOCK, 0, s>>>(
+                                a0(R.H), B.nchunks, B.chunk_off, b, x, r, B.part, r32)));
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+static int b_spmv_dot(const amg_handle* H, cudaStream_t s) {
+  const Batch& B = H->batch;
+  AMG_DISPATCH_TPR(sell_code(H->L[0].A),
+                   (k_b_spmv_dot<TPR><<<chunk_grid(H), SELL_BLOCK, 0, s>>>(
+                       a0(H), B.nchunks, B.chunk_off, H->p, H->q, B.part, B.sc)));
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+static int b_update(const amg_handle* H, double* x, cudaStream_t s) {
+  const Batch& B = H->batch;
+  k_b_update<<<chunk_grid(H), SELL_BLOCK, 0, s>>>(a0(H), B.nchunks, B.chunk_off, x, H->r, H->p,
+                                                  H->q, B.part, B.sc, H->r32);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -220,13 +251,9 @@ static int b_body(const BatchRun& R, double* x, cudaStream_t s) {
   AMG_TRY(seg<SEG_RZ>(R, s));
   k_b_p_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), H->p, H->z, H->batch.sc);
   AMG_LAUNCH_CHECK();
-  AMG_DISPATCH_TPR(sell_code(L.A), (k_b_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(
-                                a0(H), H->p, H->q, H->batch.part, H->batch.sc)));
-  AMG_LAUNCH_CHECK();
+  AMG_TRY(b_spmv_dot(H, s));
   AMG_TRY(seg<SEG_PQ>(R, s));
-  k_b_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), x, H->r, H->p, H->q, H->batch.part,
-                                         H->batch.sc, H->r32);
-  AMG_LAUNCH_CHECK();
+  AMG_TRY(b_update(H, x, s));
   AMG_CUDA_TRY(cudaMemsetAsync(H->batch.nactive, 0, sizeof(int), s));
   AMG_TRY(seg<SEG_RR>(R, s));
   return AMG_OK;
@@ -331,12 +358,9 @@ int pcg_batch_run(amg_handle* H, const double* b, double* x, const pcg_options* 
     AMG_TRY(vcycle_run(H, H->r, H->z, R.dots, H->q, s, B.part, H->r32));
     AMG_TRY(seg<SEG_RZ_FIRST>(R, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(H->p, H->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    AMG_DISPATCH_TPR(sell_code(H->L[0].A), (k_b_spmv_dot<TPR><<<grid, SELL_BLOCK, 0, s>>>(
-                                        a0(H), H->p, H->q, B.part, B.sc)));
-    AMG_LAUNCH_CHECK();
+    AMG_TRY(b_spmv_dot(H, s));
     AMG_TRY(seg<SEG_PQ>(R, s));
-    k_b_update<<<grid, SELL_BLOCK, 0, s>>>(a0(H), x, H->r, H->p, H->q, B.part, B.sc, H->r32);
-    AMG_LAUNCH_CHECK();
+    AMG_TRY(b_update(H, x, s));
     AMG_CUDA_TRY(cudaMemsetAsync(B.nactive, 0, sizeof(int), s));
     AMG_TRY(seg<SEG_RR>(R, s));
     k = 1;
@@ -392,9 +416,20 @@ int batch_init(amg_handle* H, cudaStream_t s) {
     off[k + 1] = off[k] + (rows + L.A.C - 1) / L.A.C;
   }
   if (off.back() != B.nslices) return AMG_ERR_DEVICE_CHECK;
+  // chunks of at most BATCH_CHUNK slices, never across two systems
+  std::vector<int64_t> coff, sch(B.nsys + 1, 0);
+  for (int k = 0; k < B.nsys; ++k) {
+    sch[k] = (int64_t)coff.size();
+    for (int64_t sl = off[k]; sl < off[k + 1]; sl += BATCH_CHUNK) coff.push_back(sl);
+  }
+  sch[B.nsys] = (int64_t)coff.size();
+  B.nchunks = (int64_t)coff.size();
+  coff.push_back(B.nslices);
   Arena& ar = H->arena;
   AMG_TRY(ar.alloc_n(&B.slice_off, B.nsys + 1));
-  AMG_TRY(ar.alloc_n(&B.part, 2 * B.nslices));
+  AMG_TRY(ar.alloc_n(&B.chunk_off, B.nchunks + 1));
+  AMG_TRY(ar.alloc_n(&B.sys_chunk, B.nsys + 1));
+  AMG_TRY(ar.alloc_n(&B.part, 2 * B.nchunks));
   AMG_TRY(ar.alloc_n(&B.sc, B.nsys));
   AMG_TRY(ar.alloc_n(&B.nactive, 1));
   AMG_TRY(ar.alloc_n(&B.loop_ctl, 2));
@@ -402,7 +437,11 @@ int batch_init(amg_handle* H, cudaStream_t s) {
   AMG_CUDA_TRY(cudaMallocHost((void**)&B.sc_host, sizeof(Scal) * B.nsys));
   AMG_CUDA_TRY(cudaMemcpyAsync(B.slice_off, off.data(), sizeof(int64_t) * off.size(),
                                cudaMemcpyHostToDevice, s));
-  AMG_CUDA_TRY(cudaMemsetAsync(B.part, 0, sizeof(double) * 2 * B.nslices, s));
+  AMG_CUDA_TRY(cudaMemcpyAsync(B.chunk_off, coff.data(), sizeof(int64_t) * coff.size(),
+                               cudaMemcpyHostToDevice, s));
+  AMG_CUDA_TRY(cudaMemcpyAsync(B.sys_chunk, sch.data(), sizeof(int64_t) * sch.size(),
+                               cudaMemcpyHostToDevice, s));
+  AMG_CUDA_TRY(cudaMemsetAsync(B.part, 0, sizeof(double) * 2 * B.nchunks, s));
   AMG_CUDA_TRY(cudaMemsetAsync(B.sc, 0, sizeof(Scal) * B.nsys, s));
   AMG_CUDA_TRY(cudaStreamSynchronize(s));
   return AMG_OK;

@@ -169,11 +169,20 @@ struct Level {
 
 // Batched PCG state (pcg_solve_batch): per-system scalars and per-slice
 // partial sums over the level-0 slices, which never straddle two systems.
+// Level-0 slices of each system are grouped into chunks of at most
+// BATCH_CHUNK consecutive slices; a warp walks whole chunks, keeps its dot
+// sums per thread over a chunk's slices and writes one pair of partials per
+// chunk (one warp reduction per chunk, none inside the slice loop).
+constexpr int BATCH_CHUNK = 16;
+
 struct Batch {
   int nsys = 0;
   int64_t nslices = 0;
   int64_t* slice_off = nullptr;  // device, nsys + 1: slices of system k
-  double* part = nullptr;        // device, 2 * nslices
+  int64_t nchunks = 0;
+  int64_t* chunk_off = nullptr;  // device, nchunks + 1: first slice of chunk c
+  int64_t* sys_chunk = nullptr;  // device, nsys + 1: first chunk of system k
+  double* part = nullptr;        // device, 2 * nchunks: per-chunk partial sums
   struct Scal* sc = nullptr;     // device, nsys
   struct Scal* sc_host = nullptr;  // pinned, nsys
   int* active = nullptr;         // device, nsys: copy of each system's active flag

@@ -60,26 +60,24 @@ struct VcycleDotEpi {
 // MS: the level smooths more than once per side (xp and e are used); the
 // one-sweep instantiations do not carry them, which keeps their registers
 // within the occupancy bound.  NDOT > 0 (level 0 of PCG): the kernel also
-// forms (r, z) and, for NDOT = 2, (z, q).  SP = false (one system): grid-wide
-// sums, with no warp-collective operation inside the streaming loop (a
-// per-slice warp reduction there cost 10% on 256^3 Poisson); SP = true
-// (batched systems): per-slice partials in slice_part[2 sl], [2 sl + 1],
-// reduced per system afterwards.
-template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT, bool MS,
-          bool SP = false>
+// forms (r, z) and, for NDOT = 2, (z, q), as grid-wide sums with no
+// warp-collective operation inside the streaming loop (a per-slice warp
+// reduction there cost 10% on 256^3 Poisson).  Batched systems use
+// k_post_chunks below.
+template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT, bool MS>
 __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     k_post(SellView<V> AP, const BT* __restrict__ b, const T* __restrict__ s,
            const T* __restrict__ r, const int32_t* __restrict__ agg, const T* __restrict__ xc,
            XT* __restrict__ x, const double* __restrict__ q, Reduce red, PcgScalars* sc,
-           const T* __restrict__ xp, T* __restrict__ e, double* __restrict__ slice_part) {
+           const T* __restrict__ xp, T* __restrict__ e) {
   const Lanes<TPR> ln;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   constexpr int ND = NDOT > 0 ? NDOT : 1;
   // the running sums sit in shared memory (one slot per thread, the same
   // additions in the same order as registers would do): the streaming loop
   // already fills the 32-register budget of full occupancy
-  __shared__ double dacc[ND][NDOT > 0 && !SP ? SELL_BLOCK : 1];
-  if constexpr (NDOT > 0 && !SP) {
+  __shared__ double dacc[ND][NDOT > 0 ? SELL_BLOCK : 1];
+  if constexpr (NDOT > 0) {
 #pragma unroll
     for (int k = 0; k < NDOT; ++k) dacc[k][threadIdx.x] = 0.0;
   }
@@ -89,31 +87,52 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
     XT zi;
     const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi,
                                             MS ? xp : nullptr, MS ? e : nullptr);
-    if constexpr (NDOT > 0 && SP) {
-      double ds[NDOT];
-#pragma unroll
-      for (int k = 0; k < NDOT; ++k) ds[k] = 0.0;
-      if (i >= 0) {
-        ds[0] = (double)b[i] * (double)zi;
-        if (NDOT > 1) ds[NDOT > 1 ? 1 : 0] = (double)zi * q[i];
-      }
-#pragma unroll
-      for (int k = 0; k < NDOT; ++k) {
-        const double v = warp_sum(ds[k]);
-        if ((threadIdx.x & 31) == 0) slice_part[sl * 2 + k] = v;
-      }
-    } else if constexpr (NDOT > 0) {
+    if constexpr (NDOT > 0) {
       if (i >= 0) {
         dacc[0][threadIdx.x] += (double)b[i] * (double)zi;
         if (NDOT > 1) dacc[NDOT > 1 ? 1 : 0][threadIdx.x] += (double)zi * q[i];
       }
     }
   }
-  if constexpr (NDOT > 0 && !SP) {
+  if constexpr (NDOT > 0) {
     double d[ND];
 #pragma unroll
     for (int k = 0; k < NDOT; ++k) d[k] = dacc[k][threadIdx.x];
     grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
+  }
+}
+
+// The level-0 post-smoother of batched systems with (r, z) (and (z, q)) per
+// chunk of BATCH_CHUNK slices of one system: a warp walks whole chunks,
+// keeps the sums per thread over the chunk's slices and reduces once at its
+// end into part[2 c], part[2 c + 1] (no warp reduction in the slice loop).
+template <int TPR, typename V, typename T, typename BT, typename XT, int NDOT>
+__global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
+    k_post_chunks(SellView<V> AP, int64_t nchunks, const int64_t* __restrict__ chunk_off,
+                  const BT* __restrict__ b, const T* __restrict__ s, const T* __restrict__ r,
+                  const int32_t* __restrict__ agg, const T* __restrict__ xc,
+                  XT* __restrict__ x, const double* __restrict__ q, double* __restrict__ part) {
+  const Lanes<TPR> ln;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;
+       c += nw) {
+    const int64_t s0 = chunk_off[c], s1 = chunk_off[c + 1];
+    if (!AP.live(s0)) continue;  // warp-uniform: one system per chunk
+    double d0 = 0.0, d1 = 0.0;
+    for (int64_t sl = s0; sl < s1; ++sl) {
+      XT zi;
+      const int64_t i = post_slice<TPR, LdRO>(AP, b, s, r, agg, xc, x, sl, ln, zi);
+      if (i >= 0) {
+        d0 += (double)b[i] * (double)zi;
+        if (NDOT > 1) d1 += (double)zi * q[i];
+      }
+    }
+    d0 = warp_sum(d0);
+    if (NDOT > 1) d1 = warp_sum(d1);
+    if ((threadIdx.x & 31) == 0) {
+      part[2 * c] = d0;
+      if (NDOT > 1) part[2 * c + 1] = d1;
+    }
   }
 }
 
@@ -303,16 +322,19 @@ __global__ void k_dots_rz(int64_t n, const double* r, const double* z, const dou
   grid_reduce<NDOT>(d, red, VcycleDotEpi{sc});
 }
 
-// Per-slice (r, z) and (z, q) partials over the level-0 slices (batched
-// systems whose whole hierarchy is one level).
+// Per-chunk (r, z) and (z, q) partials over the level-0 chunks of batched
+// systems (see Batch), for V-cycles whose level-0 post-smoother does not
+// form them.
 template <int NDOT>
-__global__ void k_slice_dots(SellView<double> A, const double* r, const double* z,
-                             const double* q, double* slice_part) {
+__global__ void k_chunk_dots(SellView<double> A, int64_t nchunks,
+                             const int64_t* __restrict__ chunk_off, const double* r,
+                             const double* z, const double* q, double* part) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.ngroups;
-       sl += nw) {
-    const int64_t b0 = A.rbeg(sl, 32), b1 = A.rend(sl, 32);
+  for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < nchunks;
+       c += nw) {
+    // the chunk's rows are contiguous (system-aligned slices)
+    const int64_t b0 = A.rbeg(chunk_off[c], 32), b1 = A.rend(chunk_off[c + 1] - 1, 32);
     double d0 = 0.0, d1 = 0.0;
     for (int64_t i = b0 + lane; i < b1; i += 32) {
       d0 += r[i] * z[i];
@@ -320,24 +342,25 @@ __global__ void k_slice_dots(SellView<double> A, const double* r, const double* 
     }
     d0 = warp_sum(d0);
     if (NDOT > 1) d1 = warp_sum(d1);
-    if (lane == 0) {  // two slots per slice, as every batched reduction uses
-      slice_part[sl * 2] = d0;
-      if (NDOT > 1) slice_part[sl * 2 + 1] = d1;
+    if (lane == 0) {  // two slots per chunk, as every batched reduction uses
+      part[c * 2] = d0;
+      if (NDOT > 1) part[c * 2 + 1] = d1;
     }
   }
 }
 
 static int slice_dots(const amg_handle* H, const double* r, const double* z, const double* q,
-                      int dots, double* slice_part, cudaStream_t s) {
+                      int dots, double* part, cudaStream_t s) {
   // rbeg/rend with C = 32 are exact for system-aligned slices (row0 set)
   const Level& L = H->L[0];
-  if (!L.A.row0) return AMG_ERR_ARG;
+  const Batch& B = H->batch;
+  if (!L.A.row0 || !B.chunk_off) return AMG_ERR_ARG;
   const SellView<double> v = view<double>(L.A, L.A.v64);
-  const int grid = sell_grid(sell_groups(L.A), H->num_sms);
+  const int grid = sell_grid(B.nchunks, H->num_sms);
   if (dots == 1)
-    k_slice_dots<1><<<grid, SELL_BLOCK, 0, s>>>(v, r, z, q, slice_part);
+    k_chunk_dots<1><<<grid, SELL_BLOCK, 0, s>>>(v, B.nchunks, B.chunk_off, r, z, q, part);
   else
-    k_slice_dots<2><<<grid, SELL_BLOCK, 0, s>>>(v, r, z, q, slice_part);
+    k_chunk_dots<2><<<grid, SELL_BLOCK, 0, s>>>(v, B.nchunks, B.chunk_off, r, z, q, part);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
@@ -477,8 +500,7 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
     if (in.xp) {
       AMG_DISPATCH_TPR(sell_code(L.AP),
                        (k_post<TPR, V, T, BT, XT, 0, true><<<grid, SELL_BLOCK, 0, s>>>(
-                           v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, in.xp, in.e,
-                           nullptr)));
+                           v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, in.xp, in.e)));
       AMG_LAUNCH_CHECK();
       return AMG_OK;
     }
@@ -504,19 +526,20 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
     }
   }
   if constexpr (NDOT > 0) {
-    if (slice_part) {
+    if (slice_part) {  // batched systems: per-chunk partials
+      const Batch& B = H->batch;
+      if (!B.chunk_off) return AMG_ERR_ARG;
+      const int cg = sell_grid(B.nchunks, H->num_sms);
       AMG_DISPATCH_TPR(sell_code(L.AP),
-                       (k_post<TPR, V, T, BT, XT, NDOT, false, true><<<grid, SELL_BLOCK, 0, s>>>(
-                           v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, nullptr, nullptr,
-                           slice_part)));
+                       (k_post_chunks<TPR, V, T, BT, XT, NDOT><<<cg, SELL_BLOCK, 0, s>>>(
+                           v, B.nchunks, B.chunk_off, b, sc, r, L.agg, xc, x, q, slice_part)));
       AMG_LAUNCH_CHECK();
       return AMG_OK;
     }
   }
   AMG_DISPATCH_TPR(sell_code(L.AP),
                    (k_post<TPR, V, T, BT, XT, NDOT, false><<<grid, SELL_BLOCK, 0, s>>>(
-                       v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, nullptr, nullptr,
-                       nullptr)));
+                       v, b, sc, r, L.agg, xc, x, q, H->red, H->sc, nullptr, nullptr)));
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
