@@ -352,9 +352,18 @@ int mlp_get_grad(const mlp_handle* M, double* host);
 int mlp_features(const amg_csr* A, int64_t nx, int64_t ny, int64_t nz, float* feat,
                  amg_stream_t stream);
 
-/* omega[i] = network(feat[i]) for n rows (device float arrays).  Asynchronous. */
+/*
+ * omega[i] = network(feat[i]) for n rows (device float arrays).  By default
+ * the two hidden layers run on the tensor cores (TF32 operands, FP32
+ * accumulation; omega within about 1e-3 of the FP32 pass); after
+ * mlp_set_exact_forward(M, 1), in FP32 on the CUDA cores.  Asynchronous.
+ */
 int mlp_forward(const mlp_handle* M, int64_t n, const float* feat, float* omega,
                 amg_stream_t stream);
+
+/* Forward pass in FP32 on the CUDA cores (exact = 1) or on the tensor cores
+ * (0, default).  Not in the paper.  Errors: AMG_ERR_ARG. */
+int mlp_set_exact_forward(mlp_handle* M, int exact);
 
 /*
  * Gradient of sum_i domega[i] * omega[i] with respect to the parameters
@@ -517,6 +526,14 @@ int amg_debug_fail_alloc_after(long count);
  * timeout path.  Errors: AMG_ERR_ARG (H NULL).
  */
 int amg_debug_tail_timeout(amg_handle* H, int on);
+
+/*
+ * out[i] = GELU(u[i]) as the tensor-core MLP forward pass evaluates it (erf
+ * by Abramowitz & Stegun 7.1.26), for n device floats, so tests can bound
+ * its error against the exact GELU.  No counterpart in the paper.  Errors:
+ * AMG_ERR_ARG.  Asynchronous.
+ */
+int mlp_debug_gelu(const float* u, float* out, int64_t n, amg_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -95,6 +95,7 @@ SIGNATURES = {
     "mlp_set_params": (C.c_int, [_P, _P]),
     "mlp_get_grad": (C.c_int, [_P, _P]),
     "mlp_set_omega_max": (C.c_int, [_P, C.c_double]),
+    "mlp_set_exact_forward": (C.c_int, [_P, C.c_int]),
     "mlp_features": (C.c_int, [C.POINTER(AmgCsr), C.c_int64, C.c_int64, C.c_int64, _P, _P]),
     "mlp_forward": (C.c_int, [_P, C.c_int64, _P, _P, _P]),
     "mlp_backward": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int, _P]),
@@ -110,6 +111,7 @@ SIGNATURES = {
     "amg_pairwise_match": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_pairwise_match_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_debug_fail_alloc_after": (C.c_int, [C.c_long]),
+    "mlp_debug_gelu": (C.c_int, [_P, _P, C.c_int64, _P]),
     "amg_debug_tail_timeout": (C.c_int, [_P, C.c_int]),
 }
 

@@ -130,6 +130,7 @@ struct Level {
   int64_t ap_nnz = 0;
   int vstore = VAL_F64;
   double* d = nullptr;     // l1 row sums
+  double* dinv = nullptr;  // 1 / d
   double* s64 = nullptr;   // smoother scale s_i = omega_i * (1 / d_i)
   float* s32 = nullptr;
   int32_t* agg = nullptr;      // row -> aggregate on level l+1

@@ -10,6 +10,7 @@
 // W3[32], b3.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -28,6 +29,7 @@ constexpr int BW_BLOCKS_MAX = 1024;
 
 struct mlp_handle {
   float omega_max = 1.0f;  // output cap: omega = max(omega_max * sigmoid(z), OMEGA_MIN)
+  int exact = 0;           // 1: the FP32 CUDA-core forward pass instead of the tensor cores
   float* params = nullptr;
   double* grad = nullptr;   // accumulated gradient (FP64)
   double* gpart = nullptr;  // per-block partial gradients
@@ -54,41 +56,49 @@ __device__ __forceinline__ float gelu_df(float u) {
 // divisions and the logarithm the cost of this kernel): one reciprocal of
 // a_ii, and the logarithm as log1p((max - min) / min), which stays accurate
 // when max and min are close.
+__device__ __forceinline__ void row_features(int64_t i, int64_t nx, int64_t nxy,
+                                             const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ ci,
+                                             const double* __restrict__ v, float (&f)[NF]) {
+  const int64_t e0 = rp[i], e1 = rp[i + 1];
+  float aii = 0.0f;
+  for (int64_t e = e0; e < e1; ++e)
+    if (ci[e] == i) aii = (float)v[e];
+  const float inv = 1.0f / aii;
+  float off[6] = {0, 0, 0, 0, 0, 0}, l1 = 0.0f, amax = 0.0f, amin = 0.0f;
+  int cnt = 0;
+  for (int64_t e = e0; e < e1; ++e) {
+    const int64_t d = (int64_t)ci[e] - i;
+    if (d == 0) continue;
+    const float a = (float)v[e];
+    int slot = -1;
+    if (d == -1) slot = 0;
+    else if (d == 1) slot = 1;
+    else if (d == -nx) slot = 2;
+    else if (d == nx) slot = 3;
+    else if (d == -nxy) slot = 4;
+    else if (d == nxy) slot = 5;
+    if (slot >= 0) off[slot] = a * inv;
+    const float m = fabsf(a);
+    l1 += m;
+    amax = cnt == 0 ? m : fmaxf(amax, m);
+    amin = cnt == 0 ? m : fminf(amin, m);
+    ++cnt;
+  }
+  for (int k = 0; k < 6; ++k) f[k] = off[k];
+  f[6] = l1 * inv;
+  f[7] = (cnt > 0 && amin > 0.0f) ? log1pf((amax - amin) / amin) : 0.0f;
+  f[8] = (float)cnt / 6.0f;
+}
+
 __global__ void k_features(int64_t n, int64_t nx, int64_t nxy, const int64_t* __restrict__ rp,
                            const int32_t* __restrict__ ci, const double* __restrict__ v,
                            float* __restrict__ feat) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e0 = rp[i], e1 = rp[i + 1];
-    float aii = 0.0f;
-    for (int64_t e = e0; e < e1; ++e)
-      if (ci[e] == i) aii = (float)v[e];
-    const float inv = 1.0f / aii;
-    float off[6] = {0, 0, 0, 0, 0, 0}, l1 = 0.0f, amax = 0.0f, amin = 0.0f;
-    int cnt = 0;
-    for (int64_t e = e0; e < e1; ++e) {
-      const int64_t d = (int64_t)ci[e] - i;
-      if (d == 0) continue;
-      const float a = (float)v[e];
-      int slot = -1;
-      if (d == -1) slot = 0;
-      else if (d == 1) slot = 1;
-      else if (d == -nx) slot = 2;
-      else if (d == nx) slot = 3;
-      else if (d == -nxy) slot = 4;
-      else if (d == nxy) slot = 5;
-      if (slot >= 0) off[slot] = a * inv;
-      const float m = fabsf(a);
-      l1 += m;
-      amax = cnt == 0 ? m : fmaxf(amax, m);
-      amin = cnt == 0 ? m : fminf(amin, m);
-      ++cnt;
-    }
-    float* f = feat + i * NF;
-    for (int k = 0; k < 6; ++k) f[k] = off[k];
-    f[6] = l1 * inv;
-    f[7] = (cnt > 0 && amin > 0.0f) ? log1pf((amax - amin) / amin) : 0.0f;
-    f[8] = (float)cnt / 6.0f;
+    float f[NF];
+    row_features(i, nx, nxy, rp, ci, v, f);
+    for (int k = 0; k < NF; ++k) feat[i * NF + k] = f[k];
   }
 }
 
@@ -194,6 +204,181 @@ __global__ void __launch_bounds__(FW_WARPS * 32)
       omega[r0 + lane] = fmaxf(omega_max * sg, OMEGA_MIN);
     }
     __syncwarp();
+  }
+}
+
+// Forward pass on the tensor cores: the 9 -> 32 and 32 -> 32 layers of a tile
+// of 16 rows are warp-level matrix products (mma.sync m16n8k8, TF32 operands
+// rounded to nearest, FP32 accumulation); GELU, the 32 -> 1 layer and the
+// sigmoid run in FP32 on the accumulators.  Fragment layouts of m16n8k8
+// (g = lane / 4, t = lane % 4): A (16 x 8, row major) a0 = (g, t), a1 =
+// (g + 8, t), a2 = (g, t + 4), a3 = (g + 8, t + 4); B (8 x 8, k x n) b0 =
+// (t, g), b1 = (t + 4, g); C (16 x 8) c0 = (g, 2t), c1 = (g, 2t + 1), c2 =
+// (g + 8, 2t), c3 = (g + 8, 2t + 1).  The weights stay in registers as B
+// fragments for the whole launch; a tile's features and first-layer
+// activations go through shared memory to become A fragments.
+// GELU uses erf_as7126.  omega agrees with the FP32 pass to about 1e-3 (TF32
+// keeps 10 mantissa bits).
+constexpr int TC_WARPS = 4;
+constexpr int TC_LD = 36;  // padded row of the activation tile (conflict-free A loads)
+
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula
+// 7.1.26: for x >= 0, erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5)
+// e^(-x^2) with t = 1 / (1 + p x), |error| <= 1.5e-7; odd in x.  About a
+// dozen instructions (a fast reciprocal and exponential, five FMAs), against
+// the exact erff's longer sequence; the tensor-core forward pass, whose TF32
+// operands already limit omega to about 1e-3, uses it in its GELUs.
+__device__ __forceinline__ float erf_as7126(float x) {
+  const float ax = fabsf(x);
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+  const float poly =
+      t * fmaf(fmaf(fmaf(fmaf(1.061405429f, t, -1.453152027f), t, 1.421413741f), t,
+                    -0.284496736f),
+               t, 0.254829592f);
+  const float r = fmaf(-poly, __expf(-ax * ax), 1.0f);
+  return copysignf(r, x);
+}
+
+__device__ __forceinline__ float gelu_fast(float u) {
+  return 0.5f * u * (1.0f + erf_as7126(u * 0.70710678f));
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// The tile's features and first-layer activations are stored already
+// rounded to TF32; the next tile's features are loaded into registers while
+// the current one is computed.
+__global__ void __launch_bounds__(TC_WARPS * 32)
+    k_mlp_forward_tc(int64_t n, const float* __restrict__ params,
+                     const float* __restrict__ feat, float omega_max,
+                     float* __restrict__ omega) {
+  __shared__ uint32_t fs[TC_WARPS][16 * 16];     // a tile's features (TF32), 9 of 16 used
+  __shared__ uint32_t hs[TC_WARPS][16 * TC_LD];  // first-layer activations (TF32)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  // B fragments: W1^T (k = feature, n = neuron; k >= 9 is zero) and W2^T
+  uint32_t w1b[2][4][2], w2b[4][4][2];
+  float b1v[4][2], b2v[4][2], w3v[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int o = 8 * nt + g;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int k0 = 8 * ks + t, k1 = k0 + 4;
+      w1b[ks][nt][0] = to_tf32(k0 < NF ? params[OFF_W1 + o * NF + k0] : 0.0f);
+      w1b[ks][nt][1] = to_tf32(k1 < NF ? params[OFF_W1 + o * NF + k1] : 0.0f);
+    }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      w2b[ks][nt][0] = to_tf32(params[OFF_W2 + o * NH + 8 * ks + t]);
+      w2b[ks][nt][1] = to_tf32(params[OFF_W2 + o * NH + 8 * ks + t + 4]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {  // this thread's accumulator columns 8 nt + 2 t + j
+      b1v[nt][j] = params[OFF_B1 + 8 * nt + 2 * t + j];
+      b2v[nt][j] = params[OFF_B2 + 8 * nt + 2 * t + j];
+      w3v[nt][j] = params[OFF_W3 + 8 * nt + 2 * t + j];
+    }
+  }
+  const float b3 = params[OFF_B3];
+  uint32_t* f = fs[w];
+  uint32_t* h = hs[w];
+  for (int k = lane; k < 16 * 16; k += 32) f[k] = 0u;
+  const int64_t ntiles = (n + 15) / 16;
+  const int64_t step = (int64_t)gridDim.x * TC_WARPS;
+  constexpr int FPL = (16 * NF + 31) / 32;  // feature values per lane and tile
+  // this lane's share of a tile's 16 x 9 features (0 beyond the last row)
+  auto load_tile = [&](int64_t tl, float (&v)[FPL]) {
+#pragma unroll
+    for (int q = 0; q < FPL; ++q) {
+      const int k = lane + 32 * q;
+      const int64_t e = tl * 16 * NF + k;
+      v[q] = (tl < ntiles && k < 16 * NF && e < n * NF) ? __ldg(feat + e) : 0.0f;
+    }
+  };
+  float nxt[FPL];
+  load_tile((int64_t)blockIdx.x * TC_WARPS + w, nxt);
+  for (int64_t tile = (int64_t)blockIdx.x * TC_WARPS + w; tile < ntiles; tile += step) {
+    const int64_t r0 = tile * 16;
+    const int rows = (int)(n - r0 < 16 ? n - r0 : 16);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < FPL; ++q) {
+      const int k = lane + 32 * q;
+      if (k < 16 * NF) f[(k / NF) * 16 + k % NF] = to_tf32(nxt[q]);
+    }
+    load_tile(tile + step, nxt);
+    __syncwarp();
+    // layer 1: U1 = F W1^T + b1 (4 column tiles of 8, K = 16 with zeros beyond 9)
+    float c1[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      c1[nt][0] = c1[nt][2] = b1v[nt][0];
+      c1[nt][1] = c1[nt][3] = b1v[nt][1];
+    }
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int k = 8 * ks + t;
+      const uint32_t a0 = f[g * 16 + k], a1 = f[(g + 8) * 16 + k], a2 = f[g * 16 + k + 4],
+                     a3 = f[(g + 8) * 16 + k + 4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) mma_tf32(c1[nt], a0, a1, a2, a3, w1b[ks][nt][0], w1b[ks][nt][1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        h[g * TC_LD + 8 * nt + 2 * t + j] = to_tf32(gelu_fast(c1[nt][j]));
+        h[(g + 8) * TC_LD + 8 * nt + 2 * t + j] = to_tf32(gelu_fast(c1[nt][2 + j]));
+      }
+    __syncwarp();
+    // layer 2: U2 = H1 W2^T + b2, then z = GELU(U2) w3 + b3 per row
+    float c2[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      c2[nt][0] = c2[nt][2] = b2v[nt][0];
+      c2[nt][1] = c2[nt][3] = b2v[nt][1];
+    }
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const int k = 8 * ks + t;
+      const uint32_t a0 = h[g * TC_LD + k], a1 = h[(g + 8) * TC_LD + k],
+                     a2 = h[g * TC_LD + k + 4], a3 = h[(g + 8) * TC_LD + k + 4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) mma_tf32(c2[nt], a0, a1, a2, a3, w2b[ks][nt][0], w2b[ks][nt][1]);
+    }
+    float zg = 0.0f, zg8 = 0.0f;  // partial z of rows g and g + 8 over this thread's columns
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        zg = fmaf(w3v[nt][j], gelu_fast(c2[nt][j]), zg);
+        zg8 = fmaf(w3v[nt][j], gelu_fast(c2[nt][2 + j]), zg8);
+      }
+    // the four threads of a group hold a row's 32 columns between them
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+      zg += __shfl_xor_sync(0xffffffffu, zg, o);
+      zg8 += __shfl_xor_sync(0xffffffffu, zg8, o);
+    }
+    if (t == 0) {
+      if (g < rows) omega[r0 + g] = fmaxf(omega_max * (1.0f / (1.0f + expf(-(zg + b3)))), OMEGA_MIN);
+      if (g + 8 < rows)
+        omega[r0 + g + 8] = fmaxf(omega_max * (1.0f / (1.0f + expf(-(zg8 + b3)))), OMEGA_MIN);
+    }
   }
 }
 
@@ -383,6 +568,12 @@ int mlp_set_params(mlp_handle* M, const float* host) {
   return AMG_OK;
 }
 
+int mlp_set_exact_forward(mlp_handle* M, int exact) {
+  if (!M || (exact != 0 && exact != 1)) return AMG_ERR_ARG;
+  M->exact = exact;
+  return AMG_OK;
+}
+
 int mlp_set_omega_max(mlp_handle* M, double omega_max) {
   if (!M || !(omega_max >= 1.0 && omega_max < 2.0)) return AMG_ERR_ARG;
   M->omega_max = (float)omega_max;
@@ -411,9 +602,29 @@ int mlp_forward(const mlp_handle* M, int64_t n, const float* feat, float* omega,
                 amg_stream_t stream) {
   if (!M || n < 0 || !feat || !omega) return AMG_ERR_ARG;
   if (n == 0) return AMG_OK;
-  // 5 blocks fit an SM (41.6 KB of shared memory each): one wave
-  k_mlp_forward_tiled<<<grid_for((n + 31) / 32, FW_WARPS, M->num_sms, 5), FW_WARPS * 32, 0,
-                        (cudaStream_t)stream>>>(n, M->params, feat, M->omega_max, omega);
+  if (M->exact) {
+    // FP32 CUDA-core pass; 5 blocks fit an SM (41.6 KB of shared memory each)
+    k_mlp_forward_tiled<<<grid_for((n + 31) / 32, FW_WARPS, M->num_sms, 5), FW_WARPS * 32, 0,
+                          (cudaStream_t)stream>>>(n, M->params, feat, M->omega_max, omega);
+  } else {
+    k_mlp_forward_tc<<<grid_for((n + 15) / 16, TC_WARPS, M->num_sms, 8), TC_WARPS * 32, 0,
+                       (cudaStream_t)stream>>>(n, M->params, feat, M->omega_max, omega);
+  }
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+__global__ void k_gelu_fast(int64_t n, const float* u, float* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = gelu_fast(u[i]);
+}
+
+int mlp_debug_gelu(const float* u, float* out, int64_t n, amg_stream_t stream) {
+  if (!u || !out || n < 0) return AMG_ERR_ARG;
+  if (n == 0) return AMG_OK;
+  k_gelu_fast<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0,
+                (cudaStream_t)stream>>>(n, u, out);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }

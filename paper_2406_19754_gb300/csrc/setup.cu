@@ -37,11 +37,20 @@ __global__ void k_l1_diag(int64_t n, const int64_t* rowptr, const int32_t* col,
 }
 
 // s_i = omega_i * (1 / d_i) (omega == NULL: 1).
-__global__ void k_smoother_scale(int64_t n, const double* d, const float* omega, double* s64,
+// 1 / d_i, once per level at setup (an FP64 division is a long sequence on
+// GB300's reduced-rate FP64 pipe; new smoother weights only multiply).
+__global__ void k_recip(int64_t n, const double* d, double* dinv) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dinv[i] = __ddiv_rn(1.0, d[i]);
+}
+
+// s_i = omega_i * (1 / d_i) (omega == 1 when null).
+__global__ void k_smoother_scale(int64_t n, const double* dinv, const float* omega, double* s64,
                                  float* s32) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double inv = __ddiv_rn(1.0, d[i]);
+    const double inv = dinv[i];
     double w = omega ? (double)omega[i] : 1.0;
     double s = __dmul_rn(w, inv);
     s64[i] = s;
@@ -1043,7 +1052,7 @@ static void release_level_ops(Arena& ar, Level& L) {
 
 int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s) {
   Level& L = H->L[0];
-  k_smoother_scale<<<grid_for(L.n, 256, H->num_sms, 8), 256, 0, s>>>(L.n, L.d, omega, L.s64,
+  k_smoother_scale<<<grid_for(L.n, 256, H->num_sms, 8), 256, 0, s>>>(L.n, L.dinv, omega, L.s64,
                                                                      L.s32);
   AMG_LAUNCH_CHECK();
   if (L.ah64) AMG_TRY(build_ah(H->arena, L, H->num_sms, s));
@@ -1085,13 +1094,16 @@ int setup_hierarchy(amg_handle* H, const amg_csr* A, cudaStream_t s, const amg_h
     const double* va = l == 0 ? A->val : H->L[l].val;
     double* diag = nullptr;
     AMG_TRY(ar.alloc_n(&H->L[l].d, n));
+    AMG_TRY(ar.alloc_n(&H->L[l].dinv, n));
     AMG_TRY(ar.alloc_n(&H->L[l].s64, n));
     if (f32) AMG_TRY(ar.alloc_n(&H->L[l].s32, n));
     AMG_TRY(ar.alloc_n(&diag, n));
     const int g1 = grid_for(n, 256, sms, 8);
     k_l1_diag<<<g1, 256, 0, s>>>(n, rp, ci, va, H->L[l].d, diag);
     AMG_LAUNCH_CHECK();
-    k_smoother_scale<<<g1, 256, 0, s>>>(n, H->L[l].d, nullptr, H->L[l].s64, H->L[l].s32);
+    k_recip<<<g1, 256, 0, s>>>(n, H->L[l].d, H->L[l].dinv);
+    AMG_LAUNCH_CHECK();
+    k_smoother_scale<<<g1, 256, 0, s>>>(n, H->L[l].dinv, nullptr, H->L[l].s64, H->L[l].s32);
     AMG_LAUNCH_CHECK();
     if (like) {  // new values on an assembled hierarchy: its aggregates, no matching
       ar.release(diag);

@@ -51,6 +51,11 @@ class Mlp:
         self.omega_max = float(omega_max)
         _check(self._lib.mlp_set_omega_max(self.h, self.omega_max), "mlp_set_omega_max")
 
+    def set_exact_forward(self, exact: bool = True) -> None:
+        """FP32 CUDA-core forward pass (True) or the tensor-core one (False, default)."""
+        _check(self._lib.mlp_set_exact_forward(self.h, 1 if exact else 0),
+               "mlp_set_exact_forward")
+
     def start_at_plain_smoother(self) -> None:
         """Output bias so that a zero hidden signal gives omega = 1 (plain
         l1-Jacobi) under the cap omega_max > 1: sigmoid(b3) = 1 / omega_max."""
@@ -213,15 +218,22 @@ def evaluate(weights: str | None, side: int = 256, sigma: float = 2.5, seed: int
     feat = mlp.features(Ad, (side, side, side))
     om = mlp.forward(feat)
     # inference cost per evaluation: features + forward + new smoother scales
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(repeats):
-        feat = mlp.features(Ad, (side, side, side))
-        om = mlp.forward(feat)
+    def ms(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(repeats):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / repeats
+
+    def infer():
+        mlp.forward(mlp.features(Ad, (side, side, side)), out=om)
         H.set_smoother_weights(om)
-    e1.record()
-    torch.cuda.synchronize()
-    out["inference_ms"] = e0.elapsed_time(e1) / repeats
+
+    out["inference_ms"] = ms(infer)
+    out["features_ms"] = ms(lambda: mlp.features(Ad, (side, side, side)))
+    out["set_weights_ms"] = ms(lambda: H.set_smoother_weights(om))
     fw0, fw1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fw0.record()
     for _ in range(repeats):

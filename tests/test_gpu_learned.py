@@ -35,7 +35,9 @@ def test_forward_backward_match_oracle(amg, orc, lm):
     p = (0.5 * standard_normal(21, m.nparam)).astype(np.float32)
     m.set_params(p)
     feat = m.features(amg.csr_to_device(A), shape)
+    m.set_exact_forward(True)  # FP32 on the CUDA cores
     om = m.forward(feat).cpu().numpy()
+    m.set_exact_forward(False)
     f64 = feat.cpu().numpy().astype(np.float64)
     om_o, _ = orc.mlp_forward(p.astype(np.float64), f64)
     np.testing.assert_allclose(om, om_o, rtol=2e-5, atol=1e-6)
@@ -49,12 +51,54 @@ def test_forward_backward_match_oracle(amg, orc, lm):
     np.testing.assert_allclose(m.grad(), 2 * g, rtol=1e-12)
 
 
+@pytest.mark.parametrize("shape,omega_max", [((10, 9, 8), 1.0), ((7, 6, 5), 1.0),
+                                             ((7, 6, 5), 1.9)])
+def test_tensor_core_forward_matches_oracle(amg, orc, lm, shape, omega_max):
+    # TF32 operands keep 10 mantissa bits: omega within 3e-3 of the FP64 network
+    # (210 rows: a ragged last tile of 16)
+    A = _problem(shape)
+    n = shape[0] * shape[1] * shape[2]
+    m = lm.Mlp(2, omega_max)
+    p = (0.5 * standard_normal(23, m.nparam)).astype(np.float32)
+    p[-1] = 1.0
+    m.set_params(p)
+    feat = m.features(amg.csr_to_device(A), shape)
+    om = m.forward(feat).cpu().numpy()
+    om_o, _ = orc.mlp_forward(p.astype(np.float64), feat.cpu().numpy().astype(np.float64),
+                              omega_max)
+    err = np.abs(om - om_o).max()
+    print("tensor-core forward: max |omega - omega_oracle| = %.2e over %d rows" % (err, n))
+    assert err <= 3e-3
+    assert om.min() > 0.0 and om.max() <= omega_max
+
+
+def test_fast_gelu_error_bound(amg):
+    # the tensor-core forward's GELU (erf by Abramowitz & Stegun 7.1.26, within
+    # 1.5e-7 of erf) against the exact GELU in float64
+    import ctypes as C
+
+    from paper_2406_19754_gb300 import _lib
+
+    u = torch.linspace(-9.0, 9.0, 200001, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(u)
+    lib = _lib.load()
+    assert lib.mlp_debug_gelu(C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()), u.numel(),
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0
+    torch.cuda.synchronize()
+    ud = u.double().cpu()
+    exact = torch.nn.functional.gelu(ud)
+    err = (out.double().cpu() - exact).abs() / ud.abs().clamp(min=1.0)
+    print("fast GELU: max |error| / max(1, |u|) = %.2e" % float(err.max()))
+    assert float(err.max()) <= 3e-7
+
+
 @pytest.mark.parametrize("omega_max", [1.5, 1.9])
 def test_forward_backward_with_omega_cap(amg, orc, lm, omega_max):
     # omega = max(omega_max sigmoid(z), 1e-3): the over-relaxing form of the network
     A, shape = _problem(), (10, 9, 8)
     n = 720
     m = lm.Mlp(4, omega_max)
+    m.set_exact_forward(True)
     p = (0.5 * standard_normal(22, m.nparam)).astype(np.float32)
     p[-1] = 3.0  # output bias: most rows above omega = 1
     m.set_params(p)
