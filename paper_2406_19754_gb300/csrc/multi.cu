@@ -64,12 +64,13 @@ constexpr int MV_U = 4;
 // thread); their grids are sized to one full wave of that.
 constexpr int MV_BLOCKS = 4;
 
-template <int KPL, typename AccT, typename V, typename G>
+// The row helpers below add to acc as the caller set it (0, or the start value
+// of a folded subtraction); NEG subtracts each entry's product instead (an
+// FMA with the negated value), as the single-vector kernels do.
+template <int KPL, typename AccT, bool NEG = false, typename V, typename G>
 __device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, int K, int lane,
                                        AccT (&acc)[KPL], G g) {
   const RowSpan r = row_span(A, i, C);
-#pragma unroll
-  for (int q = 0; q < KPL; ++q) acc[q] = AccT(0);
   for (int k0 = 0; k0 < r.w; k0 += MV_U) {
     int jj[MV_U];
     AccT aa[MV_U];
@@ -97,7 +98,7 @@ __device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, i
 #pragma unroll
         for (int q = 0; q < KPL; ++q) {
           const int c = lane + 32 * q;
-          if (c < K) acc[q] = fma(aa[u], gg[u][q], acc[q]);
+          if (c < K) acc[q] = fma(NEG ? -aa[u] : aa[u], gg[u][q], acc[q]);
         }
   }
 }
@@ -129,7 +130,7 @@ __device__ __forceinline__ bool stage_slice(const SellView<V>& A, int64_t sl, in
   return true;
 }
 
-template <int KPL, typename T, typename G>
+template <int KPL, bool NEG = false, typename T, typename G>
 __device__ __forceinline__ void staged_row(const int32_t* scol, const T* sval, int C, int w,
                                            int r, int K, int lane, T (&acc)[KPL], G g) {
   T gg[SL_MAXW][KPL];
@@ -141,11 +142,9 @@ __device__ __forceinline__ void staged_row(const int32_t* scol, const T* sval, i
       gg[u][q] = (u < w && c < K) ? g(scol[u * C + r], c) : T(0);
     }
 #pragma unroll
-  for (int q = 0; q < KPL; ++q) acc[q] = T(0);
-#pragma unroll
   for (int u = 0; u < SL_MAXW; ++u)
     if (u < w) {
-      const T a = sval[u * C + r];
+      const T a = NEG ? -sval[u * C + r] : sval[u * C + r];
 #pragma unroll
       for (int q = 0; q < KPL; ++q)
         if (lane + 32 * q < K) acc[q] = fma(a, gg[u][q], acc[q]);
@@ -155,7 +154,7 @@ __device__ __forceinline__ void staged_row(const int32_t* scol, const T* sval, i
 // Two rows of a staged slice at once (the second when two): all gathers of
 // both rows are in flight before either row's FMAs, so a warp waits one
 // gather latency per pair of rows.
-template <int KPL, typename T, typename G>
+template <int KPL, bool NEG = false, typename T, typename G>
 __device__ __forceinline__ void staged_rows2(const int32_t* scol, const T* sval, int C, int w,
                                              int r, bool two, int K, int lane, T (&acc0)[KPL],
                                              T (&acc1)[KPL], G g) {
@@ -170,12 +169,10 @@ __device__ __forceinline__ void staged_rows2(const int32_t* scol, const T* sval,
       g1[u][q] = in && two ? g(scol[u * C + r + 1], c) : T(0);
     }
 #pragma unroll
-  for (int q = 0; q < KPL; ++q) acc0[q] = acc1[q] = T(0);
-#pragma unroll
   for (int u = 0; u < SL_MAXW; ++u)
     if (u < w) {
-      const T a0 = sval[u * C + r];
-      const T a1 = two ? sval[u * C + r + 1] : T(0);
+      const T a0 = NEG ? -sval[u * C + r] : sval[u * C + r];
+      const T a1 = two ? (NEG ? -sval[u * C + r + 1] : sval[u * C + r + 1]) : T(0);
 #pragma unroll
       for (int q = 0; q < KPL; ++q)
         if (lane + 32 * q < K) {
@@ -260,11 +257,20 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     const int rows = (int)(Ah.n - i0 < C ? Ah.n - i0 : C);
     int w;
     const bool staged = stage_slice(Ah, sl, C, lane, scol, sval, w);
+    // r = b - Ah b as the single-vector kernels form it: from b down by
+    // negated FMAs
+    auto start = [&](int64_t i, T(&acc)[KPL]) {
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) {
+        const int c = lane + 32 * q;
+        acc[q] = c < K ? to_f(B[i * K + c], T(0)) : T(0);
+      }
+    };
     auto finish = [&](int64_t i, const T(&acc)[KPL]) {
 #pragma unroll
       for (int q = 0; q < KPL; ++q) {
         const int c = lane + 32 * q;
-        if (c < K) R[i * K + c] = to_f(B[i * K + c], T(0)) - acc[q];
+        if (c < K) R[i * K + c] = acc[q];
       }
     };
     // FP32 vectors: two rows in flight; FP64 ones (twice the registers): one
@@ -272,13 +278,15 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     for (int r = 0; r < rows; r += RS) {
       const bool two = RS == 2 && r + 1 < rows;
       T acc0[KPL], acc1[KPL];
+      start(i0 + r, acc0);
+      if (two) start(i0 + r + 1, acc1);
       if (staged && RS == 2) {
-        staged_rows2<KPL>(scol, sval, C, w, r, two, K, lane, acc0, acc1, gather);
+        staged_rows2<KPL, true>(scol, sval, C, w, r, two, K, lane, acc0, acc1, gather);
       } else if (staged) {
-        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc0, gather);
+        staged_row<KPL, true>(scol, sval, C, w, r, K, lane, acc0, gather);
       } else {
-        row_mv<KPL, T>(Ah, i0 + r, C, K, lane, acc0, gather);
-        if (two) row_mv<KPL, T>(Ah, i0 + r + 1, C, K, lane, acc1, gather);
+        row_mv<KPL, T, true>(Ah, i0 + r, C, K, lane, acc0, gather);
+        if (two) row_mv<KPL, T, true>(Ah, i0 + r + 1, C, K, lane, acc1, gather);
       }
       finish(i0 + r, acc0);
       if (two) finish(i0 + r + 1, acc1);
@@ -349,6 +357,15 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     const int rows = (int)(AP.n - i0 < C ? AP.n - i0 : C);
     int w;
     const bool staged = stage_slice(AP, sl, C, lane, scol, sval, w);
+    // z = s (b + r - AP x_c) + x_c[agg] as the single-vector kernels form it:
+    // from b + r down by negated FMAs, then one FMA
+    auto start = [&](int64_t i, T(&acc)[KPL]) {
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) {
+        const int c = lane + 32 * q;
+        acc[q] = c < K ? to_f(B[i * K + c], T(0)) + R[i * K + c] : T(0);
+      }
+    };
     auto finish = [&](int64_t i, const T(&acc)[KPL]) {
       const T si = s[i];
       const int64_t ai = agg[i];
@@ -356,9 +373,7 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
       for (int q = 0; q < KPL; ++q) {
         const int c = lane + 32 * q;
         if (c < K) {
-          const T bi = to_f(B[i * K + c], T(0));
-          const T yi = si * bi + Xc[ai * K + c];
-          const XT zi = to_f(yi + si * (R[i * K + c] - acc[q]), XT(0));
+          const XT zi = to_f(fma(si, acc[q], Xc[ai * K + c]), XT(0));
           Z[i * K + c] = zi;
           if (DOTS) {
             d[0][q] += (double)B[i * K + c] * (double)zi;
@@ -372,13 +387,15 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     for (int r = 0; r < rows; r += RS) {
       const bool two = RS == 2 && r + 1 < rows;
       T acc0[KPL], acc1[KPL];
+      start(i0 + r, acc0);
+      if (two) start(i0 + r + 1, acc1);
       if (staged && RS == 2) {
-        staged_rows2<KPL>(scol, sval, C, w, r, two, K, lane, acc0, acc1, gather);
+        staged_rows2<KPL, true>(scol, sval, C, w, r, two, K, lane, acc0, acc1, gather);
       } else if (staged) {
-        staged_row<KPL>(scol, sval, C, w, r, K, lane, acc0, gather);
+        staged_row<KPL, true>(scol, sval, C, w, r, K, lane, acc0, gather);
       } else {
-        row_mv<KPL, T>(AP, i0 + r, C, K, lane, acc0, gather);
-        if (two) row_mv<KPL, T>(AP, i0 + r + 1, C, K, lane, acc1, gather);
+        row_mv<KPL, T, true>(AP, i0 + r, C, K, lane, acc0, gather);
+        if (two) row_mv<KPL, T, true>(AP, i0 + r + 1, C, K, lane, acc1, gather);
       }
       finish(i0 + r, acc0);
       if (two) finish(i0 + r + 1, acc1);
@@ -480,6 +497,8 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
   for (int q = 0; q < KPL; ++q) d[0][q] = d[1][q] = 0.0;
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < A.n; i += nw) {
     double acc[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) acc[q] = 0.0;
     row_mv<KPL, double>(A, i, C, K, lane, acc,
                         [&](int j, int c) { return __ldg(X + (int64_t)j * K + c); });
 #pragma unroll
@@ -540,6 +559,8 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     for (int r = 0; r < rows; ++r) {
       const int64_t i = i0 + r;
       double acc[KPL];
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) acc[q] = 0.0;
       if (staged)
         staged_row<KPL>(scol, sval, C, w, r, K, lane, acc, gather);
       else

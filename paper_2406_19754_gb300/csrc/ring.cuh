@@ -269,35 +269,40 @@ struct RingWarp {
   }
 };
 
-// acc + sum of a_k g(col_k) for k = k0 .. k0 + N - 1, k ascending: the N
-// gathers issue together, then the FMAs follow in order.  Exactly N FMAs:
-// on GB300's FP64 pipe a predicated-off FMA would still cost its cycles.
-template <int N, typename T, typename V, typename G>
+// acc + sum of a_k g(col_k) (NEG: acc - sum, by FMAs with the negated
+// values) for k = k0 .. k0 + N - 1, k ascending: the N gathers issue
+// together, then the FMAs follow in order.  Exactly N FMAs: on GB300's FP64
+// pipe a predicated-off FMA would still cost its cycles.
+template <int N, bool NEG, typename T, typename V, typename G>
 __device__ __forceinline__ T ring_chunk(const RingWarp<V>& ring, int k0, T acc, G g) {
   T x[N];
 #pragma unroll
   for (int u = 0; u < N; ++u) x[u] = g(ring.col(k0 + u));
 #pragma unroll
-  for (int u = 0; u < N; ++u) acc = fma(to_f(ring.val(k0 + u), T(0)), x[u], acc);
+  for (int u = 0; u < N; ++u) {
+    const T a = to_f(ring.val(k0 + u), T(0));
+    acc = fma(NEG ? -a : a, x[u], acc);
+  }
   return acc;
 }
 
-// sum_k a_k g(col_k) over the w entries of this lane's row in the current
-// stage, k ascending (the per-lane kernels' order): chunks of 8 and one
-// remainder chunk of the exact length (w is warp-uniform).
-template <typename T, typename V, typename G>
-__device__ __forceinline__ T ring_row_sum(const RingWarp<V>& ring, int w, G g) {
-  T acc = T(0);
+// init + sum_k a_k g(col_k) (NEG: init - sum) over the w entries of this
+// lane's row in the current stage, k ascending (the per-lane kernels'
+// order): chunks of 8 and one remainder chunk of the exact length (w is
+// warp-uniform).
+template <typename T, bool NEG = false, typename V, typename G>
+__device__ __forceinline__ T ring_row_sum(const RingWarp<V>& ring, int w, G g, T init = T(0)) {
+  T acc = init;
   int k0 = 0;
-  for (; k0 + 8 <= w; k0 += 8) acc = ring_chunk<8>(ring, k0, acc, g);
+  for (; k0 + 8 <= w; k0 += 8) acc = ring_chunk<8, NEG>(ring, k0, acc, g);
   switch (w - k0) {
-    case 1: acc = ring_chunk<1>(ring, k0, acc, g); break;
-    case 2: acc = ring_chunk<2>(ring, k0, acc, g); break;
-    case 3: acc = ring_chunk<3>(ring, k0, acc, g); break;
-    case 4: acc = ring_chunk<4>(ring, k0, acc, g); break;
-    case 5: acc = ring_chunk<5>(ring, k0, acc, g); break;
-    case 6: acc = ring_chunk<6>(ring, k0, acc, g); break;
-    case 7: acc = ring_chunk<7>(ring, k0, acc, g); break;
+    case 1: acc = ring_chunk<1, NEG>(ring, k0, acc, g); break;
+    case 2: acc = ring_chunk<2, NEG>(ring, k0, acc, g); break;
+    case 3: acc = ring_chunk<3, NEG>(ring, k0, acc, g); break;
+    case 4: acc = ring_chunk<4, NEG>(ring, k0, acc, g); break;
+    case 5: acc = ring_chunk<5, NEG>(ring, k0, acc, g); break;
+    case 6: acc = ring_chunk<6, NEG>(ring, k0, acc, g); break;
+    case 7: acc = ring_chunk<7, NEG>(ring, k0, acc, g); break;
     default: break;
   }
   return acc;

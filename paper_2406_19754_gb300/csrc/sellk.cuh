@@ -45,11 +45,15 @@ struct Lanes {
 // sliceptr + k C + i mod C), and the row's entries are visited in the same
 // order.  Compressed columns (SELL_D16 in the layout code; A.d16 set) give
 // the same j for every slot, so the sum is the same bits either way.
-template <int TPR, typename AccT, typename V, typename G>
+//
+// NEG: init - sum_k a_k g(col_k) instead, each entry by an FMA with the
+// negated value (no separate subtraction); init is added by the row's first
+// lane (t == 0) only.
+template <int TPR, typename AccT, bool NEG = false, typename V, typename G>
 __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const Lanes<TPR>& ln,
-                                         G g) {
+                                         G g, AccT init = AccT(0)) {
   constexpr int C = Lanes<TPR>::C, W = Lanes<TPR>::W;
-  AccT acc = AccT(0);
+  AccT acc = ln.t == 0 ? init : AccT(0);
   if (!A.row0 && A.C != C) {
     const int64_t i = s * C + ln.r;
     if (i < A.n) {
@@ -65,7 +69,7 @@ __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const 
         for (int k = ln.t; k < w; k += W) {
           const int j = __ldg(bp + k) + (int)ld_stream(dp + (int64_t)k * A.C);
           const AccT a = to_f(ld_stream(vp + (int64_t)k * A.C), AccT(0));
-          acc = fma(a, g(j), acc);
+          acc = fma(NEG ? -a : a, g(j), acc);
         }
       } else {
         const int32_t* cp = A.col + beg;
@@ -73,7 +77,7 @@ __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const 
         for (int k = ln.t; k < w; k += W) {
           const int j = ld_stream(cp + (int64_t)k * A.C);
           const AccT a = to_f(ld_stream(vp + (int64_t)k * A.C), AccT(0));
-          acc = fma(a, g(j), acc);
+          acc = fma(NEG ? -a : a, g(j), acc);
         }
       }
     }
@@ -91,7 +95,7 @@ __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const 
     for (int k = ln.t; k < w; k += W) {
       const int j = __ldg(bp + k) + (int)ld_stream(dp + (int64_t)k * C);
       const AccT a = to_f(ld_stream(vp + (int64_t)k * C), AccT(0));
-      acc = fma(a, g(j), acc);
+      acc = fma(NEG ? -a : a, g(j), acc);
     }
   } else {
     const int32_t* cp = A.col + beg + ln.r;
@@ -99,7 +103,7 @@ __device__ __forceinline__ AccT sell_row(const SellView<V>& A, int64_t s, const 
     for (int k = ln.t; k < w; k += W) {
       const int j = ld_stream(cp + (int64_t)k * C);
       const AccT a = to_f(ld_stream(vp + (int64_t)k * C), AccT(0));
-      acc = fma(a, g(j), acc);
+      acc = fma(NEG ? -a : a, g(j), acc);
     }
   }
 #pragma unroll

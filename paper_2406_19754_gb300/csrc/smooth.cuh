@@ -39,12 +39,16 @@ struct LdL2 {
   }
 };
 
+// r_i = b_i - (Ah b)_i, accumulated from b_i down (negated FMAs: one FP64
+// instruction an entry and none for the subtraction).
 template <int TPR, typename Ld, typename V, typename T, typename BT>
 __device__ __forceinline__ void pre_slice(const SellView<V>& Ah, const BT* b, T* r, int64_t sl,
                                           const Lanes<TPR>& ln) {
-  const T acc = sell_row<TPR, T>(Ah, sl, ln, [&](int j) { return to_f(Ld::ld(b + j), T(0)); });
   const int64_t i = lane_row(Ah, sl, ln);
-  if (i >= 0) r[i] = to_f(Ld::ld(b + i), T(0)) - acc;
+  const T bi = i >= 0 ? to_f(Ld::ld(b + i), T(0)) : T(0);
+  const T acc = sell_row<TPR, T, true>(
+      Ah, sl, ln, [&](int j) { return to_f(Ld::ld(b + j), T(0)); }, bi);
+  if (i >= 0) r[i] = acc;
 }
 
 template <typename Ld, typename T>
@@ -62,16 +66,29 @@ __device__ __forceinline__ T restrict_sum(const int32_t* m, int stride, const T*
 // xp: the pre-smoothed x when more than one sweep made it (else it is S b);
 // e: if set, receives the residual b - A y of y = xp + P x_c, which further
 // post-smoothing sweeps start from.
+// One sweep (xp and e null): z_i = s_i (b_i + r_i - (AP x_c)_i) + x_c[agg(i)]
+// (= S b + P x_c + S (r - AP x_c)), accumulated from b_i + r_i down with
+// negated FMAs, then one FMA.
 template <int TPR, typename Ld, typename V, typename T, typename BT, typename XT>
 __device__ __forceinline__ int64_t post_slice(const SellView<V>& AP, const BT* b, const T* s,
                                               const T* r, const int32_t* agg, const T* xc, XT* x,
                                               int64_t sl, const Lanes<TPR>& ln, XT& z,
                                               const T* xp = nullptr, T* e = nullptr) {
+  if (!xp && !e) {
+    const int64_t i = lane_row(AP, sl, ln);
+    const T init = i >= 0 ? to_f(Ld::ld(b + i), T(0)) + Ld::ld(r + i) : T(0);
+    const T acc =
+        sell_row<TPR, T, true>(AP, sl, ln, [&](int J) { return Ld::ld(xc + J); }, init);
+    if (i >= 0) {
+      z = to_f(fma(s[i], acc, Ld::ld(xc + agg[i])), XT(0));
+      x[i] = z;
+    }
+    return i;
+  }
   const T acc = sell_row<TPR, T>(AP, sl, ln, [&](int J) { return Ld::ld(xc + J); });
   const int64_t i = lane_row(AP, sl, ln);
   if (i >= 0) {
-    // explicit FMAs: every kernel that runs this (and the multi-RHS kernels,
-    // which contract the same expressions) rounds identically
+    // explicit FMAs: every kernel that runs this rounds identically
     const T si = s[i];
     const T xci = Ld::ld(xc + agg[i]);
     const T yi = xp ? Ld::ld(xp + i) + xci : fma(si, to_f(Ld::ld(b + i), T(0)), xci);

@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(RING_THREADS, 4)
       ring.drain();
       return;
     }
-    const T acc =
-        ring_row_sum<T>(ring, ring.width(), [&](int j) { return to_f(__ldg(b + j), T(0)); });
-    if (has) r[i] = bi - acc;
+    // pre_slice's arithmetic: from b_i down by negated FMAs
+    const T acc = ring_row_sum<T, true>(
+        ring, ring.width(), [&](int j) { return to_f(__ldg(b + j), T(0)); }, bi);
+    if (has) r[i] = acc;
     ring.release();
   }
 }
@@ -204,12 +205,12 @@ __global__ void __launch_bounds__(RING_THREADS, 4)
     }
     // x_c of the row's own aggregate: gathered with the row's entries
     const T xci = has ? __ldg(xc + ai) : T(0);
-    const T acc = ring_row_sum<T>(ring, ring.width(), [&](int J) { return __ldg(xc + J); });
+    // post_slice's arithmetic (one sweep): from b_i + r_i down, then one FMA
+    const T init = has ? to_f(bi, T(0)) + ri : T(0);
+    const T acc =
+        ring_row_sum<T, true>(ring, ring.width(), [&](int J) { return __ldg(xc + J); }, init);
     if (has) {
-      // post_slice's expressions, in its order
-      const T yi = fma(si, to_f(bi, T(0)), xci);
-      const T ei = ri - acc;
-      const XT zi = to_f(fma(si, ei, yi), XT(0));
+      const XT zi = to_f(fma(si, acc, xci), XT(0));
       x[i] = zi;
       if constexpr (NDOT > 0) d[0] += (double)bi * (double)zi;
       if constexpr (NDOT > 1) d[NDOT > 1 ? 1 : 0] += (double)zi * qi;
