@@ -535,6 +535,18 @@ int amg_debug_tail_timeout(amg_handle* H, int on);
  */
 int mlp_debug_gelu(const float* u, float* out, int64_t n, amg_stream_t stream);
 
+/*
+ * The V-cycle kernels' precision conversions on n device elements:
+ * out32[i] = in64[i] rounded to binary32 (nearest, ties to even) and
+ * out64[i] = in32[i] widened to binary64, both by the integer-pipe routines
+ * the FP32 hierarchies' kernels use, so tests can compare them bit for bit
+ * with the hardware conversions.  Either pair may be NULL.  No counterpart in
+ * the paper (its FP32 runs are not mixed-precision).  Errors: AMG_ERR_ARG
+ * (n < 0, or one pointer of a pair NULL).  Asynchronous.
+ */
+int amg_debug_convert(const double* in64, float* out32, const float* in32, double* out64,
+                      int64_t n, amg_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

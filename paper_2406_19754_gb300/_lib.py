@@ -112,6 +112,7 @@ SIGNATURES = {
     "amg_pairwise_match_noalloc": (C.c_int, [C.POINTER(AmgCsr), _P, C.POINTER(C.c_int), _P]),
     "amg_debug_fail_alloc_after": (C.c_int, [C.c_long]),
     "mlp_debug_gelu": (C.c_int, [_P, _P, C.c_int64, _P]),
+    "amg_debug_convert": (C.c_int, [_P, _P, _P, _P, C.c_int64, _P]),
     "amg_debug_tail_timeout": (C.c_int, [_P, C.c_int]),
 }
 

@@ -319,6 +319,12 @@ int amg_vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kern
   return vcycle_profile(H, r, z, out, max_out, count, (cudaStream_t)stream);
 }
 
+int amg_debug_convert(const double* in64, float* out32, const float* in32, double* out64,
+                      int64_t n, amg_stream_t stream) {
+  if (n < 0 || (!in64) != (!out32) || (!in32) != (!out64)) return AMG_ERR_ARG;
+  return debug_convert(in64, out32, in32, out64, n, (cudaStream_t)stream);
+}
+
 int amg_spmv(const amg_handle* H, int level, double alpha, const double* x, double beta,
              double* y, amg_stream_t stream) {
   if (!H || level < 0 || level >= (int)H->L.size() || !x || !y || (const double*)y == x)

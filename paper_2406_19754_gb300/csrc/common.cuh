@@ -339,6 +339,72 @@ __device__ __forceinline__ double to_f(__nv_bfloat16 v, double) {
   return (double)__bfloat162float(v);
 }
 
+// Conversions between binary64 and binary32 on the integer pipe, for kernels
+// that convert every element of a blocked (N x K) vector.  GB300's FP64 pipe,
+// which also executes the conversion instructions, retires about two lane
+// operations per SM clock, so such a kernel is bound by it.  For a value in
+// binary32's normal range the conversions are bit operations on the IEEE 754
+// encodings (1 sign, 11 exponent bits biased by 1023 and 52 fraction bits;
+// 1, 8 biased by 127, 23): rebias the exponent, keep the top 23 fraction
+// bits, and round to nearest, ties to even, on the 29 dropped bits.  Zeros
+// take the bit path too.  Any other input (NaN, infinity, subnormal or out of
+// range: rare in the solver's vectors) clears `ok`, and the array forms below
+// then convert the whole array in hardware.  There is no branch per element,
+// so a caller's loads all issue before the first conversion.  The results are
+// the hardware conversion's bits.
+__device__ __forceinline__ float f64_to_f32_bits(double x, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const bool in = e - 897u < 254u;  // binary32 biased exponent e - 896 in 1..254
+  uint32_t r = ((e - 896u) << 23) | (__funnelshift_l(lo, hi, 3) & 0x7FFFFFu);
+  // carry out of the dropped bits: above half, or exactly half and r odd; a
+  // carry out of the fraction steps the exponent (to infinity past 254)
+  r += ((lo & 0x1FFFFFFFu) + 0x0FFFFFFFu + (r & 1u)) >> 29;
+  ok = ok && (in || ((hi << 1) | lo) == 0u);
+  return __uint_as_float((hi & 0x80000000u) | (in ? r : 0u));
+}
+
+// Exact: a normal binary32 value's exponent rebiased by 1023 - 127 = 896,
+// its 23 fraction bits the top of the 52.
+__device__ __forceinline__ double f32_to_f64_bits(float f, bool& ok) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t m = u & 0x7FFFFFFFu;
+  const bool in = (m >> 23) - 1u < 254u;  // biased exponent 1..254
+  ok = ok && (in || m == 0u);
+  return __hiloint2double((int)((u & 0x80000000u) | (in ? (m >> 3) + (896u << 20) : 0u)),
+                          (int)(in ? u << 29 : 0u));
+}
+
+template <int N>
+__device__ __forceinline__ void cvt_n(const double (&in)[N], float (&out)[N]) {
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < N; ++q) out[q] = f64_to_f32_bits(in[q], ok);
+  if (!ok)
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = __double2float_rn(in[q]);
+}
+template <int N>
+__device__ __forceinline__ void cvt_n(const float (&in)[N], double (&out)[N]) {
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < N; ++q) out[q] = f32_to_f64_bits(in[q], ok);
+  if (!ok)
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = (double)in[q];
+}
+template <int N, typename T>
+__device__ __forceinline__ void cvt_n(const T (&in)[N], T (&out)[N]) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) out[q] = in[q];
+}
+template <int N>
+__device__ __forceinline__ void cvt_n(const __nv_bfloat16 (&in)[N], float (&out)[N]) {
+#pragma unroll
+  for (int q = 0; q < N; ++q) out[q] = __bfloat162float(in[q]);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -509,6 +575,8 @@ int set_level0_weights(amg_handle* H, const float* omega, cudaStream_t s);
 // the level-0 pre-smoother instead of converting every FP64 element.
 int vcycle_run(const amg_handle* H, const double* r, double* z, int dots, const double* q,
                cudaStream_t s, double* slice_part = nullptr, const float* r32 = nullptr);
+int debug_convert(const double* in64, float* out32, const float* in32, double* out64,
+                  int64_t n, cudaStream_t s);
 int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_time* out,
                    int max_out, int* count, cudaStream_t s);
 int time_level(const amg_handle* H, int l, int reps, const double* b64, double* z64, float* ms,

@@ -116,15 +116,54 @@ __device__ __forceinline__ void row_mv(const SellView<V>& A, int64_t i, int C, i
 constexpr int SL_MAXW = 8;
 constexpr int SL_CAP = SL_MAXW * 32;
 
+// Asynchronous 4- and 8-byte copies global -> shared (cp.async): the copies of a
+// whole slice are in flight at once without holding registers.
+template <int N>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc) {
+  static_assert(N == 4 || N == 8, "4- or 8-byte copies");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(
+                   (unsigned)__cvta_generic_to_shared(sdst)),
+               "l"(__cvta_generic_to_global(gsrc)), "n"(N)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 template <typename V, typename T>
 __device__ __forceinline__ bool stage_slice(const SellView<V>& A, int64_t sl, int C, int lane,
                                             int32_t* scol, T* sval, int& w) {
   const int64_t beg = __ldg(A.sliceptr + sl);
   w = (int)((__ldg(A.sliceptr + sl + 1) - beg) / C);
   if (w > SL_MAXW || w * C > SL_CAP) return false;  // slices of 64 rows fit fewer columns
-  for (int e = lane; e < w * C; e += 32) {
-    scol[e] = __ldg(A.col + beg + e);
-    sval[e] = to_f(__ldg(A.val + beg + e), T(0));
+  const int m = w * C;
+  if constexpr (sizeof(V) == sizeof(T)) {  // values stored as computed: copied as they are
+    for (int e = lane; e < m; e += 32) {
+      cp_async<4>(scol + e, A.col + beg + e);
+      cp_async<sizeof(T)>(sval + e, A.val + beg + e);
+    }
+    cp_async_wait_all();
+  } else {  // BF16 values widened on the way: four entries a lane in flight per round
+    for (int e0 = 0; e0 < m; e0 += 128) {
+      int32_t cc[4];
+      V vv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = e0 + lane + 32 * k;
+        if (e < m) {
+          cc[k] = __ldg(A.col + beg + e);
+          vv[k] = __ldg(A.val + beg + e);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int e = e0 + lane + 32 * k;
+        if (e < m) {
+          scol[e] = cc[k];
+          sval[e] = to_f(vv[k], T(0));
+        }
+      }
+    }
   }
   __syncwarp();
   return true;
@@ -184,16 +223,11 @@ __device__ __forceinline__ void staged_rows2(const int32_t* scol, const T* sval,
 
 // Column sums over the grid: per-block sums in fixed warp order, then the
 // last block adds the blocks in order and calls epi(c, t) for every column.
-template <int KPL, int NV, typename Epi>
-__device__ void cols_reduce(double (&v)[NV][KPL], int K, double* part, int maxb,
-                            unsigned* ticket, Epi epi) {
-  __shared__ double sh[NV][MROWS_BLOCK / 32][64];
+// sh[m][w][c]: warp w's sum of value m for column c.
+template <int NV, typename Epi>
+__device__ void cols_finish(double (&sh)[NV][MROWS_BLOCK / 32][64], int K, double* part,
+                            int maxb, unsigned* ticket, Epi epi) {
   __shared__ bool last;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int m = 0; m < NV; ++m)
-#pragma unroll
-    for (int q = 0; q < KPL; ++q) sh[m][w][lane + 32 * q] = v[m][q];
   __syncthreads();
   const int nw = blockDim.x >> 5;
   for (int t = threadIdx.x; t < NV * K; t += blockDim.x) {
@@ -236,6 +270,42 @@ __device__ void cols_reduce(double (&v)[NV][KPL], int K, double* part, int maxb,
     epi(threadIdx.x, t);
   }
   if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// Lane l holds columns l + 32 q.
+template <int KPL, int NV, typename Epi>
+__device__ void cols_reduce(double (&v)[NV][KPL], int K, double* part, int maxb,
+                            unsigned* ticket, Epi epi) {
+  __shared__ double sh[NV][MROWS_BLOCK / 32][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < NV; ++m)
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) sh[m][w][lane + 32 * q] = v[m][q];
+  cols_finish(sh, K, part, maxb, ticket, epi);
+}
+
+// Vector-column lanes (see k_m_pre_v): lane (rs, cg) holds columns
+// cg VW .. cg VW + VW - 1 of the rows it took; the warp's RW row lanes of a
+// column are added in row-lane order.
+template <int VW, int NV, typename Epi>
+__device__ void cols_reduce_v(double (&v)[NV][VW], int K, double* part, int maxb,
+                              unsigned* ticket, Epi epi) {
+  __shared__ double sh[NV][MROWS_BLOCK / 32][64];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int G = K / VW, RW = 32 / G, cg = lane % G, rs = lane / G;
+  for (int k = 0; k < RW; ++k) {
+    if (rs == k)
+#pragma unroll
+      for (int m = 0; m < NV; ++m)
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+          double& t = sh[m][w][cg * VW + j];
+          t = k == 0 ? v[m][j] : t + v[m][j];
+        }
+    __syncwarp();
+  }
+  cols_finish(sh, K, part, maxb, ticket, epi);
 }
 
 // ------------------------------------------------------------------ V-cycle kernels
@@ -292,6 +362,31 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
       if (two) finish(i0 + r + 1, acc1);
     }
     __syncwarp();  // the next slice overwrites the staging
+  }
+}
+
+// w = v rounded to FP32, four elements a thread (16-byte loads when v and w
+// are 16-byte aligned, vec = true).
+__global__ void k_m_to_f32(int64_t m, const double* __restrict__ v, float* __restrict__ w,
+                           bool vec) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * t < m;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 4 * t;
+    double a[4];
+    float b[4];
+    if (vec && i + 4 <= m) {
+      const double2 a0 = __ldcs((const double2*)(v + i)), a1 = __ldcs((const double2*)(v + i + 2));
+      a[0] = a0.x, a[1] = a0.y, a[2] = a1.x, a[3] = a1.y;
+      cvt_n(a, b);
+      *(float4*)(w + i) = make_float4(b[0], b[1], b[2], b[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[k] = i + k < m ? v[i + k] : 0.0;
+      cvt_n(a, b);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (i + k < m) w[i + k] = b[k];
+    }
   }
 }
 
@@ -360,24 +455,37 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     // z = s (b + r - AP x_c) + x_c[agg] as the single-vector kernels form it:
     // from b + r down by negated FMAs, then one FMA
     auto start = [&](int64_t i, T(&acc)[KPL]) {
+      BT bv[KPL];
+      T rr[KPL];
 #pragma unroll
       for (int q = 0; q < KPL; ++q) {
         const int c = lane + 32 * q;
-        acc[q] = c < K ? to_f(B[i * K + c], T(0)) + R[i * K + c] : T(0);
+        bv[q] = c < K ? B[i * K + c] : BT(0);
+        rr[q] = c < K ? R[i * K + c] : T(0);
       }
+      cvt_n(bv, acc);
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) acc[q] = acc[q] + rr[q];
     };
     auto finish = [&](int64_t i, const T(&acc)[KPL]) {
       const T si = s[i];
       const int64_t ai = agg[i];
+      T zt[KPL];
+#pragma unroll
+      for (int q = 0; q < KPL; ++q) {
+        const int c = lane + 32 * q;
+        zt[q] = c < K ? fma(si, acc[q], Xc[ai * K + c]) : T(0);
+      }
+      XT zv[KPL];
+      cvt_n(zt, zv);
 #pragma unroll
       for (int q = 0; q < KPL; ++q) {
         const int c = lane + 32 * q;
         if (c < K) {
-          const XT zi = to_f(fma(si, acc[q], Xc[ai * K + c]), XT(0));
-          Z[i * K + c] = zi;
+          Z[i * K + c] = zv[q];
           if (DOTS) {
-            d[0][q] += (double)B[i * K + c] * (double)zi;
-            d[1][q] += (double)zi * Q[i * K + c];
+            d[0][q] += (double)B[i * K + c] * (double)zv[q];
+            d[1][q] += (double)zv[q] * Q[i * K + c];
           }
         }
       }
@@ -403,6 +511,206 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     __syncwarp();
   }
   if constexpr (DOTS) cols_reduce<KPL, 2>(d, K, part, maxb, ticket, epi);
+}
+
+// ------------------------------------------------------------------ vector-column kernels
+//
+// The smoothers again, with each lane on VW = 16 / sizeof(T) adjacent columns
+// of one row (one 16-byte access per gathered row) instead of on columns
+// l and l + 32: lane l takes column group cg = l % G (G = K / VW groups) of
+// row rs = l / G of the RW = 32 / G rows a warp advances by per pass (lanes
+// past RW G idle).  A warp's gather then moves RW rows' K values in one
+// instruction, where the per-column kernels spend K / 32 instructions on one
+// row, so the slices' rows cost a fraction of the issue slots.  Per element the
+// arithmetic and its order are unchanged (start value, then one negated FMA
+// per ELL entry, padding included, then the final FMA), so the results are the
+// single-vector V-cycle's bits.  Used when VW divides K and every vector
+// starts on 16 bytes.
+
+template <int N>
+__device__ __forceinline__ void ld_cols(const float* __restrict__ p, float (&o)[N]) {
+  static_assert(N % 4 == 0, "four floats per access");
+#pragma unroll
+  for (int k = 0; k < N / 4; ++k) {
+    const float4 v = __ldg((const float4*)p + k);
+    o[4 * k] = v.x, o[4 * k + 1] = v.y, o[4 * k + 2] = v.z, o[4 * k + 3] = v.w;
+  }
+}
+template <int N>
+__device__ __forceinline__ void ld_cols(const double* __restrict__ p, double (&o)[N]) {
+  static_assert(N % 2 == 0, "two doubles per access");
+#pragma unroll
+  for (int k = 0; k < N / 2; ++k) {
+    const double2 v = __ldg((const double2*)p + k);
+    o[2 * k] = v.x, o[2 * k + 1] = v.y;
+  }
+}
+template <int N>
+__device__ __forceinline__ void st_cols(float* __restrict__ p, const float (&o)[N]) {
+#pragma unroll
+  for (int k = 0; k < N / 4; ++k)
+    ((float4*)p)[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+}
+template <int N>
+__device__ __forceinline__ void st_cols(double* __restrict__ p, const double (&o)[N]) {
+#pragma unroll
+  for (int k = 0; k < N / 2; ++k) ((double2*)p)[k] = make_double2(o[2 * k], o[2 * k + 1]);
+}
+
+// acc -= sum_k a_ik X[col_k, c0 ..] for the lane's row (staged slice, or the
+// row's entries from global memory when the slice did not fit the staging).
+template <int VW, typename V, typename T>
+__device__ __forceinline__ void rows_sub_v(const SellView<V>& A, bool staged, const int32_t* scol,
+                                           const T* sval, int C, int w, int r, int64_t i, int K,
+                                           int c0, const T* __restrict__ X, T (&acc)[VW]) {
+  if (staged) {
+    T g[SL_MAXW][VW];
+#pragma unroll
+    for (int u = 0; u < SL_MAXW; ++u) {
+      if (u < w) {
+        ld_cols(X + (int64_t)scol[u * C + r] * K + c0, g[u]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) g[u][k] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SL_MAXW; ++u)
+      if (u < w) {
+        const T a = -sval[u * C + r];
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[k] = fma(a, g[u][k], acc[k]);
+      }
+    return;
+  }
+  const RowSpan rw = row_span(A, i, C);
+  for (int k0 = 0; k0 < rw.w; k0 += MV_U) {
+    int jj[MV_U];
+    T aa[MV_U];
+    T g[MV_U][VW];
+#pragma unroll
+    for (int u = 0; u < MV_U; ++u) {
+      jj[u] = 0;
+      aa[u] = T(0);
+      if (k0 + u < rw.w) {
+        const int64_t e = rw.off + (int64_t)(k0 + u) * rw.stride;
+        jj[u] = __ldg(A.col + e);
+        aa[u] = to_f(__ldg(A.val + e), T(0));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < MV_U; ++u) {
+      if (k0 + u < rw.w) {
+        ld_cols(X + (int64_t)jj[u] * K + c0, g[u]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VW; ++k) g[u][k] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < MV_U; ++u)
+      if (k0 + u < rw.w)
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[k] = fma(-aa[u], g[u][k], acc[k]);
+  }
+}
+
+// R = B - Ah B (as k_m_pre), vector columns.
+template <typename V, typename T>
+__global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
+    k_m_pre_v(SellView<V> Ah, int C, int K, const T* __restrict__ B, T* __restrict__ R) {
+  constexpr int VW = 16 / sizeof(T);
+  __shared__ int32_t scol_all[MROWS_BLOCK / 32][SL_CAP];
+  __shared__ T sval_all[MROWS_BLOCK / 32][SL_CAP];
+  const int lane = threadIdx.x & 31;
+  const int G = K / VW, RW = 32 / G, cg = lane % G, rs = lane / G, c0 = cg * VW;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* scol = scol_all[threadIdx.x >> 5];
+  T* sval = sval_all[threadIdx.x >> 5];
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < Ah.nslices;
+       sl += nw) {
+    const int64_t i0 = sl * C;
+    const int rows = (int)(Ah.n - i0 < C ? Ah.n - i0 : C);
+    int w;
+    const bool staged = stage_slice(Ah, sl, C, lane, scol, sval, w);
+    for (int p = 0; p < rows; p += RW) {
+      const bool live = rs < RW && p + rs < rows;
+      const int r = live ? p + rs : 0;  // idle lanes shadow row 0 and store nothing
+      const int64_t i = i0 + r;
+      T acc[VW];
+      ld_cols(B + i * K + c0, acc);
+      rows_sub_v<VW>(Ah, staged, scol, sval, C, w, r, i, K, c0, B, acc);
+      if (live) st_cols(R + i * K + c0, acc);
+    }
+    __syncwarp();  // the next slice overwrites the staging
+  }
+}
+
+// Z = s (B + R - AP Xc) + Xc[agg] (as k_m_post), vector columns; with DOTS
+// the column sums (B, Z) and (Z, Q) go to epi.
+template <typename V, typename T, typename BT, typename XT, bool DOTS>
+__global__ void __launch_bounds__(MROWS_BLOCK, DOTS ? 3 : MV_BLOCKS)
+    k_m_post_v(SellView<V> AP, int C, int K, const BT* __restrict__ B, const T* __restrict__ s,
+               const T* __restrict__ R, const int32_t* __restrict__ agg,
+               const T* __restrict__ Xc, XT* __restrict__ Z, const double* __restrict__ Q,
+               double* part, int maxb, unsigned* ticket, MultiRzEpi epi) {
+  constexpr int VW = 16 / sizeof(T);
+  __shared__ int32_t scol_all[MROWS_BLOCK / 32][SL_CAP];
+  __shared__ T sval_all[MROWS_BLOCK / 32][SL_CAP];
+  const int lane = threadIdx.x & 31;
+  const int G = K / VW, RW = 32 / G, cg = lane % G, rs = lane / G, c0 = cg * VW;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* scol = scol_all[threadIdx.x >> 5];
+  T* sval = sval_all[threadIdx.x >> 5];
+  double d[2][VW];
+#pragma unroll
+  for (int k = 0; k < VW; ++k) d[0][k] = d[1][k] = 0.0;
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < AP.nslices;
+       sl += nw) {
+    const int64_t i0 = sl * C;
+    const int rows = (int)(AP.n - i0 < C ? AP.n - i0 : C);
+    int w;
+    const bool staged = stage_slice(AP, sl, C, lane, scol, sval, w);
+    for (int p = 0; p < rows; p += RW) {
+      const bool live = rs < RW && p + rs < rows;
+      const int r = live ? p + rs : 0;
+      const int64_t i = i0 + r;
+      T acc[VW];
+      {
+        BT bv[VW];
+        T rv[VW];
+        ld_cols(B + i * K + c0, bv);
+        ld_cols(R + i * K + c0, rv);
+        cvt_n(bv, acc);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) acc[k] = acc[k] + rv[k];
+      }
+      rows_sub_v<VW>(AP, staged, scol, sval, C, w, r, i, K, c0, Xc, acc);
+      const T si = s[i];
+      T xv[VW];
+      ld_cols(Xc + (int64_t)agg[i] * K + c0, xv);
+#pragma unroll
+      for (int k = 0; k < VW; ++k) xv[k] = fma(si, acc[k], xv[k]);
+      XT zv[VW];
+      cvt_n(xv, zv);
+      if (live) {
+        st_cols(Z + i * K + c0, zv);
+        if constexpr (DOTS) {
+          BT bv[VW];
+          double qv[VW];
+          ld_cols(B + i * K + c0, bv);
+          ld_cols(Q + i * K + c0, qv);
+#pragma unroll
+          for (int k = 0; k < VW; ++k) {
+            d[0][k] += (double)bv[k] * (double)zv[k];
+            d[1][k] += (double)zv[k] * qv[k];
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if constexpr (DOTS) cols_reduce_v<VW, 2>(d, K, part, maxb, ticket, epi);
 }
 
 // Coarsest level for K columns: Y = L^-1 B, then X = L^-T Y, one thread per
@@ -501,17 +809,26 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     for (int q = 0; q < KPL; ++q) acc[q] = 0.0;
     row_mv<KPL, double>(A, i, C, K, lane, acc,
                         [&](int j, int c) { return __ldg(X + (int64_t)j * K + c); });
+    double rv[KPL];
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
       const int c = lane + 32 * q;
+      rv[q] = 0.0;
       if (c < K) {
         const double bi = B[i * K + c];
         const double ri = bi - acc[q];
+        rv[q] = ri;
         R[i * K + c] = ri;
-        if (R32) R32[i * K + c] = (float)ri;
         d[0][q] += ri * ri;
         d[1][q] += bi * bi;
       }
+    }
+    if (R32) {
+      float r32[KPL];
+      cvt_n(rv, r32);
+#pragma unroll
+      for (int q = 0; q < KPL; ++q)
+        if (lane + 32 * q < K) R32[i * K + lane + 32 * q] = r32[q];
     }
   }
   cols_reduce<KPL, 2>(d, K, part, maxb, ticket, epi);
@@ -624,17 +941,26 @@ __global__ void __launch_bounds__(MROWS_BLOCK)
     d[0][q] = 0.0;
   }
   for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    double rv[KPL];
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
       const int c = lane + 32 * q;
+      rv[q] = 0.0;
       if (act[q]) {
         const int64_t e = i * K + c;
         X[e] = X[e] + al[q] * P[e];
         const double ri = R[e] - al[q] * Q[e];
+        rv[q] = ri;
         R[e] = ri;
-        if (R32) R32[e] = (float)ri;
         d[0][q] += ri * ri;
       }
+    }
+    if (R32) {
+      float r32[KPL];
+      cvt_n(rv, r32);
+#pragma unroll
+      for (int q = 0; q < KPL; ++q)
+        if (act[q]) R32[i * K + lane + 32 * q] = r32[q];
     }
   }
   cols_reduce<KPL, 1>(d, K, part, maxb, ticket, epi);
@@ -681,15 +1007,45 @@ static int mgrid_mv(const amg_handle* H, int64_t rows) {
   return grid_for(rows * 32, MROWS_BLOCK, H->num_sms, MV_BLOCKS);
 }
 
-// R32: the FP32 copy of R0 (FP32 hierarchies inside PCG), read by the
-// level-0 pre-smoother instead of converting each gathered FP64 element.
+// Smoother launches: the vector-column kernels when vec (VW divides K, all
+// vectors 16-byte aligned), else the per-column ones.
+template <typename V, typename T>
+static void m_pre(const amg_handle* H, bool vec, int K, const Level& L, const SellView<V>& v,
+                  const T* b, T* r, cudaStream_t s) {
+  const int g = mgrid_mv(H, L.n);
+  if (vec)
+    k_m_pre_v<V, T><<<g, MROWS_BLOCK, 0, s>>>(v, L.A.C, K, b, r);
+  else
+    AMG_DISPATCH_KPL(K, (k_m_pre<KPL, V, T, T><<<g, MROWS_BLOCK, 0, s>>>(v, L.A.C, K, b, r)));
+}
+
+template <bool DOTS, typename V, typename T, typename BT, typename XT>
+static void m_post(const amg_handle* H, const MultiWs& W, bool vec, int K, const Level& L,
+                   const SellView<V>& v, const BT* b, const T* xc, XT* z, const double* Q,
+                   MultiRzEpi epi, cudaStream_t s) {
+  const T* sv = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
+  const T* rv = (const T*)W.lr[&L - H->L.data()];
+  const int maxb = H->red.max_blocks;
+  if (vec) {
+    const int g = grid_for(L.n * 32, MROWS_BLOCK, H->num_sms, DOTS ? 3 : MV_BLOCKS);
+    k_m_post_v<V, T, BT, XT, DOTS><<<g, MROWS_BLOCK, 0, s>>>(
+        v, L.AP.C, K, b, sv, rv, L.agg, xc, z, Q, W.part, maxb, W.ticket, epi);
+  } else {
+    const int g = mgrid_mv(H, L.n);
+    AMG_DISPATCH_KPL(K, (k_m_post<KPL, V, T, BT, XT, DOTS><<<g, MROWS_BLOCK, 0, s>>>(
+                            v, L.AP.C, K, b, sv, rv, L.agg, xc, z, Q, W.part, maxb, W.ticket,
+                            epi)));
+  }
+}
+
+// R32: the FP32 copy of R0 (FP32 hierarchies), read by the level-0
+// pre-smoother: each element is converted once, not once per gather.
 template <typename T>
 static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, double* Z0,
                     bool dots, const double* Q, int beta_form, bool first, cudaStream_t s,
                     const float* R32) {
   const int K = W.K;
   const int nl = (int)H->L.size();
-  const int maxb = H->red.max_blocks;
   MultiRzEpi epi{W.sc, beta_form, first ? 1 : 0};
   auto coarse = [&](const auto* b, auto* x) -> int {
     const int64_t n = H->nco;
@@ -701,33 +1057,21 @@ static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, dou
     return AMG_OK;
   };
   if (nl == 1) return AMG_ERR_UNSUPPORTED;  // single-level hierarchies: use pcg_solve
+  if (sizeof(T) == 4 && !R32) return AMG_ERR_ARG;
+  // the workspace is 256-byte aligned; R0, Z0 (and R32, Q) are checked
+  const bool vec = K % (16 / (int)sizeof(T)) == 0 &&
+                   (((uintptr_t)R0 | (uintptr_t)Z0 | (uintptr_t)R32 | (uintptr_t)Q) & 15u) == 0;
   for (int l = 0; l < nl - 1; ++l) {
     const Level& L = H->L[l];
     T* r = (T*)W.lr[l];
-    const int g = mgrid_mv(H, L.n);
     if constexpr (sizeof(T) == 8) {
-      const double* b = l == 0 ? R0 : (const double*)W.lb[l];
-      const SellView<double> v = view<double>(L.A, L.ah64);
-      AMG_DISPATCH_KPL(K, (k_m_pre<KPL, double, double, double><<<g, MROWS_BLOCK, 0, s>>>(
-                              v, L.A.C, K, b, r)));
+      m_pre(H, vec, K, L, view<double>(L.A, L.ah64), l == 0 ? R0 : (const double*)W.lb[l], r, s);
     } else {
-      if (L.vstore == VAL_BF16) {
-        const SellView<__nv_bfloat16> v = view<__nv_bfloat16>(L.A, L.ah16);
-        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, __nv_bfloat16, float, float><<<g, MROWS_BLOCK, 0, s>>>(
-                                v, L.A.C, K, (const float*)W.lb[l], r)));
-      } else if (l == 0 && R32) {
-        const SellView<float> v = view<float>(L.A, L.ah32);
-        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, float, float, float><<<g, MROWS_BLOCK, 0, s>>>(
-                                v, L.A.C, K, R32, r)));
-      } else if (l == 0) {
-        const SellView<float> v = view<float>(L.A, L.ah32);
-        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, float, float, double><<<g, MROWS_BLOCK, 0, s>>>(
-                                v, L.A.C, K, R0, r)));
-      } else {
-        const SellView<float> v = view<float>(L.A, L.ah32);
-        AMG_DISPATCH_KPL(K, (k_m_pre<KPL, float, float, float><<<g, MROWS_BLOCK, 0, s>>>(
-                                v, L.A.C, K, (const float*)W.lb[l], r)));
-      }
+      const float* b = l == 0 ? R32 : (const float*)W.lb[l];
+      if (L.vstore == VAL_BF16)
+        m_pre(H, vec, K, L, view<__nv_bfloat16>(L.A, L.ah16), b, r, s);
+      else
+        m_pre(H, vec, K, L, view<float>(L.A, L.ah32), b, r, s);
     }
     AMG_LAUNCH_CHECK();
     k_m_restrict<T><<<grid_for(L.nc * K, 256, H->num_sms, 8), 256, 0, s>>>(
@@ -737,50 +1081,29 @@ static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, dou
   AMG_TRY(coarse((const T*)W.lb[nl - 1], (T*)W.lx[nl - 1]));
   for (int l = nl - 2; l >= 0; --l) {
     const Level& L = H->L[l];
-    const int g = mgrid_mv(H, L.n);
     const T* xc = (const T*)W.lx[l + 1];
-    const T* sv = (const T*)(sizeof(T) == 8 ? (const void*)L.s64 : (const void*)L.s32);
-    const T* rv = (const T*)W.lr[l];
     if constexpr (sizeof(T) == 8) {
       const SellView<double> v = view<double>(L.AP, L.AP.v64);
-      if (l == 0 && dots) {
-        AMG_DISPATCH_KPL(K, (k_m_post<KPL, double, double, double, double, true>
-                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0, Q,
-                                                        W.part, maxb, W.ticket, epi)));
-      } else if (l == 0) {
-        AMG_DISPATCH_KPL(K, (k_m_post<KPL, double, double, double, double, false>
-                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0, Q,
-                                                        W.part, maxb, W.ticket, epi)));
-      } else {
-        AMG_DISPATCH_KPL(K, (k_m_post<KPL, double, double, double, double, false>
-                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, (const double*)W.lb[l], sv,
-                                                        rv, L.agg, xc, (double*)W.lx[l], Q, W.part,
-                                                        maxb, W.ticket, epi)));
-      }
+      if (l == 0 && dots)
+        m_post<true>(H, W, vec, K, L, v, R0, xc, Z0, Q, epi, s);
+      else if (l == 0)
+        m_post<false>(H, W, vec, K, L, v, R0, xc, Z0, Q, epi, s);
+      else
+        m_post<false>(H, W, vec, K, L, v, (const double*)W.lb[l], xc, (double*)W.lx[l], Q, epi,
+                      s);
     } else {
       if (l == 0) {
         const SellView<float> v = view<float>(L.AP, L.AP.v32);
-        if (dots) {
-          AMG_DISPATCH_KPL(K, (k_m_post<KPL, float, float, double, double, true>
-                               <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0,
-                                                          Q, W.part, maxb, W.ticket, epi)));
-        } else {
-          AMG_DISPATCH_KPL(K, (k_m_post<KPL, float, float, double, double, false>
-                               <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, R0, sv, rv, L.agg, xc, Z0,
-                                                          Q, W.part, maxb, W.ticket, epi)));
-        }
+        if (dots)
+          m_post<true>(H, W, vec, K, L, v, R0, xc, Z0, Q, epi, s);
+        else
+          m_post<false>(H, W, vec, K, L, v, R0, xc, Z0, Q, epi, s);
       } else if (L.vstore == VAL_BF16) {
-        const SellView<__nv_bfloat16> v = view<__nv_bfloat16>(L.AP, L.AP.v16);
-        AMG_DISPATCH_KPL(K, (k_m_post<KPL, __nv_bfloat16, float, float, float, false>
-                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, (const float*)W.lb[l], sv,
-                                                        rv, L.agg, xc, (float*)W.lx[l], Q, W.part,
-                                                        maxb, W.ticket, epi)));
+        m_post<false>(H, W, vec, K, L, view<__nv_bfloat16>(L.AP, L.AP.v16),
+                      (const float*)W.lb[l], xc, (float*)W.lx[l], Q, epi, s);
       } else {
-        const SellView<float> v = view<float>(L.AP, L.AP.v32);
-        AMG_DISPATCH_KPL(K, (k_m_post<KPL, float, float, float, float, false>
-                             <<<g, MROWS_BLOCK, 0, s>>>(v, L.AP.C, K, (const float*)W.lb[l], sv,
-                                                        rv, L.agg, xc, (float*)W.lx[l], Q, W.part,
-                                                        maxb, W.ticket, epi)));
+        m_post<false>(H, W, vec, K, L, view<float>(L.AP, L.AP.v32), (const float*)W.lb[l], xc,
+                      (float*)W.lx[l], Q, epi, s);
       }
     }
     AMG_LAUNCH_CHECK();
@@ -868,7 +1191,13 @@ void multi_free(amg_handle* H) {
 int vcycle_multi(amg_handle* H, int K, const double* R, double* Z, cudaStream_t s) {
   MultiWs* W = nullptr;
   AMG_TRY(multi_ws(H, K, &W));
-  return m_vcycle_any(H, *W, R, Z, false, nullptr, PCG_BETA_FR, true, s);
+  if (W->R32) {  // FP32 V-cycle: R rounded to FP32 once
+    const int64_t m = H->L[0].n * K;
+    const bool vec = (((uintptr_t)R | (uintptr_t)W->R32) & 15u) == 0;
+    k_m_to_f32<<<grid_for((m + 3) / 4, 256, H->num_sms, 8), 256, 0, s>>>(m, R, W->R32, vec);
+    AMG_LAUNCH_CHECK();
+  }
+  return m_vcycle_any(H, *W, R, Z, false, nullptr, PCG_BETA_FR, true, s, W->R32);
 }
 
 int pcg_multi_run(amg_handle* H, int K, const double* B, double* X, const pcg_options* o,

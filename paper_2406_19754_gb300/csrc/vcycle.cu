@@ -308,6 +308,38 @@ static __global__ void k_vec_to_f32(int64_t n, const double* __restrict__ v,
     w[i] = (float)v[i];
 }
 
+// Groups of four elements, as the blocked kernels convert them: an input out
+// of the bit path's range sends its whole group to the hardware conversion.
+static __global__ void k_debug_convert(int64_t n, const double* __restrict__ in64,
+                                       float* __restrict__ out32, const float* __restrict__ in32,
+                                       double* __restrict__ out64) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; 4 * t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 4 * t;
+    const int m = (int)(n - i < 4 ? n - i : 4);
+    if (in64) {
+      double a[4];
+      float b[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[k] = k < m ? in64[i + k] : 0.0;
+      cvt_n(a, b);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < m) out32[i + k] = b[k];
+    }
+    if (in32) {
+      float a[4];
+      double b[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a[k] = k < m ? in32[i + k] : 0.0f;
+      cvt_n(a, b);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < m) out64[i + k] = b[k];
+    }
+  }
+}
+
 // Dots for the single-level case (the whole preconditioner is the coarse solve).
 template <int NDOT>
 __global__ void k_dots_rz(int64_t n, const double* r, const double* z, const double* q, Reduce red,
@@ -958,6 +990,15 @@ int vcycle_profile(const amg_handle* H, const double* r, double* z, amg_kernel_t
   const int m = (int)prof.rec.size();
   if (count) *count = m;
   for (int k = 0; k < m && k < max_out; ++k) out[k] = prof.rec[k];
+  return AMG_OK;
+}
+
+int debug_convert(const double* in64, float* out32, const float* in32, double* out64,
+                  int64_t n, cudaStream_t s) {
+  if (n == 0) return AMG_OK;
+  const int g = (int)std::min<int64_t>((n + 1023) / 1024, 4096);
+  k_debug_convert<<<g, 256, 0, s>>>(n, in64, out32, in32, out64);
+  AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
 

@@ -2,7 +2,12 @@
 
 The blocked V-cycle must reproduce every column's single V-cycle bit for bit
 (same per-column operation order).  Blocked PCG: per column, the iteration
-count +-1 and the solution to 1e-10 relative against the oracle's PCG."""
+count +-1 and the solution to 1e-10 relative against the oracle's PCG.
+
+Column counts cover both kernel forms: 16-byte column vectors when 4 (FP32)
+or 2 (FP64) divides K -- K = 2, 4, 8, 12, 32, 48, 64, including lane layouts
+that leave lanes idle (12, 48) -- and per-column lanes otherwise (1, 5, 33)
+or when a vector is not 16-byte aligned."""
 
 import numpy as np
 import pytest
@@ -14,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
-@pytest.mark.parametrize("K", [1, 5, 32, 33, 64])
+@pytest.mark.parametrize("K", [1, 2, 4, 5, 8, 12, 32, 33, 48, 64])
 def test_vcycle_multi_equals_single_columns(amg, precision, K):
     A = poisson3d(19, 13, 11)  # ragged slices
     n = 19 * 13 * 11
@@ -24,6 +29,23 @@ def test_vcycle_multi_equals_single_columns(amg, precision, K):
     for c in range(K):
         zc = H.vcycle(R[:, c].contiguous())
         assert torch.equal(Z[:, c], zc), c
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_vcycle_multi_unaligned_vectors(amg, precision):
+    # R and Z 8 bytes past a 16-byte boundary: the per-column kernels run,
+    # with the same bits as the vector kernels on aligned copies
+    A = poisson3d(19, 13, 11)
+    n, K = 19 * 13 * 11, 8
+    H = amg.Hierarchy(*amg.csr_to_device(A), precision=precision, max_coarse=60)
+    buf = torch.as_tensor(uniform01(9, n * K + 1), device="cuda")
+    R = buf[1:].view(n, K)
+    zbuf = torch.zeros(n * K + 1, dtype=torch.float64, device="cuda")
+    Z = zbuf[1:].view(n, K)
+    assert R.data_ptr() % 16 == 8 and Z.data_ptr() % 16 == 8
+    H.vcycle_multi(R, Z)
+    assert torch.equal(Z, H.vcycle_multi(R.clone()))
+    assert torch.equal(Z[:, 5], H.vcycle(R[:, 5].contiguous()))
 
 
 def test_vcycle_multi_bf16_levels(amg):
