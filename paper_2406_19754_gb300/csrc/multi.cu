@@ -558,8 +558,9 @@ __device__ __forceinline__ void st_cols(double* __restrict__ p, const double (&o
 }
 
 // acc -= sum_k a_ik X[col_k, c0 ..] for the lane's row (staged slice, or the
-// row's entries from global memory when the slice did not fit the staging).
-template <int VW, typename V, typename T>
+// row's entries from global memory when the slice did not fit the staging);
+// acc += ... with NEG false.
+template <int VW, bool NEG = true, typename V, typename T>
 __device__ __forceinline__ void rows_sub_v(const SellView<V>& A, bool staged, const int32_t* scol,
                                            const T* sval, int C, int w, int r, int64_t i, int K,
                                            int c0, const T* __restrict__ X, T (&acc)[VW]) {
@@ -577,7 +578,7 @@ __device__ __forceinline__ void rows_sub_v(const SellView<V>& A, bool staged, co
 #pragma unroll
     for (int u = 0; u < SL_MAXW; ++u)
       if (u < w) {
-        const T a = -sval[u * C + r];
+        const T a = NEG ? -sval[u * C + r] : sval[u * C + r];
 #pragma unroll
         for (int k = 0; k < VW; ++k) acc[k] = fma(a, g[u][k], acc[k]);
       }
@@ -611,7 +612,7 @@ __device__ __forceinline__ void rows_sub_v(const SellView<V>& A, bool staged, co
     for (int u = 0; u < MV_U; ++u)
       if (k0 + u < rw.w)
 #pragma unroll
-        for (int k = 0; k < VW; ++k) acc[k] = fma(-aa[u], g[u][k], acc[k]);
+        for (int k = 0; k < VW; ++k) acc[k] = fma(NEG ? -aa[u] : aa[u], g[u][k], acc[k]);
   }
 }
 
@@ -894,6 +895,46 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
     __syncwarp();
   }
   cols_reduce<KPL, 1>(d, K, part, maxb, ticket, epi);
+}
+
+// Q = A P and (p, q) per column, vector columns (two doubles a lane); see
+// k_m_pre_v for the lane layout.
+__global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
+    k_m_spmm_dot_v(SellView<double> A, int C, int K, const double* __restrict__ P,
+                   double* __restrict__ Q, double* part, int maxb, unsigned* ticket,
+                   MultiPqEpi epi) {
+  constexpr int VW = 2;
+  __shared__ int32_t scol_all[MROWS_BLOCK / 32][SL_CAP];
+  __shared__ double sval_all[MROWS_BLOCK / 32][SL_CAP];
+  const int lane = threadIdx.x & 31;
+  const int G = K / VW, RW = 32 / G, cg = lane % G, rs = lane / G, c0 = cg * VW;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t* scol = scol_all[threadIdx.x >> 5];
+  double* sval = sval_all[threadIdx.x >> 5];
+  double d[1][VW] = {{0.0, 0.0}};
+  for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < A.nslices;
+       sl += nw) {
+    const int64_t i0 = sl * C;
+    const int rows = (int)(A.n - i0 < C ? A.n - i0 : C);
+    int w;
+    const bool staged = stage_slice(A, sl, C, lane, scol, sval, w);
+    for (int p = 0; p < rows; p += RW) {
+      const bool live = rs < RW && p + rs < rows;
+      const int r = live ? p + rs : 0;
+      const int64_t i = i0 + r;
+      double acc[VW] = {0.0, 0.0};
+      rows_sub_v<VW, false>(A, staged, scol, sval, C, w, r, i, K, c0, P, acc);
+      if (live) {
+        st_cols(Q + i * K + c0, acc);
+        double pv[VW];
+        ld_cols(P + i * K + c0, pv);
+#pragma unroll
+        for (int k = 0; k < VW; ++k) d[0][k] += pv[k] * acc[k];
+      }
+    }
+    __syncwarp();
+  }
+  cols_reduce_v<VW, 1>(d, K, part, maxb, ticket, epi);
 }
 
 struct MultiRrEpi {
@@ -1234,8 +1275,12 @@ int pcg_multi_run(amg_handle* H, int K, const double* B, double* X, const pcg_op
     AMG_TRY(m_vcycle_any(H, *W, W->R, W->Z, true, W->Q, beta_form, true, s, W->R32));
     AMG_CUDA_TRY(cudaMemcpyAsync(W->P, W->Z, sizeof(double) * n * K, cudaMemcpyDeviceToDevice, s));
     for (;;) {
-      AMG_DISPATCH_KPL(K, (k_m_spmm_dot<KPL><<<gmv, MROWS_BLOCK, 0, s>>>(
-                              A, C, K, W->P, W->Q, W->part, maxb, W->ticket, pe)));
+      if (K % 2 == 0)  // two doubles a lane (the workspace is 16-byte aligned)
+        k_m_spmm_dot_v<<<gmv, MROWS_BLOCK, 0, s>>>(A, C, K, W->P, W->Q, W->part, maxb,
+                                                  W->ticket, pe);
+      else
+        AMG_DISPATCH_KPL(K, (k_m_spmm_dot<KPL><<<gmv, MROWS_BLOCK, 0, s>>>(
+                                A, C, K, W->P, W->Q, W->part, maxb, W->ticket, pe)));
       AMG_LAUNCH_CHECK();
       AMG_CUDA_TRY(cudaMemsetAsync(W->nactive, 0, sizeof(int), s));
       AMG_DISPATCH_KPL(K, (k_m_update<KPL><<<g, MROWS_BLOCK, 0, s>>>(n, K, X, W->R, W->P, W->Q,

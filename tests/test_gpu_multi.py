@@ -57,9 +57,10 @@ def test_vcycle_multi_bf16_levels(amg):
         assert torch.equal(Z[:, c], H.vcycle(R[:, c].contiguous()))
 
 
-def test_pcg_multi_matches_oracle_per_column(amg, orc):
+@pytest.mark.parametrize("K", [12, 7])  # vector-column and per-column kernels
+def test_pcg_multi_matches_oracle_per_column(amg, orc, K):
     A = poisson3d(20)
-    n, K = 8000, 12
+    n = 8000
     H = amg.Hierarchy(*amg.csr_to_device(A))
     Bh = uniform01(100, n * K).reshape(n, K)
     Bh[:, 3] = 0.0  # converged before the first step
