@@ -714,6 +714,52 @@ __global__ void __launch_bounds__(MROWS_BLOCK, DOTS ? 3 : MV_BLOCKS)
   if constexpr (DOTS) cols_reduce_v<VW, 2>(d, K, part, maxb, ticket, epi);
 }
 
+// Restriction with vector columns: thread t sums column group t % G (VW
+// columns, G = K / VW) of aggregate t / G.  The member indices come first,
+// then all their rows' loads, then the additions in member order (as
+// k_m_restrict adds them; the list ends at the first negative index).
+constexpr int RS_U = 8;
+template <typename T>
+__global__ void k_m_restrict_v(int64_t nc, int stride, int K,
+                               const int32_t* __restrict__ members, const T* __restrict__ R,
+                               T* __restrict__ Bc) {
+  constexpr int VW = 16 / sizeof(T);
+  const int G = K / VW;
+  const int64_t total = nc * G;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t I = t / G;
+    const int c0 = (int)(t % G) * VW;
+    const int32_t* m = members + I * stride;
+    T acc[VW];
+    ld_cols(R + (int64_t)__ldg(m) * K + c0, acc);
+    bool live = true;
+    for (int k0 = 1; k0 < stride && live; k0 += RS_U) {
+      int ii[RS_U];
+#pragma unroll
+      for (int u = 0; u < RS_U; ++u) ii[u] = k0 + u < stride ? __ldg(m + k0 + u) : -1;
+      T g[RS_U][VW];
+#pragma unroll
+      for (int u = 0; u < RS_U; ++u) {
+        if (ii[u] >= 0) {
+          ld_cols(R + (int64_t)ii[u] * K + c0, g[u]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < VW; ++k) g[u][k] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RS_U; ++u) {
+        live = live && ii[u] >= 0;
+        if (live)
+#pragma unroll
+          for (int k = 0; k < VW; ++k) acc[k] = acc[k] + g[u][k];
+      }
+    }
+    st_cols(Bc + I * K + c0, acc);
+  }
+}
+
 // Coarsest level for K columns: Y = L^-1 B, then X = L^-T Y, one thread per
 // output element (n <= 3072).  Each dot product is summed exactly as the
 // single-RHS coarse kernel sums it: 32 lane partials over a stride of 32,
@@ -1115,8 +1161,12 @@ static int m_vcycle(const amg_handle* H, const MultiWs& W, const double* R0, dou
         m_pre(H, vec, K, L, view<float>(L.A, L.ah32), b, r, s);
     }
     AMG_LAUNCH_CHECK();
-    k_m_restrict<T><<<grid_for(L.nc * K, 256, H->num_sms, 8), 256, 0, s>>>(
-        L.nc, L.stride, K, L.members, r, (T*)W.lb[l + 1]);
+    if (vec)
+      k_m_restrict_v<T><<<grid_for(L.nc * (K / (16 / (int)sizeof(T))), 256, H->num_sms, 8), 256,
+                          0, s>>>(L.nc, L.stride, K, L.members, r, (T*)W.lb[l + 1]);
+    else
+      k_m_restrict<T><<<grid_for(L.nc * K, 256, H->num_sms, 8), 256, 0, s>>>(
+          L.nc, L.stride, K, L.members, r, (T*)W.lb[l + 1]);
     AMG_LAUNCH_CHECK();
   }
   AMG_TRY(coarse((const T*)W.lb[nl - 1], (T*)W.lx[nl - 1]));
