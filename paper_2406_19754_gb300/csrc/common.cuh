@@ -376,23 +376,55 @@ __device__ __forceinline__ double f32_to_f64_bits(float f, bool& ok) {
                           (int)(in ? u << 29 : 0u));
 }
 
+// The hardware conversions of a whole array, out of line: inlined, the
+// compiler predicates them into the caller, and predicated-off FP64-pipe
+// instructions still take the pipe's cycles.
+template <typename A, typename B, int N>
+struct CvtArr {
+  B v[N];
+};
+template <int N>
+__device__ __noinline__ CvtArr<double, float, N> cvt_hw(CvtArr<double, double, N> a) {
+  CvtArr<double, float, N> r;
+#pragma unroll
+  for (int q = 0; q < N; ++q) r.v[q] = __double2float_rn(a.v[q]);
+  return r;
+}
+template <int N>
+__device__ __noinline__ CvtArr<float, double, N> cvt_hw(CvtArr<float, float, N> a) {
+  CvtArr<float, double, N> r;
+#pragma unroll
+  for (int q = 0; q < N; ++q) r.v[q] = (double)a.v[q];
+  return r;
+}
+
 template <int N>
 __device__ __forceinline__ void cvt_n(const double (&in)[N], float (&out)[N]) {
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < N; ++q) out[q] = f64_to_f32_bits(in[q], ok);
-  if (!ok)
+  if (!ok) {
+    CvtArr<double, double, N> a;
 #pragma unroll
-    for (int q = 0; q < N; ++q) out[q] = __double2float_rn(in[q]);
+    for (int q = 0; q < N; ++q) a.v[q] = in[q];
+    const CvtArr<double, float, N> r = cvt_hw<N>(a);
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = r.v[q];
+  }
 }
 template <int N>
 __device__ __forceinline__ void cvt_n(const float (&in)[N], double (&out)[N]) {
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < N; ++q) out[q] = f32_to_f64_bits(in[q], ok);
-  if (!ok)
+  if (!ok) {
+    CvtArr<float, float, N> a;
 #pragma unroll
-    for (int q = 0; q < N; ++q) out[q] = (double)in[q];
+    for (int q = 0; q < N; ++q) a.v[q] = in[q];
+    const CvtArr<float, double, N> r = cvt_hw<N>(a);
+#pragma unroll
+    for (int q = 0; q < N; ++q) out[q] = r.v[q];
+  }
 }
 template <int N, typename T>
 __device__ __forceinline__ void cvt_n(const T (&in)[N], T (&out)[N]) {

@@ -63,6 +63,8 @@ constexpr int MV_U = 4;
 // Row kernels (row_mv) are resident MV_BLOCKS blocks per SM (64 registers a
 // thread); their grids are sized to one full wave of that.
 constexpr int MV_BLOCKS = 4;
+// the post-smoother with column dot products (two FP64 sums per column)
+constexpr int MV_BLOCKS_DOTS = 3;
 
 // The row helpers below add to acc as the caller set it (0, or the start value
 // of a folded subtraction); NEG subtracts each entry's product instead (an
@@ -650,7 +652,7 @@ __global__ void __launch_bounds__(MROWS_BLOCK, MV_BLOCKS)
 // Z = s (B + R - AP Xc) + Xc[agg] (as k_m_post), vector columns; with DOTS
 // the column sums (B, Z) and (Z, Q) go to epi.
 template <typename V, typename T, typename BT, typename XT, bool DOTS>
-__global__ void __launch_bounds__(MROWS_BLOCK, DOTS ? 3 : MV_BLOCKS)
+__global__ void __launch_bounds__(MROWS_BLOCK, DOTS ? MV_BLOCKS_DOTS : MV_BLOCKS)
     k_m_post_v(SellView<V> AP, int C, int K, const BT* __restrict__ B, const T* __restrict__ s,
                const T* __restrict__ R, const int32_t* __restrict__ agg,
                const T* __restrict__ Xc, XT* __restrict__ Z, const double* __restrict__ Q,
@@ -1114,7 +1116,7 @@ static void m_post(const amg_handle* H, const MultiWs& W, bool vec, int K, const
   const T* rv = (const T*)W.lr[&L - H->L.data()];
   const int maxb = H->red.max_blocks;
   if (vec) {
-    const int g = grid_for(L.n * 32, MROWS_BLOCK, H->num_sms, DOTS ? 3 : MV_BLOCKS);
+    const int g = grid_for(L.n * 32, MROWS_BLOCK, H->num_sms, DOTS ? MV_BLOCKS_DOTS : MV_BLOCKS);
     k_m_post_v<V, T, BT, XT, DOTS><<<g, MROWS_BLOCK, 0, s>>>(
         v, L.AP.C, K, b, sv, rv, L.agg, xc, z, Q, W.part, maxb, W.ticket, epi);
   } else {
