@@ -17,12 +17,28 @@ import numpy as np
 from . import build as _build
 
 _lib = None
+_openmp = False
+
+
+def use_openmp(on: bool = True) -> None:
+    """Load the OpenMP build (the same sources; its parallel row loops give
+    the same bits) instead of the single-thread one.  Call before the first
+    oracle call of the process; OMP_NUM_THREADS sets the thread count."""
+    global _openmp
+    if _lib is not None and on != _openmp:
+        raise RuntimeError("the oracle library is already loaded")
+    _openmp = on
+
+
+def threads() -> int:
+    """Threads the loaded oracle's parallel row loops use (1: plain build)."""
+    return int(lib().orc_threads())
 
 
 def lib():
     global _lib
     if _lib is None:
-        _lib = C.CDLL(_build.build())
+        _lib = C.CDLL(_build.build(openmp=_openmp))
         _declare(_lib)
     return _lib
 
@@ -32,6 +48,7 @@ _I64 = C.c_int64
 
 
 def _declare(L):
+    L.orc_threads.restype = C.c_int
     L.orc_dot.restype = C.c_double
     L.orc_dot.argtypes = [_I64, _P, _P]
     L.orc_spmv.argtypes = [_I64, _P, _P, _P, _P, _P]

@@ -79,6 +79,14 @@
 //    iteration cap; the tolerance is a parameter), and on p^T A p <= 0.
 //  * Dot products: partial sums over fixed blocks of 4096 entries, then the
 //    partials in order.
+//
+// Threads.  Built plainly this is a single-thread program.  Built with
+// -fopenmp (liboracle_omp.so, for timing the CPU baseline on all host cores)
+// the loops marked ROWS_PARALLEL run their iterations on several threads.
+// Each such loop writes only its own row's (or aggregate's, or dot-product
+// block's) output and reads nothing another iteration writes, and every sum
+// keeps its order, so both builds give the same bits.  The setup phase stays
+// serial.
 
 #include <algorithm>
 #include <cmath>
@@ -86,6 +94,13 @@
 #include <cstring>
 #include <functional>
 #include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#define ROWS_PARALLEL _Pragma("omp parallel for schedule(static)")
+#else
+#define ROWS_PARALLEL
+#endif
 
 namespace {
 
@@ -131,17 +146,22 @@ struct Hierarchy {
 
 double dot_blocked(int64_t n, const double* x, const double* y) {
   const int64_t B = 4096;
-  double total = 0.0;
-  for (int64_t b0 = 0; b0 < n; b0 += B) {
-    int64_t b1 = std::min(n, b0 + B);
-    double part = 0.0;
-    for (int64_t i = b0; i < b1; ++i) part += x[i] * y[i];
-    total += part;
+  const int64_t nb = (n + B - 1) / B;
+  std::vector<double> part(nb);
+  ROWS_PARALLEL
+  for (int64_t k = 0; k < nb; ++k) {
+    const int64_t b0 = k * B, b1 = std::min(n, b0 + B);
+    double s = 0.0;
+    for (int64_t i = b0; i < b1; ++i) s += x[i] * y[i];
+    part[k] = s;
   }
+  double total = 0.0;
+  for (int64_t k = 0; k < nb; ++k) total += part[k];
   return total;
 }
 
 void spmv(const Csr& A, const double* x, double* y) {
+  ROWS_PARALLEL
   for (int64_t i = 0; i < A.n; ++i) {
     double s = 0.0;
     for (int64_t e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) s += A.val[e] * x[A.col[e]];
@@ -714,6 +734,7 @@ int64_t sweeps_at(const Hierarchy& H, int l) {
 void jacobi_sweep(const Level& L, const double* b, double* x, double* r) {
   const int64_t n = L.A.n;
   spmv(L.A, x, r);
+  ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) x[i] = x[i] + L.dinv[i] * (b[i] - r[i]);
 }
 
@@ -731,14 +752,17 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
   }
   const int64_t nu = sweeps_at(H, l);
   std::vector<double> r(n), bc(L.nc), xc(L.nc);
+  ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) x[i] = L.dinv[i] * b[i];  // pre-smooth, zero guess
   for (int64_t k = 1; k < nu; ++k) jacobi_sweep(L, b, x, r.data());
   spmv(L.A, x, r.data());
+  ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];  // residual
   const int stride = L.stride;
   if (H.smooth_p) {
     spmv(L.Pt, r.data(), bc.data());  // restriction b_c = P^T r
   } else {
+    ROWS_PARALLEL
     for (int64_t I = 0; I < L.nc; ++I) {  // restriction b_c = P^T r
       double s = 0.0;
       for (int k = 0; k < stride; ++k) {
@@ -752,8 +776,10 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
   vcycle(H, l + 1, bc.data(), xc.data());
   if (H.smooth_p) {  // prolongation x += P x_c
     spmv(L.P, xc.data(), r.data());
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] + r[i];
   } else {
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) x[i] = x[i] + xc[L.agg[i]];
   }
   for (int64_t k = 0; k < nu; ++k) jacobi_sweep(L, b, x, r.data());  // post-smooth
@@ -774,6 +800,7 @@ PcgOut pcg(const Csr& A, const std::function<void(const double*, double*)>& prec
   PcgOut o;
   std::vector<double> r(n), z(n), p(n), q(n), rold;
   spmv(A, x, q.data());
+  ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
   double bnorm = std::sqrt(dot_blocked(n, b, b));
   if (bnorm == 0.0) bnorm = 1.0;
@@ -796,6 +823,7 @@ PcgOut pcg(const Csr& A, const std::function<void(const double*, double*)>& prec
     }
     double alpha = rz / pq;
     if (beta_form == 1) rold = r;
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) {
       x[i] = x[i] + alpha * p[i];
       r[i] = r[i] - alpha * q[i];
@@ -823,11 +851,13 @@ PcgOut pcg(const Csr& A, const std::function<void(const double*, double*)>& prec
     } else {
       beta = rz_new / rz;
     }
+    ROWS_PARALLEL
     for (int64_t i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     rz = rz_new;
   }
   o.iters = k;
   spmv(A, x, q.data());
+  ROWS_PARALLEL
   for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
   o.true_relres = std::sqrt(dot_blocked(n, q.data(), q.data())) / bnorm;
   return o;
@@ -839,6 +869,15 @@ PcgOut pcg(const Csr& A, const std::function<void(const double*, double*)>& prec
 extern "C" {
 
 double orc_dot(int64_t n, const double* x, const double* y) { return dot_blocked(n, x, y); }
+
+// Threads the parallel row loops use (1 in the plain build).
+int orc_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 void orc_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x,
               double* y) {

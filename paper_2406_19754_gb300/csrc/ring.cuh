@@ -163,6 +163,7 @@ struct RingWarp {
   int lane;
   uint64_t pol;
   bool ok = true;
+  int64_t nbeg = 0, nend = 0;  // lane 0: bounds of the slice release() copies next
 
   __device__ __forceinline__ RingWarp(const SellView<V>& A_, const RingGeom& g_,
                                       const RingRows& rows_, unsigned char* smem_raw)
@@ -188,10 +189,9 @@ struct RingWarp {
   // come with it; the last slice's are read from global memory.
   __device__ __forceinline__ bool full(int64_t sl) const { return (sl + 1) * 32 <= A.n; }
 
-  // lane 0: copy slice sl (and its per-row vectors) into stage d
-  __device__ __forceinline__ void issue(int64_t sl, int d) {
-    const int64_t beg = __ldg(A.sliceptr + sl);
-    const int w = (int)((__ldg(A.sliceptr + sl + 1) - beg) >> 5);
+  // lane 0: copy slice sl = [beg, end) (and its per-row vectors) into stage d
+  __device__ __forceinline__ void issue(int64_t sl, int d, int64_t beg, int64_t end) {
+    const int w = (int)((end - beg) >> 5);
     widths[d] = w;
     const uint32_t vb = (uint32_t)w * 32u * (uint32_t)sizeof(V), cb = (uint32_t)w * 128u;
     const bool f = full(sl);
@@ -219,13 +219,21 @@ struct RingWarp {
       mbar_init_fence();
       for (int d = 0; d < g.D; ++d) {
         const int64_t sl = first + (int64_t)d * nwt;
-        if (sl < A.nslices) issue(sl, d);
+        if (sl < A.nslices) issue(sl, d, __ldg(A.sliceptr + sl), __ldg(A.sliceptr + sl + 1));
       }
     }
     __syncwarp();
   }
 
+  // Waits for the current slice.  Lane 0 first loads the bounds of the slice
+  // that release() will copy next, so that load's latency passes during the
+  // wait and the slice's arithmetic instead of delaying the copy.
   __device__ __forceinline__ bool wait() {
+    const int64_t nxt = cur + (int64_t)g.D * nwt;
+    if (lane == 0 && nxt < A.nslices) {
+      nbeg = __ldg(A.sliceptr + nxt);
+      nend = __ldg(A.sliceptr + nxt + 1);
+    }
     ok = mbar_wait_bounded(bar(stage), phase);
     return __all_sync(0xffffffffu, ok);
   }
@@ -248,7 +256,7 @@ struct RingWarp {
   __device__ __forceinline__ void release() {
     __syncwarp();
     const int64_t nxt = cur + (int64_t)g.D * nwt;
-    if (lane == 0 && nxt < A.nslices) issue(nxt, stage);
+    if (lane == 0 && nxt < A.nslices) issue(nxt, stage, nbeg, nend);
     cur += nwt;
     if (++stage == g.D) {
       stage = 0;
