@@ -354,7 +354,7 @@ int mlp_features(const amg_csr* A, int64_t nx, int64_t ny, int64_t nz, float* fe
 
 /*
  * omega[i] = network(feat[i]) for n rows (device float arrays).  By default
- * the two hidden layers run on the tensor cores (TF32 operands, FP32
+ * the two hidden layers run on the tensor cores (FP16 operands, FP32
  * accumulation; omega within about 1e-3 of the FP32 pass); after
  * mlp_set_exact_forward(M, 1), in FP32 on the CUDA cores.  Asynchronous.
  */

@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace amg {
@@ -208,25 +210,31 @@ __global__ void __launch_bounds__(FW_WARPS * 32)
 }
 
 // Forward pass on the tensor cores: the 9 -> 32 and 32 -> 32 layers of a tile
-// of 16 rows are warp-level matrix products (mma.sync m16n8k8, TF32 operands
-// rounded to nearest, FP32 accumulation); GELU, the 32 -> 1 layer and the
-// sigmoid run in FP32 on the accumulators.  Fragment layouts of m16n8k8
-// (g = lane / 4, t = lane % 4): A (16 x 8, row major) a0 = (g, t), a1 =
-// (g + 8, t), a2 = (g, t + 4), a3 = (g + 8, t + 4); B (8 x 8, k x n) b0 =
-// (t, g), b1 = (t + 4, g); C (16 x 8) c0 = (g, 2t), c1 = (g, 2t + 1), c2 =
-// (g + 8, 2t), c3 = (g + 8, 2t + 1).  The weights stay in registers as B
-// fragments for the whole launch; a tile's features and first-layer
-// activations go through shared memory to become A fragments.
-// GELU uses erf_as7126.  omega agrees with the FP32 pass to about 1e-3 (TF32
-// keeps 10 mantissa bits).
+// of 16 rows are warp-level matrix products (mma.sync m16n8k16 with FP16
+// operands rounded to nearest, FP32 accumulation); GELU, the 32 -> 1 layer
+// and the sigmoid run in FP32 on the accumulators.  FP16 keeps 10 explicit
+// mantissa bits, as TF32 does, at half the register cost per operand.
+// Fragment layouts of m16n8k16 (g = lane / 4, t = lane % 4; a register holds
+// two FP16 values, the lower column in its low half):
+//   A (16 x 16, row major): a0 = (g, 2t..2t+1), a1 = (g+8, 2t..2t+1),
+//                           a2 = (g, 2t+8..2t+9), a3 = (g+8, 2t+8..2t+9);
+//   B (16 x 8, k x n):      b0 = (2t..2t+1, g), b1 = (2t+8..2t+9, g);
+//   C (16 x 8, FP32):       c0 = (g, 2t), c1 = (g, 2t+1), c2 = (g+8, 2t),
+//                           c3 = (g+8, 2t+1).
+// The C fragments of the first layer's column tiles 2s and 2s+1 hold, for
+// rows g and g+8, exactly the hidden units 16s + {2t, 2t+1, 2t+8, 2t+9} that
+// the A fragment of the second layer's k-step s needs, so the activations
+// pass from one product to the next in registers.  The features come
+// straight from global memory into the first A fragment (columns 9..15 are
+// zero); the weights stay in registers as B fragments for the whole launch.
+// GELU uses erf_as7126.  omega agrees with the FP32 pass to about 1e-3.
 constexpr int TC_WARPS = 4;
-constexpr int TC_LD = 36;  // padded row of the activation tile (conflict-free A loads)
 
 // erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula
 // 7.1.26: for x >= 0, erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5)
 // e^(-x^2) with t = 1 / (1 + p x), |error| <= 1.5e-7; odd in x.  About a
 // dozen instructions (a fast reciprocal and exponential, five FMAs), against
-// the exact erff's longer sequence; the tensor-core forward pass, whose TF32
+// the exact erff's longer sequence; the tensor-core forward pass, whose FP16
 // operands already limit omega to about 1e-3, uses it in its GELUs.
 __device__ __forceinline__ float erf_as7126(float x) {
   const float ax = fabsf(x);
@@ -243,48 +251,43 @@ __device__ __forceinline__ float gelu_fast(float u) {
   return 0.5f * u * (1.0f + erf_as7126(u * 0.70710678f));
 }
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+// two floats rounded to FP16 (nearest even), lo in the low half
+__device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
+  const __half2 h = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void mma_tf32(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+__device__ __forceinline__ void mma_f16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                        uint32_t a3, uint32_t b0, uint32_t b1) {
   asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
       "{%8,%9}, {%0,%1,%2,%3};"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// The tile's features and first-layer activations are stored already
-// rounded to TF32; the next tile's features are loaded into registers while
-// the current one is computed.
+// The next tile's features are loaded into registers while the current one
+// is computed.
 __global__ void __launch_bounds__(TC_WARPS * 32)
     k_mlp_forward_tc(int64_t n, const float* __restrict__ params,
                      const float* __restrict__ feat, float omega_max,
                      float* __restrict__ omega) {
-  __shared__ uint32_t fs[TC_WARPS][16 * 16];     // a tile's features (TF32), 9 of 16 used
-  __shared__ uint32_t hs[TC_WARPS][16 * TC_LD];  // first-layer activations (TF32)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   // B fragments: W1^T (k = feature, n = neuron; k >= 9 is zero) and W2^T
-  uint32_t w1b[2][4][2], w2b[4][4][2];
+  uint32_t w1b[4][2], w2b[2][4][2];
   float b1v[4][2], b2v[4][2], w3v[4][2];
+  auto w1 = [&](int o, int k) { return k < NF ? params[OFF_W1 + o * NF + k] : 0.0f; };
 #pragma unroll
   for (int nt = 0; nt < 4; ++nt) {
     const int o = 8 * nt + g;
+    w1b[nt][0] = pack_h2(w1(o, 2 * t), w1(o, 2 * t + 1));
+    w1b[nt][1] = pack_h2(w1(o, 2 * t + 8), w1(o, 2 * t + 9));
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
-      const int k0 = 8 * ks + t, k1 = k0 + 4;
-      w1b[ks][nt][0] = to_tf32(k0 < NF ? params[OFF_W1 + o * NF + k0] : 0.0f);
-      w1b[ks][nt][1] = to_tf32(k1 < NF ? params[OFF_W1 + o * NF + k1] : 0.0f);
-    }
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      w2b[ks][nt][0] = to_tf32(params[OFF_W2 + o * NH + 8 * ks + t]);
-      w2b[ks][nt][1] = to_tf32(params[OFF_W2 + o * NH + 8 * ks + t + 4]);
+      const float* wr = params + OFF_W2 + o * NH + 16 * ks + 2 * t;
+      w2b[ks][nt][0] = pack_h2(wr[0], wr[1]);
+      w2b[ks][nt][1] = pack_h2(wr[8], wr[9]);
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {  // this thread's accumulator columns 8 nt + 2 t + j
@@ -294,58 +297,38 @@ __global__ void __launch_bounds__(TC_WARPS * 32)
     }
   }
   const float b3 = params[OFF_B3];
-  uint32_t* f = fs[w];
-  uint32_t* h = hs[w];
-  for (int k = lane; k < 16 * 16; k += 32) f[k] = 0u;
   const int64_t ntiles = (n + 15) / 16;
   const int64_t step = (int64_t)gridDim.x * TC_WARPS;
-  constexpr int FPL = (16 * NF + 31) / 32;  // feature values per lane and tile
-  // this lane's share of a tile's 16 x 9 features (0 beyond the last row)
-  auto load_tile = [&](int64_t tl, float (&v)[FPL]) {
+  // this lane's features of a tile: rows g and g + 8, columns 2t, 2t + 1 and
+  // (lanes with t == 0) column 8; 0 beyond the last row
+  auto load_tile = [&](int64_t tl, float (&v)[6]) {
 #pragma unroll
-    for (int q = 0; q < FPL; ++q) {
-      const int k = lane + 32 * q;
-      const int64_t e = tl * 16 * NF + k;
-      v[q] = (tl < ntiles && k < 16 * NF && e < n * NF) ? __ldg(feat + e) : 0.0f;
+    for (int h = 0; h < 2; ++h) {
+      const int64_t row = tl * 16 + g + 8 * h;
+      const bool ok = tl < ntiles && row < n;
+      const float* fr = feat + row * NF;
+      v[3 * h] = ok ? __ldg(fr + 2 * t) : 0.0f;
+      v[3 * h + 1] = ok ? __ldg(fr + 2 * t + 1) : 0.0f;
+      v[3 * h + 2] = (ok && t == 0) ? __ldg(fr + 8) : 0.0f;
     }
   };
-  float nxt[FPL];
+  float nxt[6];
   load_tile((int64_t)blockIdx.x * TC_WARPS + w, nxt);
   for (int64_t tile = (int64_t)blockIdx.x * TC_WARPS + w; tile < ntiles; tile += step) {
     const int64_t r0 = tile * 16;
     const int rows = (int)(n - r0 < 16 ? n - r0 : 16);
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < FPL; ++q) {
-      const int k = lane + 32 * q;
-      if (k < 16 * NF) f[(k / NF) * 16 + k % NF] = to_tf32(nxt[q]);
-    }
+    const uint32_t f0 = pack_h2(nxt[0], nxt[1]), f1 = pack_h2(nxt[3], nxt[4]),
+                   f2 = pack_h2(nxt[2], 0.0f), f3 = pack_h2(nxt[5], 0.0f);
     load_tile(tile + step, nxt);
-    __syncwarp();
     // layer 1: U1 = F W1^T + b1 (4 column tiles of 8, K = 16 with zeros beyond 9)
     float c1[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       c1[nt][0] = c1[nt][2] = b1v[nt][0];
       c1[nt][1] = c1[nt][3] = b1v[nt][1];
+      mma_f16(c1[nt], f0, f1, f2, f3, w1b[nt][0], w1b[nt][1]);
     }
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-      const int k = 8 * ks + t;
-      const uint32_t a0 = f[g * 16 + k], a1 = f[(g + 8) * 16 + k], a2 = f[g * 16 + k + 4],
-                     a3 = f[(g + 8) * 16 + k + 4];
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) mma_tf32(c1[nt], a0, a1, a2, a3, w1b[ks][nt][0], w1b[ks][nt][1]);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        h[g * TC_LD + 8 * nt + 2 * t + j] = to_tf32(gelu_fast(c1[nt][j]));
-        h[(g + 8) * TC_LD + 8 * nt + 2 * t + j] = to_tf32(gelu_fast(c1[nt][2 + j]));
-      }
-    __syncwarp();
-    // layer 2: U2 = H1 W2^T + b2, then z = GELU(U2) w3 + b3 per row
+    // layer 2: U2 = GELU(U1) W2^T + b2, the A fragments straight from c1
     float c2[4][4];
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
@@ -353,13 +336,17 @@ __global__ void __launch_bounds__(TC_WARPS * 32)
       c2[nt][1] = c2[nt][3] = b2v[nt][1];
     }
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const int k = 8 * ks + t;
-      const uint32_t a0 = h[g * TC_LD + k], a1 = h[(g + 8) * TC_LD + k],
-                     a2 = h[g * TC_LD + k + 4], a3 = h[(g + 8) * TC_LD + k + 4];
+    for (int ks = 0; ks < 2; ++ks) {
+      const float(&lo)[4] = c1[2 * ks];
+      const float(&hi)[4] = c1[2 * ks + 1];
+      const uint32_t a0 = pack_h2(gelu_fast(lo[0]), gelu_fast(lo[1]));
+      const uint32_t a1 = pack_h2(gelu_fast(lo[2]), gelu_fast(lo[3]));
+      const uint32_t a2 = pack_h2(gelu_fast(hi[0]), gelu_fast(hi[1]));
+      const uint32_t a3 = pack_h2(gelu_fast(hi[2]), gelu_fast(hi[3]));
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) mma_tf32(c2[nt], a0, a1, a2, a3, w2b[ks][nt][0], w2b[ks][nt][1]);
+      for (int nt = 0; nt < 4; ++nt) mma_f16(c2[nt], a0, a1, a2, a3, w2b[ks][nt][0], w2b[ks][nt][1]);
     }
+    // z = GELU(U2) w3 + b3 per row
     float zg = 0.0f, zg8 = 0.0f;  // partial z of rows g and g + 8 over this thread's columns
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt)
@@ -374,11 +361,11 @@ __global__ void __launch_bounds__(TC_WARPS * 32)
       zg += __shfl_xor_sync(0xffffffffu, zg, o);
       zg8 += __shfl_xor_sync(0xffffffffu, zg8, o);
     }
-    if (t == 0) {
-      if (g < rows) omega[r0 + g] = fmaxf(omega_max * (1.0f / (1.0f + expf(-(zg + b3)))), OMEGA_MIN);
-      if (g + 8 < rows)
-        omega[r0 + g + 8] = fmaxf(omega_max * (1.0f / (1.0f + expf(-(zg8 + b3)))), OMEGA_MIN);
-    }
+    // thread t == 0 writes row g, thread t == 1 row g + 8
+    const float z = (t == 0 ? zg : zg8) + b3;
+    const int rr = t == 0 ? g : g + 8;
+    if (t < 2 && rr < rows)
+      omega[r0 + rr] = fmaxf(omega_max * (1.0f / (1.0f + expf(-z))), OMEGA_MIN);
   }
 }
 

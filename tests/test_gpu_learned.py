@@ -54,7 +54,7 @@ def test_forward_backward_match_oracle(amg, orc, lm):
 @pytest.mark.parametrize("shape,omega_max", [((10, 9, 8), 1.0), ((7, 6, 5), 1.0),
                                              ((7, 6, 5), 1.9)])
 def test_tensor_core_forward_matches_oracle(amg, orc, lm, shape, omega_max):
-    # TF32 operands keep 10 mantissa bits: omega within 3e-3 of the FP64 network
+    # FP16 operands keep 10 mantissa bits: omega within 3e-3 of the FP64 network
     # (210 rows: a ragged last tile of 16)
     A = _problem(shape)
     n = shape[0] * shape[1] * shape[2]
