@@ -39,6 +39,7 @@ struct mlp_handle {
   double* v = nullptr;
   int t = 0;
   int num_sms = 0;
+  int tc_blocks = 0;  // resident CTAs of the tensor-core forward pass on this GPU
   amg::Arena arena;
 };
 
@@ -227,28 +228,37 @@ __global__ void __launch_bounds__(FW_WARPS * 32)
 // pass from one product to the next in registers.  The features come
 // straight from global memory into the first A fragment (columns 9..15 are
 // zero); the weights stay in registers as B fragments for the whole launch.
-// GELU uses erf_as7126.  omega agrees with the FP32 pass to about 1e-3.
+// GELU uses gelu_fast.  omega agrees with the FP32 pass to about 1e-3.
 constexpr int TC_WARPS = 4;
 
-// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula
-// 7.1.26: for x >= 0, erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5)
-// e^(-x^2) with t = 1 / (1 + p x), |error| <= 1.5e-7; odd in x.  About a
-// dozen instructions (a fast reciprocal and exponential, five FMAs), against
-// the exact erff's longer sequence; the tensor-core forward pass, whose FP16
-// operands already limit omega to about 1e-3, uses it in its GELUs.
-__device__ __forceinline__ float erf_as7126(float x) {
-  const float ax = fabsf(x);
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
-  const float poly =
-      t * fmaf(fmaf(fmaf(fmaf(1.061405429f, t, -1.453152027f), t, 1.421413741f), t,
-                    -0.284496736f),
-               t, 0.254829592f);
-  const float r = fmaf(-poly, __expf(-ax * ax), 1.0f);
-  return copysignf(r, x);
+// GELU with erf by Abramowitz & Stegun, Handbook of Mathematical Functions,
+// formula 7.1.26: for x >= 0, erf(x) = 1 - P(t) e^(-x^2), P(t) = a1 t + a2
+// t^2 + a3 t^3 + a4 t^4 + a5 t^5, t = 1 / (1 + p x), |error| <= 1.5e-7; odd in
+// x.  With x = u / sqrt(2), sign(x) u = |u| turns 0.5 u (1 + erf(x)) into
+//   GELU(u) = max(u, 0) - |u| (P(t) / 2) e^(-u^2 / 2),  t = 1 / (1 + p |u| / sqrt(2)),
+// which needs no sign transfer: a hardware reciprocal and base-2 exponential
+// (rcp.approx, ex2.approx; e^y = 2^(y log2 e)), six FMAs and four other
+// operations.  The tensor-core forward pass, whose FP16 operands already
+// limit omega to about 1e-3, uses it in its GELUs.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
-
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 __device__ __forceinline__ float gelu_fast(float u) {
-  return 0.5f * u * (1.0f + erf_as7126(u * 0.70710678f));
+  const float ax = fabsf(u);
+  const float t = rcp_approx(fmaf(0.3275911f * 0.70710678f, ax, 1.0f));
+  // P(t) / 2, the coefficients a1..a5 halved
+  const float q = t * fmaf(fmaf(fmaf(fmaf(0.5307027145f, t, -0.7265760135f), t, 0.7107068705f),
+                                t, -0.142248368f),
+                           t, 0.127414796f);
+  const float e = ex2_approx(u * (u * (-0.5f * 1.44269504f)));
+  return fmaf(-(ax * q), e, fmaxf(u, 0.0f));
 }
 
 // two floats rounded to FP16 (nearest even), lo in the low half
@@ -257,18 +267,21 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-__device__ __forceinline__ void mma_f16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                        uint32_t a3, uint32_t b0, uint32_t b1) {
+// d = A B + c (c is read, d written: a bias can enter as c without a copy)
+__device__ __forceinline__ void mma_f16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                        uint32_t a3, uint32_t b0, uint32_t b1, float c0, float c1,
+                                        float c2, float c3) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "{%8,%9}, {%10,%11,%12,%13};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(c0), "f"(c1), "f"(c2),
+        "f"(c3));
 }
 
 // The next tile's features are loaded into registers while the current one
 // is computed.
-__global__ void __launch_bounds__(TC_WARPS * 32)
+__global__ void __launch_bounds__(TC_WARPS * 32, 5)
     k_mlp_forward_tc(int64_t n, const float* __restrict__ params,
                      const float* __restrict__ feat, float omega_max,
                      float* __restrict__ omega) {
@@ -323,18 +336,11 @@ __global__ void __launch_bounds__(TC_WARPS * 32)
     // layer 1: U1 = F W1^T + b1 (4 column tiles of 8, K = 16 with zeros beyond 9)
     float c1[4][4];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      c1[nt][0] = c1[nt][2] = b1v[nt][0];
-      c1[nt][1] = c1[nt][3] = b1v[nt][1];
-      mma_f16(c1[nt], f0, f1, f2, f3, w1b[nt][0], w1b[nt][1]);
-    }
+    for (int nt = 0; nt < 4; ++nt)
+      mma_f16(c1[nt], f0, f1, f2, f3, w1b[nt][0], w1b[nt][1], b1v[nt][0], b1v[nt][1],
+              b1v[nt][0], b1v[nt][1]);
     // layer 2: U2 = GELU(U1) W2^T + b2, the A fragments straight from c1
     float c2[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-      c2[nt][0] = c2[nt][2] = b2v[nt][0];
-      c2[nt][1] = c2[nt][3] = b2v[nt][1];
-    }
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks) {
       const float(&lo)[4] = c1[2 * ks];
@@ -344,7 +350,14 @@ __global__ void __launch_bounds__(TC_WARPS * 32)
       const uint32_t a2 = pack_h2(gelu_fast(hi[0]), gelu_fast(hi[1]));
       const uint32_t a3 = pack_h2(gelu_fast(hi[2]), gelu_fast(hi[3]));
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) mma_f16(c2[nt], a0, a1, a2, a3, w2b[ks][nt][0], w2b[ks][nt][1]);
+      for (int nt = 0; nt < 4; ++nt) {
+        if (ks == 0)
+          mma_f16(c2[nt], a0, a1, a2, a3, w2b[0][nt][0], w2b[0][nt][1], b2v[nt][0], b2v[nt][1],
+                  b2v[nt][0], b2v[nt][1]);
+        else
+          mma_f16(c2[nt], a0, a1, a2, a3, w2b[1][nt][0], w2b[1][nt][1], c2[nt][0], c2[nt][1],
+                  c2[nt][2], c2[nt][3]);
+      }
     }
     // z = GELU(U2) w3 + b3 per row
     float zg = 0.0f, zg8 = 0.0f;  // partial z of rows g and g + 8 over this thread's columns
@@ -364,8 +377,10 @@ __global__ void __launch_bounds__(TC_WARPS * 32)
     // thread t == 0 writes row g, thread t == 1 row g + 8
     const float z = (t == 0 ? zg : zg8) + b3;
     const int rr = t == 0 ? g : g + 8;
+    // sigmoid by the hardware reciprocal and exponential (omega needs ~1e-3)
     if (t < 2 && rr < rows)
-      omega[r0 + rr] = fmaxf(omega_max * (1.0f / (1.0f + expf(-z))), OMEGA_MIN);
+      omega[r0 + rr] =
+          fmaxf(omega_max * rcp_approx(1.0f + ex2_approx(z * -1.44269504f)), OMEGA_MIN);
   }
 }
 
@@ -513,6 +528,13 @@ int mlp_create(uint64_t seed, mlp_handle** M) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail(AMG_ERR_CUDA);
+  // the forward pass loops over tiles in a grid of exactly the CTAs that fit
+  // the GPU at once (a second, partial wave would double its tail)
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, amg::k_mlp_forward_tc,
+                                                    amg::TC_WARPS * 32, 0) != cudaSuccess)
+    return fail(AMG_ERR_CUDA);
+  h->tc_blocks = h->num_sms * std::max(occ, 1);
   int rc;
   if ((rc = h->arena.alloc_n(&h->params, NPARAM)) < 0) return fail(rc);
   if ((rc = h->arena.alloc_n(&h->grad, NPARAM)) < 0) return fail(rc);
@@ -579,7 +601,9 @@ int mlp_features(const amg_csr* A, int64_t nx, int64_t ny, int64_t nz, float* fe
   int dev = 0, sms = 0;
   AMG_CUDA_TRY(cudaGetDevice(&dev));
   AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  k_features<<<grid_for(A->n, 256, sms, 8), 256, 0, (cudaStream_t)stream>>>(
+  int occ = 0;  // a grid of the CTAs that fit at once (no partial second wave)
+  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_features, 256, 0));
+  k_features<<<grid_for(A->n, 256, sms, std::max(occ, 1)), 256, 0, (cudaStream_t)stream>>>(
       A->n, nx, nx * ny, A->rowptr, A->col, A->val, feat);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
@@ -594,8 +618,10 @@ int mlp_forward(const mlp_handle* M, int64_t n, const float* feat, float* omega,
     k_mlp_forward_tiled<<<grid_for((n + 31) / 32, FW_WARPS, M->num_sms, 5), FW_WARPS * 32, 0,
                           (cudaStream_t)stream>>>(n, M->params, feat, M->omega_max, omega);
   } else {
-    k_mlp_forward_tc<<<grid_for((n + 15) / 16, TC_WARPS, M->num_sms, 8), TC_WARPS * 32, 0,
-                       (cudaStream_t)stream>>>(n, M->params, feat, M->omega_max, omega);
+    const int64_t tiles = (n + 15) / 16;
+    const int grid = (int)std::min<int64_t>((tiles + TC_WARPS - 1) / TC_WARPS, M->tc_blocks);
+    k_mlp_forward_tc<<<grid, TC_WARPS * 32, 0, (cudaStream_t)stream>>>(n, M->params, feat,
+                                                                    M->omega_max, omega);
   }
   AMG_LAUNCH_CHECK();
   return AMG_OK;

@@ -815,15 +815,38 @@ __global__ void k_ap_fill(int64_t n, const int64_t* rowptr, const int32_t* col, 
   }
 }
 
-// Ah values: a_ij * s_j on A's sliced-ELL slots (padding stays 0).
-__global__ void k_scale_cols(int64_t m, const int32_t* col, const double* val, const double* s,
-                             double* out64, float* out32, __nv_bfloat16* out16) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const double v = __dmul_rn(val[e], s[col[e]]);
-    out64[e] = v;
-    if (out32) out32[e] = (float)v;
-    if (out16) out16[e] = __float2bfloat16_rn((float)v);
+// Ah values: a_ij * s_j on A's sliced-ELL slots (padding stays 0).  Each
+// thread takes SC_U slots a grid stride apart per step and issues all their
+// loads, then all their gathers, before any product, so that SC_U times the
+// bytes of a one-slot loop are in flight.
+constexpr int SC_U = 4;
+__global__ void k_scale_cols(int64_t m, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const double* __restrict__ s,
+                             double* __restrict__ out64, float* __restrict__ out32,
+                             __nv_bfloat16* __restrict__ out16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < m;
+       e0 += SC_U * stride) {
+    int32_t c[SC_U];
+    double a[SC_U], sj[SC_U];
+#pragma unroll
+    for (int u = 0; u < SC_U; ++u) {
+      const int64_t e = e0 + u * stride;
+      c[u] = e < m ? ld_stream(col + e) : 0;
+      a[u] = e < m ? ld_stream(val + e) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < SC_U; ++u) sj[u] = e0 + u * stride < m ? __ldg(s + c[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < SC_U; ++u) {
+      const int64_t e = e0 + u * stride;
+      if (e < m) {
+        const double v = __dmul_rn(a[u], sj[u]);
+        out64[e] = v;
+        if (out32) out32[e] = (float)v;
+        if (out16) out16[e] = __float2bfloat16_rn((float)v);
+      }
+    }
   }
 }
 
@@ -832,8 +855,10 @@ static int build_ah(Arena& ar, Level& L, int num_sms, cudaStream_t s) {
   if (!L.ah64) AMG_TRY(ar.alloc_n(&L.ah64, m));
   if (L.vstore == VAL_F32 && !L.ah32) AMG_TRY(ar.alloc_n(&L.ah32, m));
   if (L.vstore == VAL_BF16 && !L.ah16) AMG_TRY(ar.alloc_n(&L.ah16, m));
-  k_scale_cols<<<grid_for(m, 256, num_sms, 8), 256, 0, s>>>(m, L.A.col, L.A.v64, L.s64, L.ah64,
-                                                            L.ah32, L.ah16);
+  int occ = 0;  // a grid of the CTAs that fit at once (no partial second wave)
+  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_scale_cols, 256, 0));
+  k_scale_cols<<<grid_for((m + SC_U - 1) / SC_U, 256, num_sms, std::max(occ, 1)), 256, 0, s>>>(
+      m, L.A.col, L.A.v64, L.s64, L.ah64, L.ah32, L.ah16);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
