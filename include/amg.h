@@ -144,9 +144,10 @@ typedef struct amg_options {
                             row sums kept): P = P_hat - w D^-1 A_F P_hat, D and
                             w from A; 0 (default): with A, the paper's formula.
                             In [0, 1) */
-  int stream_ring;       /* 1 (default): the FP64 level kernels of a one-system
-                            hierarchy with one thread per row (pre- and
-                            post-smoother, PCG product) stream each slice into a
+  int stream_ring;       /* 1 (default): the level kernels with FP64 or FP32
+                            operator values of a one-system hierarchy with one
+                            thread per row (pre- and post-smoother; the FP64
+                            PCG product) stream each slice into a
                             shared-memory ring by bulk copies (cp.async.bulk,
                             mbarrier completion), with the library's number of
                             stages per warp; 2..4: with that many stages;

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(SELL_BLOCK, SELL_MIN_BLOCKS)
   }
 }
 
-// k_pre and k_post (one sweep, one system, one thread per row, FP64
+// k_pre and k_post (one sweep, one system, one thread per row, FP64 or FP32
 // operator values) on the shared-memory ring of ring.cuh: the same row
 // arithmetic in the same order, so the same bits as the per-lane-load
 // kernels; the dot products of the level-0 post-smoother are summed per
@@ -490,9 +490,8 @@ static int launch_pre(const amg_handle* H, const Level& L, const V* ah, const BT
   const int grid = sell_grid(sell_groups(L.A), H->num_sms);
   SellView<V> v = view<V>(L.A, ah);
   v.act = act;
-  // FP64 operators (the ring's gain is where GB300's FP64 pipe co-limits the
-  // stream; FP32 values stream faster from the per-lane kernels)
-  if constexpr (sizeof(V) == 8) {
+  // FP64 and FP32 operators (BF16 values keep the per-lane kernels)
+  if constexpr (sizeof(V) >= 4) {
     if (!act && H->opt.stream_ring) {
       RingGeom g = ring_plan(L.A, (int)sizeof(V), ring_stages(H), RingRows());
       if (g.D) {
@@ -539,7 +538,7 @@ static int launch_post(const amg_handle* H, const Level& L, const V* ap, const B
     }
   }
   if (in.xp) return AMG_ERR_ARG;  // several sweeps: the dot products follow separately
-  if constexpr (sizeof(V) == 8) {  // FP64 operators, as for k_pre
+  if constexpr (sizeof(V) >= 4) {  // FP64 and FP32 operators, as for k_pre
     if (!act && !slice_part && H->opt.stream_ring) {
       RingRows rows;  // indices 0..4 as read by k_post_ring
       rows.add(sc, (int)sizeof(T));

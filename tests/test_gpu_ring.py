@@ -5,9 +5,9 @@ Per row both forms run the same FMAs in the same order, so V-cycles (no dot
 products) agree bit for bit; PCG's dot products are summed in another order
 (the ring kernels use another grid), so its iterates agree to rounding.
 Cases cover a ragged last slice (rows not a multiple of 32), several slices
-per warp, FP64 hierarchies (the ring's kernels) next to FP32 and BF16 ones
-(per-lane kernels on both sides), and a matrix whose widest slice does not
-fit the ring (the per-lane kernels run).
+per warp, FP64 and FP32 hierarchies (the ring's kernels), FP32 with BF16
+values from level 2 (per-lane kernels on both sides there), and a matrix
+whose widest slice does not fit the ring (the per-lane kernels run).
 """
 
 import numpy as np
