@@ -364,16 +364,17 @@ SM_COUNT, SM_MAX_GHZ = 152, 2.07
 
 def fp64_pipe(H, level, kind, ms, a):
     """FP64 instructions of one pre- or post-smoother launch of an FP64
-    hierarchy (one per stored entry, plus per row: 1 for r = b - acc, 3 for
-    y, e and z, and on level 0 one more for (r, z)) against the FP64 pipe's
-    peak: those kernels are co-limited by HBM and by GB300's reduced-rate FP64
-    arithmetic."""
+    hierarchy against the FP64 pipe's peak: one FMA per stored entry; the
+    pre-smoother's r = b - (A S) b runs from b_i down by negated FMAs (nothing
+    more a row), the post-smoother adds b_i + r_i and ends with
+    z = s_i acc + x_c (two a row), and on level 0 forms (r, z) for PCG's beta
+    (one FMA a row more).  Those kernels are co-limited by HBM and by GB300's
+    reduced-rate FP64 arithmetic."""
     if a.precision != "f64" or kind not in ("pre", "post"):
         return None
     n = H.level_info(level)[0]
     slots = H.level_layout(level, ap=(kind == "post"))["slots"]
-    # level 0's post-smoother also forms (r, z) for PCG's beta (one FMA a row)
-    per_row = 1 if kind == "pre" else (4 if level == 0 else 3)
+    per_row = 0 if kind == "pre" else (3 if level == 0 else 2)
     ops = slots + per_row * n
     peak = FP64_OPS_PER_SM_CLOCK * SM_COUNT * SM_MAX_GHZ * 1e9
     rate = ops / (ms * 1e-3)
