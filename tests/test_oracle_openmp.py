@@ -25,7 +25,8 @@ out = {"threads": oracle.threads()}
 A = poisson3d(21, 19, 23)          # 9177 rows: dot products end in a ragged block
 b = uniform01(5, A[0].size - 1)
 for name, kw in (("v11", {}),
-                 ("vmatch", dict(sweeps=3, smooth_sweeps=2, variable=True, coarse="pcg"))):
+                 ("vmatch", dict(sweeps=3, smooth_sweeps=2, variable=True, coarse="pcg")),
+                 ("smatch", dict(sweeps=3, smooth_sweeps=2, coarse="pcg", smoothed=True))):
     H = oracle.Hierarchy(A, **kw)
     x, info = oracle.pcg(A, b, tol=1e-10, hier=H, history=True,
                          beta_form=1 if kw else 0)
@@ -48,7 +49,7 @@ def test_openmp_oracle_gives_the_same_bits():
     omp = _run(True, 4)
     assert plain["threads"] == 1
     assert omp["threads"] == 4
-    for name in ("v11", "vmatch"):
+    for name in ("v11", "vmatch", "smatch"):
         assert omp[name]["it"] == plain[name]["it"] > 5
         assert omp[name]["res"] == plain[name]["res"]
         assert omp[name]["x"] == plain[name]["x"]
