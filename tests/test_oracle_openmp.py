@@ -2,8 +2,9 @@
 cores) parallelises only loops whose iterations write disjoint outputs and
 keeps every sum in order, so it must reproduce the single-thread oracle bit
 for bit: the whole PCG residual history and the solution, on the matching
-hierarchy with Cholesky and on the variable V-cycle with the PCG coarsest
-solve, with several threads and a ragged last dot-product block."""
+hierarchy with Cholesky, on the variable V-cycle with the PCG coarsest solve
+and with smoothed prolongators (P and P^T through the parallel SpMV), with
+several threads and a ragged last dot-product block."""
 
 import json
 import os
